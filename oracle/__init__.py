@@ -1,0 +1,197 @@
+"""FP64 CPU oracle for MFA-DVR: ctypes wrapper over ``mfa_oracle.c``.
+
+TEST INFRASTRUCTURE ONLY.  The tests, the package smoke check and the
+benchmark's CPU-baseline / reference leg are the only callers.  The CUDA
+library and its Python binding never import this package, and this package
+imports nothing from them.
+
+The C file holds the arithmetic (B-spline model of Sec. 2.3, value and
+gradient queries, the ray caster of Algorithm 1); this module only compiles it
+with gcc and marshals arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mfa_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` next to its source (gcc, -O2, pthreads)."""
+    with _lock:
+        stale = (not os.path.exists(_LIB_PATH)
+                 or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+        if force or stale:
+            tmp = _LIB_PATH + f".tmp{os.getpid()}"
+            subprocess.check_call(
+                ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
+                 "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC,
+                 "-lm", "-lpthread"])
+            os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Model(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int32 * 3), ("n", ctypes.c_int32 * 3),
+                ("ctrl", ctypes.c_void_p),
+                ("box_min", ctypes.c_double * 3), ("box_max", ctypes.c_double * 3)]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("eye", ctypes.c_double * 3),
+                ("center", ctypes.c_double * 3), ("up", ctypes.c_double * 3),
+                ("fovy_deg", ctypes.c_double), ("ortho_height", ctypes.c_double)]
+
+
+class RenderParams(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("step", ctypes.c_double), ("max_opacity", ctypes.c_double),
+                ("ref_step", ctypes.c_double), ("tf_rgba", ctypes.c_void_p),
+                ("tf_size", ctypes.c_int32), ("tf_lo", ctypes.c_double),
+                ("tf_hi", ctypes.c_double), ("shading", ctypes.c_int32),
+                ("ka", ctypes.c_double), ("kd", ctypes.c_double),
+                ("ks", ctypes.c_double), ("shininess", ctypes.c_double)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.POINTER
+        L.orc_make_knots.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]
+        L.orc_find_span.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_double), ctypes.c_double]
+        L.orc_basis_ders.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, P(ctypes.c_double),
+                                     P(ctypes.c_double), P(ctypes.c_double)]
+        L.orc_basis_ders.restype = None
+        L.orc_basis_brute.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, P(ctypes.c_double), ctypes.c_int]
+        L.orc_basis_brute.restype = ctypes.c_double
+        L.orc_basis_brute_der.argtypes = L.orc_basis_brute.argtypes
+        L.orc_basis_brute_der.restype = ctypes.c_double
+        L.orc_eval_points.argtypes = [P(Model), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+        L.orc_render.argtypes = [P(Model), P(Camera), P(RenderParams), ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p]
+        _lib = L
+    return _lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def knots(n: int, p: int) -> np.ndarray:
+    t = np.zeros(n + p + 1, dtype=np.float64)
+    if lib().orc_make_knots(n, p, _dptr(t)) != 0:
+        raise ValueError("bad knot sizes")
+    return t
+
+
+def find_span(n: int, p: int, u: float) -> int:
+    t = knots(n, p)
+    return lib().orc_find_span(n, p, _dptr(t), float(u))
+
+
+def basis_ders(n: int, p: int, u: float):
+    """(span, N[0..p], dN[0..p]) at u for the clamped uniform knots."""
+    t = knots(n, p)
+    s = lib().orc_find_span(n, p, _dptr(t), float(u))
+    N = np.zeros(p + 1)
+    dN = np.zeros(p + 1)
+    lib().orc_basis_ders(s, float(u), p, _dptr(t), _dptr(N), _dptr(dN))
+    return s, N, dN
+
+
+def basis_brute(n: int, p: int, u: float):
+    """All n basis functions and derivatives at u by the raw recursion."""
+    t = knots(n, p)
+    N = np.array([lib().orc_basis_brute(i, p, float(u), _dptr(t), n) for i in range(n)])
+    dN = np.array([lib().orc_basis_brute_der(i, p, float(u), _dptr(t), n) for i in range(n)])
+    return N, dN
+
+
+def _model(ctrl: np.ndarray, degree, box_min=(0.0, 0.0, 0.0), box_max=(1.0, 1.0, 1.0)):
+    """ctrl: array of shape (n2, n1, n0) (u fastest in memory); FP32
+    lattices convert to FP64 exactly."""
+    ctrl = np.ascontiguousarray(ctrl, dtype=np.float64)
+    if ctrl.ndim != 3:
+        raise ValueError("ctrl must be 3-D (n_w, n_v, n_u)")
+    n = (ctrl.shape[2], ctrl.shape[1], ctrl.shape[0])
+    deg = (degree,) * 3 if np.isscalar(degree) else tuple(degree)
+    m = Model()
+    m.p[:] = [int(x) for x in deg]
+    m.n[:] = [int(x) for x in n]
+    m.ctrl = ctrl.ctypes.data
+    m.box_min[:] = [float(x) for x in box_min]
+    m.box_max[:] = [float(x) for x in box_max]
+    return m, ctrl
+
+
+def eval_points(ctrl, degree, uvw, *, brute=False, threads=None, with_spans=True):
+    """Value and gradient (f, df/du, df/dv, df/dw) in FP64 at FP32 points."""
+    m, keep = _model(ctrl, degree)
+    uvw = np.ascontiguousarray(uvw, dtype=np.float32).reshape(-1, 3)
+    npts = uvw.shape[0]
+    out = np.zeros((npts, 4), dtype=np.float64)
+    spans = np.zeros((npts, 3), dtype=np.int32) if (with_spans and not brute) else None
+    threads = threads or (os.cpu_count() or 1)
+    rc = lib().orc_eval_points(ctypes.byref(m), npts, uvw.ctypes.data, out.ctypes.data,
+                               spans.ctypes.data if spans is not None else None,
+                               int(threads), int(bool(brute)))
+    if rc != 0:
+        raise ValueError("oracle: invalid model")
+    del keep
+    return (out, spans) if spans is not None else out
+
+
+def render(ctrl, degree, camera: dict, params: dict, *, box_min=(0, 0, 0), box_max=(1, 1, 1),
+           row_step=1, threads=None, brute=False):
+    """Algorithm 1 in FP64.  Returns dict with rgba (H, W, 4), nsamples,
+    nambig, rgba_alt and nsamples_alt (see mfa_oracle.c)."""
+    m, keep = _model(ctrl, degree, box_min, box_max)
+    cam = Camera()
+    cam.kind = int(camera.get("kind", 1))
+    cam.eye[:] = [float(x) for x in camera["eye"]]
+    cam.center[:] = [float(x) for x in camera.get("center", (0.5, 0.5, 0.5))]
+    cam.up[:] = [float(x) for x in camera.get("up", (0.0, 0.0, 1.0))]
+    cam.fovy_deg = float(camera.get("fovy_deg", 60.0))
+    cam.ortho_height = float(camera.get("ortho_height", 1.0))
+    tf = np.ascontiguousarray(params["tf"], dtype=np.float32).reshape(-1, 4)
+    rp = RenderParams()
+    W, H = int(params["width"]), int(params["height"])
+    rp.width, rp.height = W, H
+    rp.step = float(params["step"])
+    rp.max_opacity = float(params.get("max_opacity", 0.99))
+    rp.ref_step = float(params.get("ref_step", 0.0))
+    rp.tf_rgba = tf.ctypes.data
+    rp.tf_size = tf.shape[0]
+    rp.tf_lo = float(params.get("tf_lo", float("nan")))
+    rp.tf_hi = float(params.get("tf_hi", float("nan")))
+    rp.shading = int(params.get("shading", 1))
+    rp.ka = float(params.get("ka", 0.1))
+    rp.kd = float(params.get("kd", 0.7))
+    rp.ks = float(params.get("ks", 0.2))
+    rp.shininess = float(params.get("shininess", 10.0))
+    rgba = np.zeros((H, W, 4), dtype=np.float64)
+    alt = np.zeros((H, W, 4), dtype=np.float64)
+    ns = np.zeros((H, W), dtype=np.int32)
+    ns_alt = np.zeros((H, W), dtype=np.int32)
+    amb = np.zeros((H, W), dtype=np.int32)
+    threads = threads or (os.cpu_count() or 1)
+    rc = lib().orc_render(ctypes.byref(m), ctypes.byref(cam), ctypes.byref(rp), int(row_step),
+                          int(threads), int(bool(brute)), rgba.ctypes.data, ns.ctypes.data,
+                          amb.ctypes.data, alt.ctypes.data, ns_alt.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle: invalid render arguments")
+    del keep, tf
+    return {"rgba": rgba, "nsamples": ns, "nambig": amb, "rgba_alt": alt, "nsamples_alt": ns_alt}
