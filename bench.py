@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark of the MFA-DVR hot path on GB300.
+
+One step = one pass of the whole path over one batch of synthetic input:
+  * mfadvr_render of the 1024^2 perspective frame of the degree-3, 128^3
+    Gaussian-sum model (ray definition, box intersection, samples at step
+    1/1024, span lookup, basis + derivatives, (p+1)^3 contraction, TF, Phong
+    shading, front-to-back compositing with early termination), and
+  * mfadvr_eval_points on 2^24 uniform parameter points (value + gradient).
+The metric counts value+gradient queries: render samples actually composited
+(exact, from the per-pixel sample counts) plus evaluated points, per second.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MFA value+grad samples/s"
+UNIT = "samples/s"
+C_FMA = {p: 2 * (p + 1) ** 3 + 3 * (p + 1) ** 2 + 4 * (p + 1) for p in range(1, 6)}
+FP32_LANES_PER_SM = 128
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the 16-bit storage comparison")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [l.strip().split(", ") for l in self.file.read().splitlines() if l.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip() == "Active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on host cores
+# ---------------------------------------------------------------------------
+
+def _oracle_sample(wl, row_step, npts):
+    """Oracle on every row_step-th row of the frame and the first npts points;
+    returns (queries, seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.render(wl["ctrl"], wl["degree"], wl["camera"], dict(wl["params"], tf=wl["tf"]), row_step=row_step)
+    t1 = time.perf_counter()
+    oracle.eval_points(wl["ctrl"], wl["degree"], wl["points"][:npts], with_spans=False)
+    t2 = time.perf_counter()
+    rs = int(r["nsamples"][::row_step].sum())
+    return rs + npts, t2 - t0, rs, t1 - t0, t2 - t1
+
+
+def run_reference(args, wl):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    row_step, npts = 16, 1 << 20
+    for _ in range(args.warmup):
+        _oracle_sample(wl, row_step, npts)
+    tot_q, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        q, t, *_ = _oracle_sample(wl, row_step, npts)
+        tot_q += q
+        tot_t += t
+    value = tot_q / tot_t
+    sample = f"every {row_step}th row of the 1024^2 frame + the first 2^20 of the 2^24 points, per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(wl, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config(wl, args):
+    return {"workload": "gauss20_128cube_p3: 1024x1024 perspective render (60 deg, step 1/1024, O_max 0.99, "
+                        "TF 256, opacity ref 1/16, shading) + eval_points on 2^24 uniform points",
+            "model": f"MFA degree {wl['degree']}, 128^3 control points, clamped uniform knots",
+            "storage": args.storage, "image": "1024x1024", "eval_points": 1 << 24,
+            "l2": "flushed between steps (256 MiB write outside the timed events)",
+            "parallelism": f"replicas x{args.gpus} (independent frames per GPU)"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, wl):
+    import numpy as np
+    import torch
+
+    from paper_2204_11762_gb300 import mfadvr
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    ctx = mfadvr.Context(local)
+    p = wl["degree"]
+    mid = ctx.load_model(wl["ctrl"], p, storage=args.storage)
+    pts = wl["points"]
+    npts = pts.shape[0]
+    prm = wl["params"]
+    W, H = prm["width"], prm["height"]
+    d_pts = torch.from_numpy(pts).to(dev)
+    d_out = torch.empty((npts, 4), dtype=torch.float32, device=dev)
+    d_tf = torch.from_numpy(wl["tf"]).to(dev)
+    d_img = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    d_ns = torch.empty((H, W), dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(m=mid):
+        ctx.render(m, wl["camera"], prm, d_tf, wl["tf"].shape[0], d_img, d_ns, stream=stream)
+        ctx.eval_points(m, d_pts, npts, d_out, None, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+    render_samples = int(d_ns.sum(dtype=torch.int64).item())
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        ctx.render(mid, wl["camera"], prm, d_tf, wl["tf"].shape[0], d_img, d_ns, stream=stream)
+        ev[k][1].record(stream)
+        ctx.eval_points(mid, d_pts, npts, d_out, None, stream=stream)
+        ev[k][2].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    wall1 = time.perf_counter()
+    clk = clocks.stop()
+    render_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    eval_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    total_ms = sum(render_ms) + sum(eval_ms)
+    assert int(d_ns.sum(dtype=torch.int64).item()) == render_samples, "sample count changed between steps"
+
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units_per_step = render_samples + npts
+    value = world * units_per_step * args.steps / (total_ms / 1000.0)
+
+    # ---- roofline of the dominant kernel (render: FP32 FMA pipe) ---------
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks = _measured_peaks()
+    sm_max_mhz = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    fma_peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    r_mean = statistics.mean(render_ms)
+    e_mean = statistics.mean(eval_ms)
+    render_tflops = render_samples * C_FMA[p] * 2 / (r_mean / 1000.0) / 1e12
+    eval_tflops = npts * C_FMA[p] * 2 / (e_mean / 1000.0) / 1e12
+    eval_io_bytes = npts * (12 + 16)
+    dominant = "render" if r_mean >= e_mean else "eval_points"
+    if dominant == "render":
+        roof = {"kernel": "render_kernel", "bound": "alu", "achieved": render_tflops, "peak": fma_peak_tflops,
+                "unit": "TFLOP/s", "frac": render_tflops / fma_peak_tflops, "traffic": None,
+                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 FLOP x {sm_max_mhz:.0f} MHz",
+                "per_unit": f"{C_FMA[p]} FMA per sample (sum-factorised contraction, degree {p})"}
+    else:
+        roof = {"kernel": "eval_points_kernel", "bound": "alu", "achieved": eval_tflops, "peak": fma_peak_tflops,
+                "unit": "TFLOP/s", "frac": eval_tflops / fma_peak_tflops, "traffic": None,
+                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 FLOP x {sm_max_mhz:.0f} MHz",
+                "per_unit": f"{C_FMA[p]} FMA per point"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else
+            f"f32 (storage {args.storage})", "data": "synthetic", "config": _config(wl, args),
+            "gpu_launches": 2 * args.steps,
+            "frames_per_s": world * 1000.0 / r_mean,
+            "render": {"samples_per_frame": render_samples, "ms_mean": r_mean,
+                       "ms_p50": statistics.median(render_ms),
+                       "ms_p99": sorted(render_ms)[min(len(render_ms) - 1, int(0.99 * len(render_ms)))],
+                       "samples_per_s": render_samples / (r_mean / 1000.0), "tflops": render_tflops},
+            "eval_points": {"points": npts, "ms_mean": e_mean, "points_per_s": npts / (e_mean / 1000.0),
+                            "tflops": eval_tflops, "io_gbs": eval_io_bytes / (e_mean / 1000.0) / 1e9,
+                            "fma_frac": eval_tflops / fma_peak_tflops,
+                            "hbm_frac": (eval_io_bytes / (e_mean / 1000.0) / 1e9) / peaks["hbm_gbs"]
+                            if "hbm_gbs" in peaks else None},
+            "roofline": roof, "clocks": clk, "wall_s": wall1 - wall0}
+
+    # ---- mixed precision: same step with 16-bit storage ------------------
+    if not args.no_mixed and args.storage == "f32":
+        mixed = {}
+        for st in ("f16", "bf16"):
+            m2 = ctx.load_model(wl["ctrl"], p, storage=st)
+            for _ in range(3):
+                flush.zero_()
+                step(m2)
+            ev2 = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+            for k in range(args.steps):
+                flush.zero_()
+                ev2[k][0].record(stream)
+                ctx.render(m2, wl["camera"], prm, d_tf, wl["tf"].shape[0], d_img, d_ns, stream=stream)
+                ev2[k][1].record(stream)
+                ctx.eval_points(m2, d_pts, npts, d_out, None, stream=stream)
+                ev2[k][2].record(stream)
+            torch.cuda.synchronize(dev)
+            rs2 = int(d_ns.sum(dtype=torch.int64).item())
+            rm = statistics.mean([e[0].elapsed_time(e[1]) for e in ev2])
+            em = statistics.mean([e[1].elapsed_time(e[2]) for e in ev2])
+            mixed[st] = {"value": (rs2 + npts) / ((rm + em) / 1000.0), "render_ms": rm, "eval_ms": em,
+                         "render_samples_per_s": rs2 / (rm / 1000.0)}
+            ctx.unload_model(m2)
+        line["mixed_precision"] = mixed
+
+    # ---- end to end through the host-buffer entry points -----------------
+    if not args.no_e2e:
+        h_pts = torch.from_numpy(pts).pin_memory()
+        h_out = torch.empty((npts, 4), dtype=torch.float32).pin_memory()
+        h_img = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+        h_tf = torch.from_numpy(wl["tf"]).pin_memory()
+        tf_np = h_tf.numpy()
+        img_np = h_img.numpy()
+        k2 = max(3, min(args.steps, 10))
+        for _ in range(2):
+            ctx.render_host(mid, wl["camera"], prm, tf_np, rgba=img_np, stream=stream)
+            ctx.eval_points_host(mid, h_pts.numpy(), out=h_out.numpy(), stream=stream)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            ctx.render_host(mid, wl["camera"], prm, tf_np, rgba=img_np, stream=stream)
+            ctx.eval_points_host(mid, h_pts.numpy(), out=h_out.numpy(), stream=stream)
+        t1 = time.perf_counter()
+        dt = t1 - t0
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([dt], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        line["e2e"] = {"value": world * units_per_step * k2 / dt, "unit": UNIT,
+                       "h2d_bytes_per_step": npts * 12 + wl["tf"].nbytes,
+                       "d2h_bytes_per_step": npts * 16 + H * W * 16, "steps": k2,
+                       "ms_per_step": 1000 * dt / k2}
+
+    # ---- CPU baseline: the oracle on a bounded sample, rank 0 at N = 1 ---
+    if not args.no_cpu_baseline and world == 1:
+        q, t, rs, tr, te = _oracle_sample(wl, 2, 1 << 22)
+        line["cpu_baseline"] = {"value": q / t, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+                                "sample": "every 2nd row of the 1024^2 frame + the first 2^22 of the 2^24 points",
+                                "render_samples_per_s": rs / tr, "eval_points_per_s": (1 << 22) / te}
+
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    from paper_2204_11762_gb300 import workloads
+    wl = workloads.gaussian_sum_workload()
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * mfadvr.h -- C ABI of the GB300 MFA-DVR library (libmfadvr.so).
+ *
+ * MFA-DVR ("MFA-DVR: direct volume rendering of MFA models", Sun, Lenz, Yu,
+ * Peterka) renders a multivariate functional approximation (MFA) directly:
+ * every sample of every ray queries a tensor-product B-spline model for its
+ * value and gradient (Sec. 3.1, Algorithm 1).  The model (Sec. 2.3) is a
+ * lattice of control points with a clamped knot vector and a degree p_d per
+ * axis over the parameter box [0,1]^3; knots are uniform:
+ *   t_0..t_p = 0,  t_{p+j} = j/m (j = 1..m-1),  t_n..t_{n+p} = 1,  m = n - p.
+ *
+ * Conventions shared by every call:
+ *  - Status: every entry point returns an mfadvr_status, 0 on success.  No
+ *    C++ exception crosses this boundary.  All argument checks run before any
+ *    device work, so a call that returns MFADVR_EINVAL has touched nothing.
+ *    A failing call stores a message readable with mfadvr_last_error().
+ *  - Lattice layout: control point (i, j, k) sits at i + n0*(j + n1*k), i.e. u
+ *    varies fastest.
+ *  - Device pointers ("_dev") are owned by the caller, must stay valid until
+ *    the work queued on the given stream has finished, and are never freed by
+ *    the library.  Host pointers are read (or written) before the call
+ *    returns.
+ *  - Streams: "stream" is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  mfadvr_eval_points and mfadvr_render only enqueue work
+ *    on it and return; the *_host variants and mfadvr_load_model synchronise.
+ *  - Threads: a context is used by one host thread at a time (or under an
+ *    external lock).
+ *  - Degrees: 1..MFADVR_MAX_DEGREE and equal on the three axes (the kernels
+ *    are compiled per degree); other degrees return MFADVR_EUNSUPPORTED.
+ *  - Knots: clamped uniform only (mfadvr_model_desc.knots must be NULL).
+ */
+#ifndef MFADVR_H
+#define MFADVR_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MFADVR_API __attribute__((visibility("default")))
+#else
+#define MFADVR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mfadvr_ctx mfadvr_ctx; /* opaque, one per device */
+typedef int32_t mfadvr_status;
+
+#define MFADVR_OK 0
+#define MFADVR_EINVAL (-1)       /* bad argument: NULL, size, non-finite value  */
+#define MFADVR_ENOMEM (-2)       /* HBM budget exceeded or allocation failed     */
+#define MFADVR_ECUDA (-3)        /* a CUDA runtime call failed                   */
+#define MFADVR_ENOTFOUND (-4)    /* no model with that id                        */
+#define MFADVR_ETIMEOUT (-5)     /* a wait ran out of time                       */
+#define MFADVR_EBUSY (-6)        /* resource in use                              */
+#define MFADVR_EUNSUPPORTED (-7) /* valid but not built (degree, knots, dtype)   */
+
+#define MFADVR_MAX_DEGREE 5
+#define MFADVR_MAX_TF_SIZE 4096
+
+/* Storage type of the control points.  F16 and BF16 store P / s with the
+ * per-model scale s = max|P| (s = 1 when all P are 0); evaluation converts to
+ * FP32, accumulates in FP32 and multiplies the result by s. */
+typedef enum { MFADVR_F32 = 0, MFADVR_F16 = 1, MFADVR_BF16 = 2 } mfadvr_dtype;
+
+/* An MFA model (Sec. 2.3): degree, control-point lattice, knots, and the
+ * world box that maps onto the parameter box [0,1]^3. */
+typedef struct {
+    int32_t degree[3];     /* p_d, 1..MFADVR_MAX_DEGREE, equal on all axes     */
+    int32_t ncp[3];        /* n_d >= p_d + 1, n_d <= 2^24                      */
+    float box_min[3];      /* world box; box_max > box_min on every axis       */
+    float box_max[3];
+    const float *ctrl;     /* HOST, n0*n1*n2 finite FP32 values (u fastest)    */
+    const float *knots[3]; /* must be NULL: clamped uniform knots             */
+    mfadvr_dtype storage;  /* storage type in HBM                              */
+} mfadvr_model_desc;
+
+/* Camera in world space (the "Ray Definition" step of Sec. 3.1).  Frame:
+ * forward f = normalize(center - eye), right r = normalize(up x f),
+ * true up u = f x r.  Pixel (x, y), row 0 at the top, has screen offsets
+ * sx = (2(x+1/2)/W - 1) * a and sy = (1 - 2(y+1/2)/H) * b:
+ *  kind 0 (orthographic): a = ortho_height*W/(2H), b = ortho_height/2;
+ *         ray origin eye + sx r + sy u, direction f;
+ *  kind 1 (perspective):  a = tan(fovy/2)*W/H, b = tan(fovy/2);
+ *         ray origin eye, direction normalize(f + sx r + sy u). */
+typedef struct {
+    int32_t kind;
+    float eye[3], center[3], up[3];
+    float fovy_deg;     /* perspective: vertical field of view, (0, 180) */
+    float ortho_height; /* orthographic: world height of the image, > 0  */
+} mfadvr_camera;
+
+/* Render settings (Algorithm 1).  Samples: t_k = t_enter + (k + 1/2) step,
+ * k = 0..N-1, N = floor((t_exit - t_enter)/step), [t_enter, t_exit] the part
+ * of the ray inside the world box (t_enter >= 0). */
+typedef struct {
+    int32_t width, height;  /* > 0                                            */
+    float step;             /* constant sample distance, world units, > 0      */
+    float max_opacity;      /* O_max: stop after a sample makes A > O_max      */
+    float ref_step;         /* opacity correction 1-(1-a)^(step/ref); <=0: off */
+    const float *tf_rgba;   /* tf_size RGBA entries (DEVICE for mfadvr_render,
+                               HOST for mfadvr_render_host)                     */
+    int32_t tf_size;        /* 1..MFADVR_MAX_TF_SIZE                           */
+    float tf_lo, tf_hi;     /* value range of the table; NaN: [min P, max P]   */
+    int32_t shading;        /* 0: value only, 1: gradient shading              */
+    float ka, kd, ks, shininess; /* Blinn-Phong, one headlight: rgb_tf (ka +
+                               kd |n.L|) + ks |n.L|^shininess, clamped to [0,1] */
+} mfadvr_render_params;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the bytes
+ * of resident models (0 = no cap).  *out receives the handle.
+ * EINVAL: out NULL or device < 0.  ECUDA: no such device. */
+MFADVR_API mfadvr_status mfadvr_create(mfadvr_ctx **out, int device, uint64_t hbm_budget_bytes);
+
+/* Free every model and the context.  NULL is accepted (no-op). */
+MFADVR_API mfadvr_status mfadvr_destroy(mfadvr_ctx *ctx);
+
+/* Copy a model into library-owned HBM (Sec. 3: the encoded model is the
+ * renderer's input).  Synchronous: the caller may free desc->ctrl on return.
+ * *model_id receives a handle >= 0.  EINVAL: bad sizes, box, non-finite
+ * control points, knots != NULL.  EUNSUPPORTED: degree outside
+ * 1..MFADVR_MAX_DEGREE or unequal per axis.  ENOMEM: over budget. */
+MFADVR_API mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, int32_t *model_id);
+
+/* Free a model's HBM.  ENOTFOUND: unknown id.  Work already queued that reads
+ * the model must have finished (the call synchronises the device). */
+MFADVR_API mfadvr_status mfadvr_unload_model(mfadvr_ctx *ctx, int32_t model_id);
+
+/* Value range [min P, max P] of the loaded control points (the default TF
+ * domain) and the storage scale s.  Any output pointer may be NULL. */
+MFADVR_API mfadvr_status mfadvr_model_info(mfadvr_ctx *ctx, int32_t model_id, float *pmin, float *pmax,
+                                float *scale, uint64_t *bytes);
+
+/* Value and first derivatives at n parameter points (queryValueMFA and
+ * queryGradientMFA of Algorithm 1, computed together as Sec. 3.1 asks).
+ *  params_dev: n x 3 FP32 (u, v, w); values outside [0,1] (and NaN, read as
+ *              0) are clamped to the box.
+ *  out_dev:    n x 4 FP32 (f, df/du, df/dv, df/dw), parameter space; 16-byte
+ *              aligned.
+ *  spans_dev:  n x 3 int32 knot-span indices s_d in [p, n_d - 1] (t_s <= u <
+ *              t_{s+1}; u = 1 in the last span), or NULL.
+ * n = 0 is a no-op.  EINVAL: NULL buffers with n > 0, n < 0, misalignment. */
+MFADVR_API mfadvr_status mfadvr_eval_points(mfadvr_ctx *ctx, int32_t model_id, const float *params_dev, int64_t n,
+                                 float *out_dev, int32_t *spans_dev, void *stream);
+
+/* As mfadvr_eval_points with HOST buffers: copies params in, evaluates and
+ * copies the results back through library-owned staging memory, then
+ * synchronises the stream. */
+MFADVR_API mfadvr_status mfadvr_eval_points_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_host,
+                                      int64_t n, float *out_host, int32_t *spans_host, void *stream);
+
+/* Ray-cast one image (Algorithm 1): per pixel, march the ray through the
+ * model's world box, query value (+ gradient when shading), map through the
+ * transfer function, shade, composite front to back and stop early once the
+ * cumulative opacity exceeds max_opacity.
+ *  rgba_dev:     height x width x 4 FP32, premultiplied RGBA, row 0 at the
+ *                top, 16-byte aligned; pixels whose ray misses the box are 0.
+ *  nsamples_dev: height x width int32 samples composited per pixel, or NULL.
+ * EINVAL: bad camera/params/buffers. */
+MFADVR_API mfadvr_status mfadvr_render(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_camera *camera,
+                            const mfadvr_render_params *params, float *rgba_dev, int32_t *nsamples_dev,
+                            void *stream);
+
+/* As mfadvr_render with HOST buffers (params->tf_rgba is then a host
+ * pointer): copies the table in, renders, copies the image (and sample
+ * counts, if requested) back and synchronises the stream. */
+MFADVR_API mfadvr_status mfadvr_render_host(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_camera *camera,
+                                 const mfadvr_render_params *params, float *rgba_host,
+                                 int32_t *nsamples_host, void *stream);
+
+/* Static text for a status code. */
+MFADVR_API const char *mfadvr_status_string(mfadvr_status status);
+
+/* Message of the last failing call on ctx ("" if none); valid until the next
+ * call on ctx.  NULL ctx gives the message of the last failing create. */
+MFADVR_API const char *mfadvr_last_error(mfadvr_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFADVR_H */

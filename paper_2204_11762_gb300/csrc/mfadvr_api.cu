@@ -1,0 +1,545 @@
+// C ABI of libmfadvr.so: context, resident model store, argument checks and
+// kernel dispatch.  See include/mfadvr.h for the contract of each call.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mfa_internal.h"
+#include "mfadvr.h"
+
+using namespace mfadvr;
+
+namespace {
+
+struct Model {
+    void *d_cp = nullptr;
+    uint64_t bytes = 0;
+    int p = 0;
+    int n[3] = {0, 0, 0};
+    int dtype = MFADVR_F32;
+    float scale = 1.0f;
+    float pmin = 0.0f, pmax = 0.0f, pabs = 0.0f;
+    float box_min[3] = {0, 0, 0}, box_max[3] = {1, 1, 1};
+};
+
+// Device buffer owned by the context, grown on demand (host-buffer calls).
+struct Staging {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t need)
+    {
+        if (need <= bytes) return cudaSuccess;
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&ptr, need);
+        if (e == cudaSuccess) bytes = need;
+        return e;
+    }
+    void release()
+    {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+    }
+};
+
+std::mutex g_create_mu;
+std::string g_create_err;
+
+}  // namespace
+
+struct mfadvr_ctx {
+    int device = 0;
+    uint64_t budget = 0, used = 0;
+    std::map<int32_t, Model> models;
+    int32_t next_id = 0;
+    std::string err;
+    Staging st_in, st_out, st_aux;
+};
+
+namespace {
+
+mfadvr_status fail(mfadvr_ctx *ctx, mfadvr_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    else {
+        std::lock_guard<std::mutex> g(g_create_mu);
+        g_create_err = buf;
+    }
+    return st;
+}
+
+mfadvr_status cuda_fail(mfadvr_ctx *ctx, cudaError_t e, const char *what)
+{
+    return fail(ctx, MFADVR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Makes ctx->device current for the duration of a call and restores the
+// caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev)
+    {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// True for device or managed memory; host pointers (registered or not) and
+// foreign pointers are refused before any launch reads them.
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+bool finite3(const float v[3]) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+ModelView view_of(const Model &m)
+{
+    ModelView v;
+    v.cp = m.d_cp;
+    v.p = m.p;
+    v.dtype = m.dtype;
+    v.scale = m.scale;
+    for (int a = 0; a < 3; ++a) {
+        v.n[a] = m.n[a];
+        v.m[a] = m.n[a] - m.p;
+    }
+    return v;
+}
+
+size_t dtype_size(int dtype) { return dtype == MFADVR_F32 ? 4 : 2; }
+
+mfadvr_status find_model(mfadvr_ctx *ctx, int32_t id, Model **out)
+{
+    auto it = ctx->models.find(id);
+    if (it == ctx->models.end()) return fail(ctx, MFADVR_ENOTFOUND, "no model with id %d", id);
+    *out = &it->second;
+    return MFADVR_OK;
+}
+
+// Camera frame and per-pixel mapping in double, rounded once to FP32.
+mfadvr_status make_setup(mfadvr_ctx *ctx, const Model &m, const mfadvr_camera *cam,
+                         const mfadvr_render_params *rp, RenderSetup *rs)
+{
+    if (!cam || !rp) return fail(ctx, MFADVR_EINVAL, "camera and params must not be NULL");
+    if (cam->kind != 0 && cam->kind != 1) return fail(ctx, MFADVR_EINVAL, "camera kind must be 0 or 1");
+    if (!finite3(cam->eye) || !finite3(cam->center) || !finite3(cam->up))
+        return fail(ctx, MFADVR_EINVAL, "camera vectors must be finite");
+    if (cam->kind == 1 && !(cam->fovy_deg > 0.0f && cam->fovy_deg < 180.0f))
+        return fail(ctx, MFADVR_EINVAL, "fovy_deg must be in (0, 180)");
+    if (cam->kind == 0 && !(cam->ortho_height > 0.0f && std::isfinite(cam->ortho_height)))
+        return fail(ctx, MFADVR_EINVAL, "ortho_height must be > 0");
+    if (rp->width <= 0 || rp->height <= 0 || rp->width > 65536 || rp->height > 65536)
+        return fail(ctx, MFADVR_EINVAL, "image size must be in 1..65536");
+    if (!(rp->step > 0.0f) || !std::isfinite(rp->step)) return fail(ctx, MFADVR_EINVAL, "step must be > 0");
+    {
+        // Bound the samples on one ray (the chord of the box is at most its
+        // diagonal) so that no launch can run unboundedly long.
+        double diag2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double e = static_cast<double>(m.box_max[a]) - m.box_min[a];
+            diag2 += e * e;
+        }
+        if (std::sqrt(diag2) / rp->step > static_cast<double>(1 << 24))
+            return fail(ctx, MFADVR_EINVAL, "step gives more than 2^24 samples per ray");
+    }
+    if (!std::isfinite(rp->max_opacity)) return fail(ctx, MFADVR_EINVAL, "max_opacity must be finite");
+    if (!std::isfinite(rp->ref_step)) return fail(ctx, MFADVR_EINVAL, "ref_step must be finite");
+    if (!rp->tf_rgba || rp->tf_size < 1 || rp->tf_size > MFADVR_MAX_TF_SIZE)
+        return fail(ctx, MFADVR_EINVAL, "tf_rgba must be set and tf_size in 1..%d", MFADVR_MAX_TF_SIZE);
+    if (rp->shading != 0 && rp->shading != 1) return fail(ctx, MFADVR_EINVAL, "shading must be 0 or 1");
+    if (!std::isfinite(rp->ka) || !std::isfinite(rp->kd) || !std::isfinite(rp->ks) ||
+        !std::isfinite(rp->shininess) || rp->shininess < 0.0f)
+        return fail(ctx, MFADVR_EINVAL, "ka, kd, ks must be finite and shininess >= 0");
+    if (std::isinf(rp->tf_lo) || std::isinf(rp->tf_hi))
+        return fail(ctx, MFADVR_EINVAL, "tf_lo/tf_hi must be finite or NaN");
+
+    double f[3], up[3], r[3], u[3];
+    for (int a = 0; a < 3; ++a) {
+        f[a] = static_cast<double>(cam->center[a]) - cam->eye[a];
+        up[a] = cam->up[a];
+    }
+    double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    if (!(fl > 0.0)) return fail(ctx, MFADVR_EINVAL, "camera eye and center coincide");
+    for (double &x : f) x /= fl;
+    r[0] = up[1] * f[2] - up[2] * f[1];
+    r[1] = up[2] * f[0] - up[0] * f[2];
+    r[2] = up[0] * f[1] - up[1] * f[0];
+    double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (!(rl > 1e-12)) return fail(ctx, MFADVR_EINVAL, "camera up is parallel to the view direction");
+    for (double &x : r) x /= rl;
+    u[0] = f[1] * r[2] - f[2] * r[1];
+    u[1] = f[2] * r[0] - f[0] * r[2];
+    u[2] = f[0] * r[1] - f[1] * r[0];
+
+    const double W = rp->width, H = rp->height;
+    double a, b;
+    if (cam->kind == 0) {
+        a = cam->ortho_height * W / (2.0 * H);
+        b = cam->ortho_height / 2.0;
+    } else {
+        const double th = std::tan(cam->fovy_deg * (M_PI / 180.0) * 0.5);
+        a = th * W / H;
+        b = th;
+    }
+    std::memset(rs, 0, sizeof *rs);
+    rs->width = rp->width;
+    rs->height = rp->height;
+    rs->kind = cam->kind;
+    for (int i = 0; i < 3; ++i) {
+        rs->eye[i] = cam->eye[i];
+        rs->fwd[i] = static_cast<float>(f[i]);
+        rs->right[i] = static_cast<float>(r[i]);
+        rs->up[i] = static_cast<float>(u[i]);
+        rs->box_min[i] = m.box_min[i];
+        rs->box_max[i] = m.box_max[i];
+        const double ext = static_cast<double>(m.box_max[i]) - m.box_min[i];
+        rs->inv_ext[i] = static_cast<float>(1.0 / ext);
+        rs->grad_scale[i] = static_cast<float>(static_cast<double>(m.n[i] - m.p) * m.scale / ext);
+    }
+    rs->sx_scale = static_cast<float>(2.0 * a / W);
+    rs->sx_off = static_cast<float>(-a);
+    rs->sy_scale = static_cast<float>(-2.0 * b / H);
+    rs->sy_off = static_cast<float>(b);
+    rs->step = rp->step;
+    rs->max_opacity = rp->max_opacity;
+    rs->correct_opacity = (rp->ref_step > 0.0f && rp->ref_step != rp->step) ? 1 : 0;
+    rs->opacity_ratio = rs->correct_opacity ? static_cast<float>(static_cast<double>(rp->step) / rp->ref_step) : 1.0f;
+    rs->tf_size = rp->tf_size;
+    const double lo = std::isnan(rp->tf_lo) ? m.pmin : rp->tf_lo;
+    const double hi = std::isnan(rp->tf_hi) ? m.pmax : rp->tf_hi;
+    rs->tf_lo = static_cast<float>(lo);
+    rs->tf_inv_range = hi > lo ? static_cast<float>(1.0 / (hi - lo)) : 0.0f;
+    rs->shading = rp->shading;
+    rs->ka = rp->ka;
+    rs->kd = rp->kd;
+    rs->ks = rp->ks;
+    rs->shininess = rp->shininess;
+    const double th = 1e-20 * m.pabs;
+    rs->gthresh2 = static_cast<float>(th * th);
+    return MFADVR_OK;
+}
+
+// A one-entry table is widened to two equal entries so the kernel's
+// interpolation never reads past the end.
+mfadvr_status stage_tf(mfadvr_ctx *ctx, const float *tf, int size, bool tf_on_host, RenderSetup *rs,
+                       cudaStream_t stream)
+{
+    if (size >= 2 && !tf_on_host) {
+        if (reinterpret_cast<uintptr_t>(tf) % 16 != 0)
+            return fail(ctx, MFADVR_EINVAL, "tf_rgba must be 16-byte aligned");
+        rs->tf = reinterpret_cast<const float4 *>(tf);
+        return MFADVR_OK;
+    }
+    const int n = size >= 2 ? size : 2;
+    cudaError_t e = ctx->st_aux.reserve(sizeof(float4) * n);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "staging allocation");
+    float4 *dst = static_cast<float4 *>(ctx->st_aux.ptr);
+    const cudaMemcpyKind kind = tf_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    e = cudaMemcpyAsync(dst, tf, sizeof(float4) * size, kind, stream);
+    if (e == cudaSuccess && size == 1) e = cudaMemcpyAsync(dst + 1, tf, sizeof(float4), kind, stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "transfer-function copy");
+    rs->tf = dst;
+    rs->tf_size = n;
+    return MFADVR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mfadvr_status mfadvr_create(mfadvr_ctx **out, int device, uint64_t hbm_budget_bytes)
+{
+    if (!out) return fail(nullptr, MFADVR_EINVAL, "out must not be NULL");
+    *out = nullptr;
+    if (device < 0) return fail(nullptr, MFADVR_EINVAL, "device must be >= 0");
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) return fail(nullptr, MFADVR_ECUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+    if (device >= count) return fail(nullptr, MFADVR_ECUDA, "device %d not present (%d devices)", device, count);
+    mfadvr_ctx *ctx = new (std::nothrow) mfadvr_ctx();
+    if (!ctx) return fail(nullptr, MFADVR_ENOMEM, "out of host memory");
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes;
+    *out = ctx;
+    return MFADVR_OK;
+}
+
+mfadvr_status mfadvr_destroy(mfadvr_ctx *ctx)
+{
+    if (!ctx) return MFADVR_OK;
+    {
+        DeviceGuard g(ctx->device);
+        cudaDeviceSynchronize();
+        for (auto &kv : ctx->models)
+            if (kv.second.d_cp) cudaFree(kv.second.d_cp);
+        ctx->st_in.release();
+        ctx->st_out.release();
+        ctx->st_aux.release();
+    }
+    delete ctx;
+    return MFADVR_OK;
+}
+
+mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, int32_t *model_id)
+{
+    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
+    if (!desc || !model_id) return fail(ctx, MFADVR_EINVAL, "desc and model_id must not be NULL");
+    if (!desc->ctrl) return fail(ctx, MFADVR_EINVAL, "desc->ctrl must not be NULL");
+    for (int a = 0; a < 3; ++a)
+        if (desc->knots[a]) return fail(ctx, MFADVR_EUNSUPPORTED, "only clamped uniform knots (knots = NULL)");
+    if (desc->storage != MFADVR_F32 && desc->storage != MFADVR_F16 && desc->storage != MFADVR_BF16)
+        return fail(ctx, MFADVR_EINVAL, "unknown storage type %d", static_cast<int>(desc->storage));
+    for (int a = 0; a < 3; ++a) {
+        if (desc->degree[a] < 1) return fail(ctx, MFADVR_EINVAL, "degree must be >= 1");
+        if (desc->ncp[a] < desc->degree[a] + 1 || desc->ncp[a] > (1 << 24))
+            return fail(ctx, MFADVR_EINVAL, "ncp[%d] = %d must be in degree+1..2^24", a, desc->ncp[a]);
+        if (!std::isfinite(desc->box_min[a]) || !std::isfinite(desc->box_max[a]) ||
+            !(desc->box_max[a] > desc->box_min[a]))
+            return fail(ctx, MFADVR_EINVAL, "box_max must exceed box_min on every axis");
+    }
+    if (desc->degree[0] > MFADVR_MAX_DEGREE || desc->degree[1] > MFADVR_MAX_DEGREE ||
+        desc->degree[2] > MFADVR_MAX_DEGREE)
+        return fail(ctx, MFADVR_EUNSUPPORTED, "degree above %d", MFADVR_MAX_DEGREE);
+    if (desc->degree[0] != desc->degree[1] || desc->degree[0] != desc->degree[2])
+        return fail(ctx, MFADVR_EUNSUPPORTED, "degrees must be equal on the three axes");
+
+    const uint64_t count = static_cast<uint64_t>(desc->ncp[0]) * desc->ncp[1] * desc->ncp[2];
+    float pmin = INFINITY, pmax = -INFINITY, pabs = 0.0f;
+    for (uint64_t i = 0; i < count; ++i) {
+        const float v = desc->ctrl[i];
+        if (!std::isfinite(v)) return fail(ctx, MFADVR_EINVAL, "control point %llu is not finite",
+                                           static_cast<unsigned long long>(i));
+        pmin = v < pmin ? v : pmin;
+        pmax = v > pmax ? v : pmax;
+        pabs = std::fabs(v) > pabs ? std::fabs(v) : pabs;
+    }
+    Model m;
+    m.p = desc->degree[0];
+    m.dtype = desc->storage;
+    for (int a = 0; a < 3; ++a) {
+        m.n[a] = desc->ncp[a];
+        m.box_min[a] = desc->box_min[a];
+        m.box_max[a] = desc->box_max[a];
+    }
+    m.pmin = pmin;
+    m.pmax = pmax;
+    m.pabs = pabs;
+    m.scale = (desc->storage == MFADVR_F32 || pabs == 0.0f) ? 1.0f : pabs;
+    m.bytes = count * dtype_size(m.dtype);
+    if (ctx->budget && ctx->used + m.bytes > ctx->budget)
+        return fail(ctx, MFADVR_ENOMEM, "model of %llu bytes exceeds the HBM budget (%llu of %llu used)",
+                    static_cast<unsigned long long>(m.bytes), static_cast<unsigned long long>(ctx->used),
+                    static_cast<unsigned long long>(ctx->budget));
+
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
+    cudaError_t e = cudaMalloc(&m.d_cp, m.bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, MFADVR_ENOMEM, "cudaMalloc(%llu): %s", static_cast<unsigned long long>(m.bytes),
+                    cudaGetErrorString(e));
+    }
+    if (m.dtype == MFADVR_F32) {
+        e = cudaMemcpy(m.d_cp, desc->ctrl, m.bytes, cudaMemcpyHostToDevice);
+    } else {
+        void *tmp = nullptr;
+        e = cudaMalloc(&tmp, count * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemcpy(tmp, desc->ctrl, count * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = launch_quantize(static_cast<const float *>(tmp), m.d_cp, static_cast<int64_t>(count), m.dtype,
+                                1.0f / m.scale, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (tmp) cudaFree(tmp);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(m.d_cp);
+        return cuda_fail(ctx, e, "model upload");
+    }
+    const int32_t id = ctx->next_id++;
+    ctx->models[id] = m;
+    ctx->used += m.bytes;
+    *model_id = id;
+    return MFADVR_OK;
+}
+
+mfadvr_status mfadvr_unload_model(mfadvr_ctx *ctx, int32_t model_id)
+{
+    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
+    Model *m = nullptr;
+    if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(m->d_cp);
+    ctx->used -= m->bytes;
+    ctx->models.erase(model_id);
+    return MFADVR_OK;
+}
+
+mfadvr_status mfadvr_model_info(mfadvr_ctx *ctx, int32_t model_id, float *pmin, float *pmax, float *scale,
+                                uint64_t *bytes)
+{
+    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
+    Model *m = nullptr;
+    if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
+    if (pmin) *pmin = m->pmin;
+    if (pmax) *pmax = m->pmax;
+    if (scale) *scale = m->scale;
+    if (bytes) *bytes = m->bytes;
+    return MFADVR_OK;
+}
+
+mfadvr_status mfadvr_eval_points(mfadvr_ctx *ctx, int32_t model_id, const float *params_dev, int64_t n,
+                                 float *out_dev, int32_t *spans_dev, void *stream)
+{
+    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
+    Model *m = nullptr;
+    if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
+    if (n < 0) return fail(ctx, MFADVR_EINVAL, "n must be >= 0");
+    if (n == 0) return MFADVR_OK;
+    if (!params_dev || !out_dev) return fail(ctx, MFADVR_EINVAL, "params and out must not be NULL");
+    if (reinterpret_cast<uintptr_t>(out_dev) % 16 != 0 || reinterpret_cast<uintptr_t>(params_dev) % 4 != 0 ||
+        reinterpret_cast<uintptr_t>(spans_dev) % 4 != 0)
+        return fail(ctx, MFADVR_EINVAL, "out must be 16-byte aligned, params and spans 4-byte aligned");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
+    if (!is_device_ptr(params_dev) || !is_device_ptr(out_dev) || (spans_dev && !is_device_ptr(spans_dev)))
+        return fail(ctx, MFADVR_EINVAL, "params, out and spans must be device pointers");
+    cudaError_t e = launch_eval_points(view_of(*m), params_dev, n, reinterpret_cast<float4 *>(out_dev), spans_dev,
+                                       static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "eval_points launch");
+    return MFADVR_OK;
+}
+
+mfadvr_status mfadvr_eval_points_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_host, int64_t n,
+                                      float *out_host, int32_t *spans_host, void *stream)
+{
+    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
+    Model *m = nullptr;
+    if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
+    if (n < 0) return fail(ctx, MFADVR_EINVAL, "n must be >= 0");
+    if (n == 0) return MFADVR_OK;
+    if (!params_host || !out_host) return fail(ctx, MFADVR_EINVAL, "params and out must not be NULL");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t in_b = static_cast<size_t>(n) * 12, out_b = static_cast<size_t>(n) * 16;
+    const size_t sp_b = spans_host ? static_cast<size_t>(n) * 12 : 0;
+    cudaError_t e = ctx->st_in.reserve(in_b);
+    if (e == cudaSuccess) e = ctx->st_out.reserve(out_b + sp_b);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "staging allocation");
+    float *d_in = static_cast<float *>(ctx->st_in.ptr);
+    float4 *d_out = static_cast<float4 *>(ctx->st_out.ptr);
+    int32_t *d_sp = spans_host ? reinterpret_cast<int32_t *>(static_cast<char *>(ctx->st_out.ptr) + out_b) : nullptr;
+    e = cudaMemcpyAsync(d_in, params_host, in_b, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_eval_points(view_of(*m), d_in, n, d_out, d_sp, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, d_out, out_b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && d_sp) e = cudaMemcpyAsync(spans_host, d_sp, sp_b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "eval_points_host");
+    return MFADVR_OK;
+}
+
+mfadvr_status mfadvr_render(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_camera *camera,
+                            const mfadvr_render_params *params, float *rgba_dev, int32_t *nsamples_dev, void *stream)
+{
+    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
+    Model *m = nullptr;
+    if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
+    RenderSetup rs;
+    if (mfadvr_status st = make_setup(ctx, *m, camera, params, &rs)) return st;
+    if (!rgba_dev || reinterpret_cast<uintptr_t>(rgba_dev) % 16 != 0)
+        return fail(ctx, MFADVR_EINVAL, "rgba must be a 16-byte aligned device pointer");
+    if (reinterpret_cast<uintptr_t>(nsamples_dev) % 4 != 0)
+        return fail(ctx, MFADVR_EINVAL, "nsamples must be 4-byte aligned");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
+    if (!is_device_ptr(rgba_dev) || !is_device_ptr(params->tf_rgba) || (nsamples_dev && !is_device_ptr(nsamples_dev)))
+        return fail(ctx, MFADVR_EINVAL, "rgba, tf_rgba and nsamples must be device pointers");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (mfadvr_status st = stage_tf(ctx, params->tf_rgba, params->tf_size, false, &rs, s)) return st;
+    rs.out = reinterpret_cast<float4 *>(rgba_dev);
+    rs.nsamples = nsamples_dev;
+    cudaError_t e = launch_render(view_of(*m), rs, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "render launch");
+    return MFADVR_OK;
+}
+
+mfadvr_status mfadvr_render_host(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_camera *camera,
+                                 const mfadvr_render_params *params, float *rgba_host, int32_t *nsamples_host,
+                                 void *stream)
+{
+    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
+    Model *m = nullptr;
+    if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
+    RenderSetup rs;
+    if (mfadvr_status st = make_setup(ctx, *m, camera, params, &rs)) return st;
+    if (!rgba_host) return fail(ctx, MFADVR_EINVAL, "rgba must not be NULL");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (mfadvr_status st = stage_tf(ctx, params->tf_rgba, params->tf_size, true, &rs, s)) return st;
+    const size_t npix = static_cast<size_t>(params->width) * params->height;
+    const size_t img_b = npix * 16, ns_b = nsamples_host ? npix * 4 : 0;
+    cudaError_t e = ctx->st_out.reserve(img_b + ns_b);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "staging allocation");
+    rs.out = static_cast<float4 *>(ctx->st_out.ptr);
+    rs.nsamples = nsamples_host ? reinterpret_cast<int32_t *>(static_cast<char *>(ctx->st_out.ptr) + img_b) : nullptr;
+    e = launch_render(view_of(*m), rs, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rgba_host, rs.out, img_b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && nsamples_host)
+        e = cudaMemcpyAsync(nsamples_host, rs.nsamples, ns_b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "render_host");
+    return MFADVR_OK;
+}
+
+const char *mfadvr_status_string(mfadvr_status status)
+{
+    switch (status) {
+    case MFADVR_OK: return "ok";
+    case MFADVR_EINVAL: return "invalid argument";
+    case MFADVR_ENOMEM: return "out of memory or over the HBM budget";
+    case MFADVR_ECUDA: return "CUDA error";
+    case MFADVR_ENOTFOUND: return "model not found";
+    case MFADVR_ETIMEOUT: return "timed out";
+    case MFADVR_EBUSY: return "busy";
+    case MFADVR_EUNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+    }
+}
+
+const char *mfadvr_last_error(mfadvr_ctx *ctx)
+{
+    if (!ctx) {
+        std::lock_guard<std::mutex> g(g_create_mu);
+        return g_create_err.c_str();
+    }
+    return ctx->err.c_str();
+}
+
+}  // extern "C"

@@ -177,10 +177,17 @@ def uniform_points(rng, count):
 # Named workloads
 # --------------------------------------------------------------------------
 
+# The transfer-function opacity of every named workload is the opacity of a
+# slab 1/16 of the box thick; samples take alpha_s = 1 - (1 - alpha)^(step /
+# REF_STEP).  Applied per sample without the correction, alpha ~ U(0, 0.5)
+# at step 1/1024 saturates every ray within a few dozen samples.
+REF_STEP = 1.0 / 16.0
+
 def small_ml_workload():
     """Degree 3, 32^3 lattice of Marschner-Lobb (Eq. 2) at the Greville
     abscissae plus N(0, 0.01) noise; 128^2 orthographic view along +z, step
-    1/256, 256-entry TF from 4 seeded nodes, shading on, O_max 0.99."""
+    1/256, 256-entry TF from 4 seeded nodes, shading on, O_max 0.99,
+    TF opacity per REF_STEP."""
     rng = np.random.default_rng(seed_for(1))
     p, n = 3, (32, 32, 32)
     ctrl = field_lattice(marschner_lobb, n, p) + rng.normal(0.0, 0.01, size=(n[2], n[1], n[0]))
@@ -188,7 +195,7 @@ def small_ml_workload():
     return {"name": "ml32_p3_ortho128", "degree": p, "ctrl": ctrl.astype(np.float32), "tf": tf,
             "camera": axis_ortho_camera(),
             "params": {"width": 128, "height": 128, "step": 1.0 / 256, "max_opacity": 0.99,
-                       "shading": 1}}
+                       "ref_step": REF_STEP, "shading": 1}}
 
 
 def gaussian_sum_workload(n_eval_points=1 << 24, with_points=True):
@@ -203,7 +210,7 @@ def gaussian_sum_workload(n_eval_points=1 << 24, with_points=True):
     pts = uniform_points(rng, n_eval_points) if with_points else None
     return {"name": "gauss20_128_p3_persp1024", "degree": p, "ctrl": ctrl, "tf": tf, "camera": cam,
             "params": {"width": 1024, "height": 1024, "step": 1.0 / 1024, "max_opacity": 0.99,
-                       "shading": 1},
+                       "ref_step": REF_STEP, "shading": 1},
             "points": pts}
 
 
@@ -217,4 +224,4 @@ def value_noise_workload(n=512):
     cam = sphere_camera(rng)
     return {"name": f"noise{n}_p4_persp3840x2160", "degree": p, "ctrl": ctrl, "tf": tf, "camera": cam,
             "params": {"width": 3840, "height": 2160, "step": 1.0 / 2048, "max_opacity": 0.99,
-                       "shading": 1}}
+                       "ref_step": REF_STEP, "shading": 1}}

@@ -1,0 +1,166 @@
+"""GPU parity of mfadvr_eval_points against the FP64 oracle, through the C ABI.
+
+Spans must match exactly; values within 1e-5 and gradients within 1e-4 of
+the model scale (see tests/_parity.py)."""
+import numpy as np
+import pytest
+
+from _parity import assert_eval_parity, dequantize
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ctx(torch_cuda):
+    from paper_2204_11762_gb300 import mfadvr
+    c = mfadvr.Context(0)
+    yield c
+    c.close()
+
+
+def _edge_points(n, p):
+    """Parameters at, just above and just below every knot (FP32), the box
+    corners, and points outside the box."""
+    pts = []
+    for d in range(3):
+        m = n[d] - p
+        for j in range(m + 1):
+            k = np.float32(j / m)
+            for u in (k, np.nextafter(k, np.float32(2)), np.nextafter(k, np.float32(-1))):
+                q = np.full(3, 0.37, dtype=np.float32)
+                q[d] = u
+                pts.append(q)
+    pts += [np.zeros(3), np.ones(3), [-0.25, 1.5, 0.5], [2.0, -1.0, 1.0], [0.5, 0.5, 1.0]]
+    return np.asarray(pts, dtype=np.float32)
+
+
+def _run(ctx, torch, mid, pts):
+    dev = torch.device("cuda:0")
+    n = pts.shape[0]
+    d_pts = torch.from_numpy(np.ascontiguousarray(pts)).to(dev)
+    d_out = torch.full((max(n, 1), 4), float("nan"), dtype=torch.float32, device=dev)
+    d_sp = torch.full((max(n, 1), 3), -1, dtype=torch.int32, device=dev)
+    ctx.eval_points(mid, d_pts, n, d_out, d_sp)
+    torch.cuda.synchronize()
+    return d_out.cpu().numpy()[:n], d_sp.cpu().numpy()[:n]
+
+
+@pytest.mark.parametrize("p,n", [(1, (2, 3, 2)), (1, (17, 9, 33)), (2, (3, 4, 5)), (2, (40, 21, 13)),
+                                 (3, (4, 4, 4)), (3, (5, 9, 6)), (3, (32, 33, 34)), (4, (5, 6, 7)),
+                                 (4, (29, 18, 25)), (5, (6, 6, 6)), (5, (9, 11, 10)), (5, (31, 24, 27))])
+def test_eval_parity_f32(ctx, torch_cuda, orc, p, n):
+    rng = np.random.default_rng(100 + p * 7 + n[0])
+    ctrl = rng.normal(size=(n[2], n[1], n[0])).astype(np.float32)
+    pts = np.concatenate([rng.uniform(0, 1, size=(3001, 3)).astype(np.float32), _edge_points(n, p)])
+    mid = ctx.load_model(ctrl, p)
+    got, sp = _run(ctx, torch_cuda, mid, pts)
+    ref, ref_sp = orc.eval_points(ctrl, p, pts)
+    assert_eval_parity(got, ref, ctrl, n, p, sp, ref_sp)
+    ctx.unload_model(mid)
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("p", [2, 3, 4, 5])
+def test_eval_parity_16bit_storage(ctx, torch_cuda, orc, storage, p):
+    """16-bit storage with a per-model scale, FP32 accumulation: parity with
+    the oracle evaluated on the lattice the model actually stores."""
+    rng = np.random.default_rng(300 + p)
+    n = (23, 17, 29)
+    ctrl = (rng.normal(size=(n[2], n[1], n[0])) * 3.7).astype(np.float32)
+    pts = rng.uniform(0, 1, size=(4000, 3)).astype(np.float32)
+    mid = ctx.load_model(ctrl, p, storage=storage)
+    info = ctx.model_info(mid)
+    assert info["scale"] == pytest.approx(float(np.abs(ctrl).max()))
+    assert info["bytes"] == ctrl.size * 2
+    got, sp = _run(ctx, torch_cuda, mid, pts)
+    deq = dequantize(ctrl, storage)
+    ref, ref_sp = orc.eval_points(deq, p, pts)
+    assert_eval_parity(got, ref, deq, n, p, sp, ref_sp)
+    ctx.unload_model(mid)
+
+
+def test_eval_empty_and_tiny(ctx, torch_cuda, orc):
+    rng = np.random.default_rng(5)
+    ctrl = rng.normal(size=(4, 4, 4)).astype(np.float32)
+    mid = ctx.load_model(ctrl, 3)
+    got, sp = _run(ctx, torch_cuda, mid, np.zeros((0, 3), dtype=np.float32))
+    assert got.shape == (0, 4)
+    pts = np.array([[0.5, 0.25, 0.75]], dtype=np.float32)
+    got, sp = _run(ctx, torch_cuda, mid, pts)
+    ref, ref_sp = orc.eval_points(ctrl, 3, pts)
+    assert_eval_parity(got, ref, ctrl, (4, 4, 4), 3, sp, ref_sp)
+    ctx.unload_model(mid)
+
+
+def test_eval_host_buffers_match_device(ctx, torch_cuda, orc):
+    rng = np.random.default_rng(9)
+    n = (20, 21, 22)
+    ctrl = rng.normal(size=(n[2], n[1], n[0])).astype(np.float32)
+    pts = rng.uniform(0, 1, size=(10007, 3)).astype(np.float32)
+    mid = ctx.load_model(ctrl, 3)
+    sp = np.empty((pts.shape[0], 3), dtype=np.int32)
+    out = ctx.eval_points_host(mid, pts, spans=sp)
+    dev_out, dev_sp = _run(ctx, torch_cuda, mid, pts)
+    np.testing.assert_array_equal(out, dev_out)
+    np.testing.assert_array_equal(sp, dev_sp)
+    ctx.unload_model(mid)
+
+
+def test_eval_full_size_gaussian_workload(ctx, torch_cuda, orc):
+    """The 128^3 degree-3 Gaussian-sum model with 2^24 uniform points, in
+    one launch as the benchmark times it; 20000 sampled outputs against the
+    oracle, every span checked against the exact floor rule."""
+    from paper_2204_11762_gb300 import workloads
+    torch = torch_cuda
+    wl = workloads.gaussian_sum_workload()
+    ctrl, p, pts = wl["ctrl"], wl["degree"], wl["points"]
+    n = ctrl.shape[::-1]
+    mid = ctx.load_model(ctrl, p)
+    got, sp = _run(ctx, torch, mid, pts)
+    idx = np.random.default_rng(0).choice(pts.shape[0], 20000, replace=False)
+    ref, ref_sp = orc.eval_points(ctrl, p, pts[idx])
+    assert_eval_parity(got[idx], ref, ctrl, n, p, sp[idx], ref_sp)
+    # every span: exact floor(u*m) (property that holds at any size)
+    m = np.array(n) - p
+    exact = np.floor(pts.astype(np.float64) * m).astype(np.int64)
+    exact = np.clip(exact, 0, m - 1) + p
+    assert np.array_equal(sp, exact)
+    ctx.unload_model(mid)
+
+
+def test_invalid_arguments(ctx, torch_cuda):
+    from paper_2204_11762_gb300 import mfadvr
+    rng = np.random.default_rng(1)
+    with pytest.raises(mfadvr.MfadvrError) as e:
+        ctx.load_model(rng.normal(size=(3, 3, 3)).astype(np.float32), 3)
+    assert e.value.status == mfadvr.EINVAL
+    with pytest.raises(mfadvr.MfadvrError) as e:
+        ctx.load_model(rng.normal(size=(8, 8, 8)).astype(np.float32), 6)
+    assert e.value.status == mfadvr.EUNSUPPORTED
+    bad = rng.normal(size=(5, 5, 5)).astype(np.float32)
+    bad[2, 2, 2] = np.nan
+    with pytest.raises(mfadvr.MfadvrError) as e:
+        ctx.load_model(bad, 2)
+    assert e.value.status == mfadvr.EINVAL
+    with pytest.raises(mfadvr.MfadvrError) as e:
+        ctx.eval_points(12345, 0, 1, 0)
+    assert e.value.status == mfadvr.ENOTFOUND
+
+
+def test_hbm_budget(torch_cuda):
+    from paper_2204_11762_gb300 import mfadvr
+    with mfadvr.Context(0, hbm_budget_bytes=40_000) as c:
+        a = c.load_model(np.zeros((20, 20, 20), dtype=np.float32), 3)  # 32000 B
+        with pytest.raises(mfadvr.MfadvrError) as e:
+            c.load_model(np.zeros((20, 20, 20), dtype=np.float32), 3)
+        assert e.value.status == mfadvr.ENOMEM
+        c.unload_model(a)
+        c.load_model(np.zeros((20, 20, 20), dtype=np.float32), 3)

@@ -1,0 +1,184 @@
+"""GPU parity of mfadvr_render (Algorithm 1) against the FP64 oracle, through
+the C ABI.  Pixels within 2e-3 per channel; where the oracle flags a tied
+decision (sample count or early termination within rounding of its
+threshold) either branch is accepted; sample counts must match one of the
+two branches."""
+import numpy as np
+import pytest
+
+from _parity import assert_render_parity, dequantize
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ctx(torch_cuda):
+    from paper_2204_11762_gb300 import mfadvr
+    c = mfadvr.Context(0)
+    yield c
+    c.close()
+
+
+def _render(ctx, torch, mid, cam, prm, tf):
+    dev = torch.device("cuda:0")
+    W, H = prm["width"], prm["height"]
+    d_tf = torch.from_numpy(np.ascontiguousarray(tf, dtype=np.float32)).to(dev)
+    d_img = torch.full((H, W, 4), float("nan"), dtype=torch.float32, device=dev)
+    d_ns = torch.full((H, W), -1, dtype=torch.int32, device=dev)
+    ctx.render(mid, cam, prm, d_tf, tf.shape[0], d_img, d_ns)
+    torch.cuda.synchronize()
+    return d_img.cpu().numpy(), d_ns.cpu().numpy()
+
+
+def _persp(eye, fovy=50.0, up=(0, 0, 1)):
+    return {"kind": 1, "eye": eye, "center": (0.5, 0.5, 0.5), "up": up, "fovy_deg": fovy}
+
+
+def test_small_marschner_lobb_workload(ctx, torch_cuda, orc):
+    """Degree 3, 32^3 Marschner-Lobb lattice, 128^2 orthographic, step 1/256."""
+    from paper_2204_11762_gb300 import workloads
+    wl = workloads.small_ml_workload()
+    mid = ctx.load_model(wl["ctrl"], wl["degree"])
+    img, ns = _render(ctx, torch_cuda, mid, wl["camera"], wl["params"], wl["tf"])
+    ref = orc.render(wl["ctrl"], wl["degree"], wl["camera"], dict(wl["params"], tf=wl["tf"]))
+    assert_render_parity(img, ns, ref)
+    assert ns.sum() > 0
+    ctx.unload_model(mid)
+
+
+@pytest.mark.parametrize("p,n,W,H,shading", [(1, 4, 4, 4, 0), (2, 5, 8, 8, 1), (3, 6, 8, 8, 1), (3, 4, 5, 7, 0),
+                                             (4, 7, 9, 6, 1), (5, 8, 6, 9, 1)])
+def test_tiny_images(ctx, torch_cuda, orc, p, n, W, H, shading):
+    from paper_2204_11762_gb300 import workloads
+    rng = np.random.default_rng(200 + p * 3 + n)
+    ctrl = rng.uniform(0, 1, size=(n, n + 1, n + 2)).astype(np.float32)
+    tf = workloads.transfer_function(rng, 32)
+    cam = _persp((1.9, 1.4, 1.7))
+    prm = {"width": W, "height": H, "step": 1 / 48, "max_opacity": 0.99, "shading": shading}
+    mid = ctx.load_model(ctrl, p)
+    img, ns = _render(ctx, torch_cuda, mid, cam, prm, tf)
+    ref = orc.render(ctrl, p, cam, dict(prm, tf=tf))
+    assert_render_parity(img, ns, ref)
+    ctx.unload_model(mid)
+
+
+@pytest.mark.parametrize("case", ["ortho_oblique", "inside_box", "opacity_correction", "tf_size_1",
+                                  "no_ert", "ragged", "world_box", "high_opacity", "explicit_tf_range"])
+def test_render_variants(ctx, torch_cuda, orc, case):
+    from paper_2204_11762_gb300 import workloads
+    import zlib
+    rng = np.random.default_rng(zlib.crc32(case.encode()))
+    p = 3
+    ctrl = (rng.normal(size=(14, 12, 13)) * 2.0).astype(np.float32)
+    tf = workloads.transfer_function(rng, 128)
+    cam = _persp((2.2, -0.9, 1.3))
+    prm = {"width": 40, "height": 32, "step": 1 / 128, "max_opacity": 0.99, "shading": 1}
+    box = ((0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    if case == "ortho_oblique":
+        cam = {"kind": 0, "eye": (2.0, 1.5, 1.8), "center": (0.5, 0.5, 0.5), "up": (0, 0, 1), "ortho_height": 1.6}
+    elif case == "inside_box":
+        cam = _persp((0.45, 0.55, 0.6), fovy=80.0)
+        cam["center"] = (0.9, 0.2, 0.1)
+    elif case == "opacity_correction":
+        prm["ref_step"] = 1 / 300
+    elif case == "tf_size_1":
+        tf = np.array([[0.3, 0.6, 0.9, 0.02]], dtype=np.float32)
+    elif case == "no_ert":
+        prm["max_opacity"] = 1.0
+    elif case == "ragged":
+        prm.update(width=37, height=23)
+    elif case == "world_box":
+        box = ((-1.0, 0.5, 2.0), (1.0, 1.5, 5.0))
+        cam = {"kind": 1, "eye": (3.0, 3.5, 6.0), "center": (0.0, 1.0, 3.5), "up": (0, 0, 1), "fovy_deg": 45.0}
+        prm["step"] = 1 / 40
+    elif case == "high_opacity":
+        tf[:, 3] = np.minimum(1.0, tf[:, 3] * 4)
+    elif case == "explicit_tf_range":
+        prm["tf_lo"], prm["tf_hi"] = -1.0, 1.5
+    mid = ctx.load_model(ctrl, p, box_min=box[0], box_max=box[1])
+    img, ns = _render(ctx, torch_cuda, mid, cam, prm, tf)
+    ref = orc.render(ctrl, p, cam, dict(prm, tf=tf), box_min=box[0], box_max=box[1])
+    assert_render_parity(img, ns, ref)
+    ctx.unload_model(mid)
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_render_16bit_storage(ctx, torch_cuda, orc, storage):
+    from paper_2204_11762_gb300 import workloads
+    rng = np.random.default_rng(77)
+    ctrl = workloads.gaussian_sum_lattice((24, 20, 22), 3, rng)
+    tf = workloads.transfer_function(rng, 256)
+    cam = workloads.sphere_camera(rng)
+    prm = {"width": 48, "height": 40, "step": 1 / 256, "max_opacity": 0.99, "shading": 1}
+    mid = ctx.load_model(ctrl, 3, storage=storage)
+    img, ns = _render(ctx, torch_cuda, mid, cam, prm, tf)
+    deq = dequantize(ctrl, storage)
+    # the TF domain stays [min P, max P] of the FP32 input
+    ref = orc.render(deq, 3, cam, dict(prm, tf=tf, tf_lo=float(ctrl.min()), tf_hi=float(ctrl.max())))
+    assert_render_parity(img, ns, ref)
+    ctx.unload_model(mid)
+
+
+def test_render_host_buffers_match_device(ctx, torch_cuda):
+    from paper_2204_11762_gb300 import workloads
+    wl = workloads.small_ml_workload()
+    mid = ctx.load_model(wl["ctrl"], wl["degree"])
+    img, ns = _render(ctx, torch_cuda, mid, wl["camera"], wl["params"], wl["tf"])
+    ns_h = np.empty_like(ns)
+    img_h = ctx.render_host(mid, wl["camera"], wl["params"], wl["tf"], nsamples=ns_h)
+    np.testing.assert_array_equal(img, img_h)
+    np.testing.assert_array_equal(ns, ns_h)
+    ctx.unload_model(mid)
+
+
+def test_full_size_gaussian_workload_sampled_rows(ctx, torch_cuda, orc):
+    """The 128^3 Gaussian-sum model at 1024^2, step 1/1024, in the launch the
+    benchmark times; every 64th row against the oracle."""
+    from paper_2204_11762_gb300 import workloads
+    wl = workloads.gaussian_sum_workload(with_points=False)
+    mid = ctx.load_model(wl["ctrl"], wl["degree"])
+    img, ns = _render(ctx, torch_cuda, mid, wl["camera"], wl["params"], wl["tf"])
+    ref = orc.render(wl["ctrl"], wl["degree"], wl["camera"], dict(wl["params"], tf=wl["tf"]), row_step=64)
+    rows = np.arange(0, wl["params"]["height"], 64)
+    assert_render_parity(img, ns, ref, rows=rows)
+    assert np.isfinite(img).all()
+    assert (img[..., 3] <= 1.0 + 1e-6).all() and (img >= -1e-6).all()
+    ctx.unload_model(mid)
+
+
+def test_render_invalid_arguments(ctx, torch_cuda):
+    from paper_2204_11762_gb300 import mfadvr
+    torch = torch_cuda
+    mid = ctx.load_model(np.ones((5, 5, 5), dtype=np.float32), 2)
+    tf = torch.ones((4, 4), device="cuda:0")
+    img = torch.empty((4, 4, 4), device="cuda:0")
+    good = {"width": 4, "height": 4, "step": 0.1}
+    for cam, prm in [({"kind": 2, "eye": (2, 2, 2)}, good),
+                     ({"kind": 1, "eye": (0.5, 0.5, 0.5)}, good),
+                     ({"kind": 1, "eye": (0.5, 0.5, 2.0), "up": (0, 0, 1)}, good),
+                     ({"kind": 1, "eye": (2, 2, 2), "fovy_deg": 180.0}, good),
+                     ({"kind": 1, "eye": (2, 2, 2)}, dict(good, step=0.0)),
+                     ({"kind": 1, "eye": (2, 2, 2)}, dict(good, width=0)),
+                     ({"kind": 1, "eye": (2, 2, 2)}, dict(good, shading=2))]:
+        with pytest.raises(mfadvr.MfadvrError) as e:
+            ctx.render(mid, cam, prm, tf, 4, img)
+        assert e.value.status == mfadvr.EINVAL
+    host_img = np.zeros((4, 4, 4), dtype=np.float32)
+    with pytest.raises(mfadvr.MfadvrError) as e:  # a host buffer is refused, not written
+        ctx.render(mid, {"kind": 1, "eye": (2, 2, 2)}, good, tf, 4, host_img)
+    assert e.value.status == mfadvr.EINVAL
+    with pytest.raises(mfadvr.MfadvrError) as e:  # 2^24+ samples per ray
+        ctx.render(mid, {"kind": 1, "eye": (2, 2, 2)}, dict(good, step=1e-8), tf, 4, img)
+    assert e.value.status == mfadvr.EINVAL
+    with pytest.raises(mfadvr.MfadvrError) as e:
+        ctx.render(mid, {"kind": 1, "eye": (2, 2, 2)}, good, tf, 0, img)
+    assert e.value.status == mfadvr.EINVAL
+    ctx.unload_model(mid)
