@@ -27,6 +27,13 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM bytes (read + write) of one render_kernel<3, float> launch on the
+# 128^3 workload from one ncu capture (profiles/render_kernel_gauss128_p3_persp1024.md),
+# valid only for the kernel sources it was taken on.
+RENDER_TRAFFIC = {"sources_sha256_16": "d02380136bb3e008", "bytes": 33649408}
+RENDER_SOURCES = ("paper_2204_11762_gb300/csrc/render_kernels.cu", "paper_2204_11762_gb300/csrc/mfa_basis.cuh",
+                  "paper_2204_11762_gb300/csrc/mfa_internal.h")
+
 METRIC = "MFA value+grad samples/s"
 UNIT = "samples/s"
 C_FMA = {p: 2 * (p + 1) ** 3 + 3 * (p + 1) ** 2 + 4 * (p + 1) for p in range(1, 6)}
@@ -36,8 +43,8 @@ FP32_LANES_PER_SM = 128
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-e2e", action="store_true")
@@ -51,6 +58,36 @@ def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def render_traffic():
+    """ncu DRAM bytes per render launch, or None once the kernel changed."""
+    import hashlib
+    h = hashlib.sha256()
+    try:
+        for f in RENDER_SOURCES:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    return RENDER_TRAFFIC["bytes"] if h.hexdigest()[:16] == RENDER_TRAFFIC["sources_sha256_16"] else None
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """Max of a per-rank float over the process group (identity at N = 1)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank_step: int, steps: int, max_ms: float, world: int) -> float:
+    """Units all ranks processed / the slowest rank's timed region (weak
+    scaling: every rank runs the same per-GPU workload)."""
+    return world * units_per_rank_step * steps / (max_ms / 1000.0)
 
 
 def _measured_peaks():
@@ -231,13 +268,9 @@ def run_ours(args, wl):
     total_ms = sum(render_ms) + sum(eval_ms)
     assert int(d_ns.sum(dtype=torch.int64).item()) == render_samples, "sample count changed between steps"
 
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dev)
     units_per_step = render_samples + npts
-    value = world * units_per_step * args.steps / (total_ms / 1000.0)
+    value = whole_job_value(units_per_step, args.steps, total_ms, world)
 
     # ---- roofline of the dominant kernel (render: FP32 FMA pipe) ---------
     props = torch.cuda.get_device_properties(dev)
@@ -253,7 +286,7 @@ def run_ours(args, wl):
     dominant = "render" if r_mean >= e_mean else "eval_points"
     if dominant == "render":
         roof = {"kernel": "render_kernel", "bound": "alu", "achieved": render_tflops, "peak": fma_peak_tflops,
-                "unit": "TFLOP/s", "frac": render_tflops / fma_peak_tflops, "traffic": None,
+                "unit": "TFLOP/s", "frac": render_tflops / fma_peak_tflops, "traffic": render_traffic(),
                 "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 FLOP x {sm_max_mhz:.0f} MHz",
                 "per_unit": f"{C_FMA[p]} FMA per sample (sum-factorised contraction, degree {p})"}
     else:
@@ -322,13 +355,8 @@ def run_ours(args, wl):
             ctx.render_host(mid, wl["camera"], prm, tf_np, rgba=img_np, stream=stream)
             ctx.eval_points_host(mid, h_pts.numpy(), out=h_out.numpy(), stream=stream)
         t1 = time.perf_counter()
-        dt = t1 - t0
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([dt], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        line["e2e"] = {"value": world * units_per_step * k2 / dt, "unit": UNIT,
+        dt = max_over_ranks(t1 - t0, dev)
+        line["e2e"] = {"value": whole_job_value(units_per_step, k2, dt * 1000.0, world), "unit": UNIT,
                        "h2d_bytes_per_step": npts * 12 + wl["tf"].nbytes,
                        "d2h_bytes_per_step": npts * 16 + H * W * 16, "steps": k2,
                        "ms_per_step": 1000 * dt / k2}

@@ -1,11 +1,12 @@
 // mfadvr_eval_points: value and first derivatives of the MFA model at
 // arbitrary parameter points (queryValueMFA + queryGradientMFA of
-// Algorithm 1, computed together as Sec. 3.1 describes).
+// Algorithm 1, computed together as Sec. 3.1 describes), and the kernel that
+// builds a model's quad array.
 //
 // One thread per point, grid-stride over a grid sized to the SM count.  The
 // span index is exact integer work (see span_exact); basis and contraction
-// run in FP32 on the FMA pipe; control points come through the read-only
-// cache (the lattices of the point workloads are L2-resident).
+// run in FP32 on the FMA pipe; the span block is (p+1) x ceil((p+1)/2)^2
+// vector loads from the quad array (L2-resident for the point workloads).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -20,13 +21,13 @@ __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const fl
                                                           int64_t n, float4 *__restrict__ out,
                                                           int32_t *__restrict__ spans)
 {
-    const T *__restrict__ cp = static_cast<const T *>(mv.cp);
     const float mf0 = static_cast<float>(mv.m[0]);
     const float mf1 = static_cast<float>(mv.m[1]);
     const float mf2 = static_cast<float>(mv.m[2]);
-    const int64_t sj = mv.n[0];
-    const int64_t sk = static_cast<int64_t>(mv.n[0]) * mv.n[1];
-    const float s0 = mv.scale * mf0, s1 = mv.scale * mf1, s2 = mv.scale * mf2;
+    constexpr float bs = BasisScale<P>::value;
+    const float sv = mv.scale / (bs * bs * bs);
+    const float s0 = sv * mf0, s1 = sv * mf1, s2 = sv * mf2;
+    const int n0 = mv.n[0], n01 = mv.n01;
 
     for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < n;
          idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -37,16 +38,30 @@ __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const fl
         const int k0 = span_exact(u, mv.m[0], mf0);
         const int k1 = span_exact(v, mv.m[1], mf1);
         const int k2 = span_exact(w, mv.m[2], mf2);
-        float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
-        basis<P>(fmaf(u, mf0, -static_cast<float>(k0)), k0, mv.m[0], Nu, dNu);
-        basis<P>(fmaf(v, mf1, -static_cast<float>(k1)), k1, mv.m[1], Nv, dNv);
-        basis<P>(fmaf(w, mf2, -static_cast<float>(k2)), k2, mv.m[2], Nw, dNw);
-
-        const T *base = cp + (k0 + sj * k1 + sk * k2);
+        const int base = k0 + n0 * k1 + n01 * k2;
         float r[4];
-        contract<P>(Nu, dNu, Nv, dNv, Nw, dNw,
-                    [&](int i, int j, int k) { return load_cp<T>(base + i + sj * j + sk * k); }, r);
-        out[idx] = make_float4(r[0] * mv.scale, r[1] * s0, r[2] * s1, r[3] * s2);
+        float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
+        if constexpr (P <= 3) {
+            // the whole block in flight before the basis is evaluated
+            float4 q[P + 1][Block<P>::JP][Block<P>::IQ];
+            load_block<P, T>(mv.quads, base, n0, n01, q);
+            basis<P>(fmaf(u, mf0, -static_cast<float>(k0)), k0, mv.m[0], Nu, dNu);
+            basis<P>(fmaf(v, mf1, -static_cast<float>(k1)), k1, mv.m[1], Nv, dNv);
+            basis<P>(fmaf(w, mf2, -static_cast<float>(k2)), k2, mv.m[2], Nw, dNw);
+            contract_pairs<P>(Nu, dNu, Nv, dNv, Nw, dNw,
+                              [&](int k, int jp, int i) { return quad_pair<P>(q, k, jp, i); }, r);
+        } else {
+            basis<P>(fmaf(u, mf0, -static_cast<float>(k0)), k0, mv.m[0], Nu, dNu);
+            basis<P>(fmaf(v, mf1, -static_cast<float>(k1)), k1, mv.m[1], Nv, dNv);
+            basis<P>(fmaf(w, mf2, -static_cast<float>(k2)), k2, mv.m[2], Nw, dNw);
+            contract_pairs<P>(Nu, dNu, Nv, dNv, Nw, dNw,
+                              [&](int k, int jp, int i) {
+                                  const float4 qv = QuadLoad<T>::at(mv.quads, base + (i & ~1) + 2 * jp * n0 + k * n01);
+                                  return (i & 1) ? make_float2(qv.z, qv.w) : make_float2(qv.x, qv.y);
+                              },
+                              r);
+        }
+        out[idx] = make_float4(r[0] * sv, r[1] * s0, r[2] * s1, r[3] * s2);
         if (spans) {
             spans[3 * idx + 0] = k0 + P;
             spans[3 * idx + 1] = k1 + P;
@@ -85,15 +100,40 @@ cudaError_t launch_eval_dtype(const ModelView &mv, const float *params, int64_t 
     }
 }
 
-__device__ __forceinline__ void store_q(__half *d, float v) { *d = __float2half_rn(v); }
-__device__ __forceinline__ void store_q(__nv_bfloat16 *d, float v) { *d = __float2bfloat16_rn(v); }
-
-template <typename T>
-__global__ void quantize_kernel(const float *__restrict__ src, T *__restrict__ dst, int64_t count, float inv_scale)
+__device__ __forceinline__ void store_quad(float4 *q, int64_t i, float a, float b, float c, float d)
 {
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        store_q(dst + i, src[i] * inv_scale);
+    q[i] = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void store_quad(uint2 *q, int64_t i, float a, float b, float c, float d, __half)
+{
+    const __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
+    q[i] = make_uint2(*reinterpret_cast<const unsigned *>(&lo), *reinterpret_cast<const unsigned *>(&hi));
+}
+__device__ __forceinline__ void store_quad(uint2 *q, int64_t i, float a, float b, float c, float d, __nv_bfloat16)
+{
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+    q[i] = make_uint2(*reinterpret_cast<const unsigned *>(&lo), *reinterpret_cast<const unsigned *>(&hi));
+}
+
+// One thread per lattice point (i, j, k): gathers P(i..i+1, j..j+1, k),
+// zero past the lattice, scales by inv_scale, rounds to the storage type.
+template <typename T>
+__global__ void build_quads_kernel(const float *__restrict__ src, void *__restrict__ dst, int n0, int n1, int n2,
+                                   float inv_scale)
+{
+    const int64_t total = static_cast<int64_t>(n0) * n1 * n2;
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int i = static_cast<int>(e % n0);
+        const int j = static_cast<int>((e / n0) % n1);
+        const bool ri = i + 1 < n0, rj = j + 1 < n1;
+        const float a = src[e] * inv_scale;
+        const float b = rj ? src[e + n0] * inv_scale : 0.0f;
+        const float c = ri ? src[e + 1] * inv_scale : 0.0f;
+        const float d = (ri && rj) ? src[e + n0 + 1] * inv_scale : 0.0f;
+        if constexpr (sizeof(T) == 4) store_quad(static_cast<float4 *>(dst), e, a, b, c, d);
+        else store_quad(static_cast<uint2 *>(dst), e, a, b, c, d, T());
+    }
 }
 
 }  // namespace
@@ -110,19 +150,24 @@ cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t
     }
 }
 
-// P / s rounded to nearest in the storage type.
-cudaError_t launch_quantize(const float *src, void *dst, int64_t count, int dtype, float inv_scale,
-                            cudaStream_t stream)
+cudaError_t launch_build_quads(const float *src, void *quads, int n0, int n1, int n2, int dtype, float inv_scale,
+                               cudaStream_t stream)
 {
-    if (count <= 0) return cudaSuccess;
-    const int blocks = static_cast<int>((count + 255) / 256 < 152 * 16 ? (count + 255) / 256 : 152 * 16);
-    if (dtype == MFADVR_F16)
-        quantize_kernel<__half><<<blocks, 256, 0, stream>>>(src, static_cast<__half *>(dst), count, inv_scale);
-    else if (dtype == MFADVR_BF16)
-        quantize_kernel<__nv_bfloat16>
-            <<<blocks, 256, 0, stream>>>(src, static_cast<__nv_bfloat16 *>(dst), count, inv_scale);
-    else
-        return cudaErrorInvalidValue;
+    const int64_t total = static_cast<int64_t>(n0) * n1 * n2;
+    if (total <= 0) return cudaSuccess;
+    const int blocks = static_cast<int>((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
+    switch (dtype) {
+    case MFADVR_F32:
+        build_quads_kernel<float><<<blocks, 256, 0, stream>>>(src, quads, n0, n1, n2, inv_scale);
+        break;
+    case MFADVR_F16:
+        build_quads_kernel<__half><<<blocks, 256, 0, stream>>>(src, quads, n0, n1, n2, inv_scale);
+        break;
+    case MFADVR_BF16:
+        build_quads_kernel<__nv_bfloat16><<<blocks, 256, 0, stream>>>(src, quads, n0, n1, n2, inv_scale);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -8,11 +8,17 @@
 
 namespace mfadvr {
 
-// A resident model as the kernels see it.  Control points are one array in
-// the storage type, u fastest: (i, j, k) at i + n[0]*(j + n[1]*k).
+// Factor by which the device-side uniform basis of degree p is scaled
+// (BasisScale in mfa_basis.cuh): contractions come out multiplied by its cube.
+constexpr float basis_scale_host(int p) { return p == 3 ? 6.0f : 1.0f; }
+
+// A resident model as the kernels see it.  The control points live in the
+// quad layout (see mfa_basis.cuh): entry (i, j, k) at i + n[0]*(j + n[1]*k)
+// holds {P(i,j,k), P(i,j+1,k), P(i+1,j,k), P(i+1,j+1,k)} in the storage type.
 struct ModelView {
-    const void *cp;
+    const void *quads;
     int n[3];       // control points per axis
+    int n01;        // n[0] * n[1]
     int m[3];       // knot spans per axis, m = n - p
     int p;          // degree (equal on all axes)
     int dtype;      // mfadvr_dtype
@@ -27,12 +33,15 @@ struct RenderSetup {
     float eye[3], fwd[3], right[3], up[3];
     float sx_scale, sx_off, sy_scale, sy_off;  // sx = sx_scale*(x+1/2) + sx_off
     float box_min[3], box_max[3], inv_ext[3];
-    float grad_scale[3];                // local-derivative -> world gradient
+    float lat_scale[3];                 // world -> lattice units: m / extent
+    float grad_scale[3];                // contraction derivative -> world gradient
     float step, max_opacity, opacity_ratio;
     int correct_opacity;                // 1 when step != ref_step
     const float4 *tf;                   // device table, tf_size >= 2 entries
     int tf_size;
-    float tf_lo, tf_inv_range;          // x = clamp((v - lo) * inv_range, 0, 1)
+    // table coordinate of a contraction result r: clamp(r*tf_a + tf_b, 0, tf_size-1)
+    // (folds the storage scale, the basis scale and [lo, hi] into one FMA)
+    float tf_a, tf_b;
     int shading;
     float ka, kd, ks, shininess;
     float gthresh2;                     // |g|^2 <= gthresh2: ambient only
@@ -43,8 +52,12 @@ struct RenderSetup {
 // Kernel launchers (asynchronous on `stream`).
 cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t n, float4 *out,
                                int32_t *spans, cudaStream_t stream);
-cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, cudaStream_t stream);
-cudaError_t launch_quantize(const float *src, void *dst, int64_t count, int dtype, float inv_scale,
-                            cudaStream_t stream);
+// `counter` is one device int the render kernel's warps take ray tiles from;
+// the launcher zeroes it on `stream` first.
+cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream);
+// Builds the quad array of an n0 x n1 x n2 FP32 lattice (device memory),
+// scaling by inv_scale and rounding to the storage type.
+cudaError_t launch_build_quads(const float *src, void *quads, int n0, int n1, int n2, int dtype, float inv_scale,
+                               cudaStream_t stream);
 
 }  // namespace mfadvr

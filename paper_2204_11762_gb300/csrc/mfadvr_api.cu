@@ -18,7 +18,7 @@ using namespace mfadvr;
 namespace {
 
 struct Model {
-    void *d_cp = nullptr;
+    void *d_quads = nullptr;  // quad layout, see mfa_basis.cuh
     uint64_t bytes = 0;
     int p = 0;
     int n[3] = {0, 0, 0};
@@ -62,6 +62,11 @@ struct mfadvr_ctx {
     int32_t next_id = 0;
     std::string err;
     Staging st_in, st_out, st_aux;
+    // Ray-tile counters of render launches: each call takes the next slot of
+    // the ring, so calls queued on different streams do not share one.
+    int *counters = nullptr;
+    unsigned next_counter = 0;
+    static constexpr unsigned kCounters = 1024;
 };
 
 namespace {
@@ -120,7 +125,8 @@ bool finite3(const float v[3]) { return std::isfinite(v[0]) && std::isfinite(v[1
 ModelView view_of(const Model &m)
 {
     ModelView v;
-    v.cp = m.d_cp;
+    v.quads = m.d_quads;
+    v.n01 = m.n[0] * m.n[1];
     v.p = m.p;
     v.dtype = m.dtype;
     v.scale = m.scale;
@@ -131,7 +137,20 @@ ModelView view_of(const Model &m)
     return v;
 }
 
-size_t dtype_size(int dtype) { return dtype == MFADVR_F32 ? 4 : 2; }
+size_t quad_size(int dtype) { return dtype == MFADVR_F32 ? 16 : 8; }
+
+mfadvr_status next_counter(mfadvr_ctx *ctx, int **out)
+{
+    if (!ctx->counters) {
+        cudaError_t e = cudaMalloc(&ctx->counters, sizeof(int) * mfadvr_ctx::kCounters);
+        if (e != cudaSuccess) {
+            ctx->counters = nullptr;
+            return cuda_fail(ctx, e, "counter allocation");
+        }
+    }
+    *out = ctx->counters + (ctx->next_counter++ % mfadvr_ctx::kCounters);
+    return MFADVR_OK;
+}
 
 mfadvr_status find_model(mfadvr_ctx *ctx, int32_t id, Model **out)
 {
@@ -153,8 +172,9 @@ mfadvr_status make_setup(mfadvr_ctx *ctx, const Model &m, const mfadvr_camera *c
         return fail(ctx, MFADVR_EINVAL, "fovy_deg must be in (0, 180)");
     if (cam->kind == 0 && !(cam->ortho_height > 0.0f && std::isfinite(cam->ortho_height)))
         return fail(ctx, MFADVR_EINVAL, "ortho_height must be > 0");
-    if (rp->width <= 0 || rp->height <= 0 || rp->width > 65536 || rp->height > 65536)
-        return fail(ctx, MFADVR_EINVAL, "image size must be in 1..65536");
+    if (rp->width <= 0 || rp->height <= 0 || rp->width > 65536 || rp->height > 65536 ||
+        static_cast<int64_t>(rp->width) * rp->height > (int64_t(1) << 30))
+        return fail(ctx, MFADVR_EINVAL, "image sides must be in 1..65536 and width*height <= 2^30");
     if (!(rp->step > 0.0f) || !std::isfinite(rp->step)) return fail(ctx, MFADVR_EINVAL, "step must be > 0");
     {
         // Bound the samples on one ray (the chord of the box is at most its
@@ -207,6 +227,7 @@ mfadvr_status make_setup(mfadvr_ctx *ctx, const Model &m, const mfadvr_camera *c
         b = th;
     }
     std::memset(rs, 0, sizeof *rs);
+    const double bs = basis_scale_host(m.p), bs3 = bs * bs * bs;
     rs->width = rp->width;
     rs->height = rp->height;
     rs->kind = cam->kind;
@@ -219,7 +240,8 @@ mfadvr_status make_setup(mfadvr_ctx *ctx, const Model &m, const mfadvr_camera *c
         rs->box_max[i] = m.box_max[i];
         const double ext = static_cast<double>(m.box_max[i]) - m.box_min[i];
         rs->inv_ext[i] = static_cast<float>(1.0 / ext);
-        rs->grad_scale[i] = static_cast<float>(static_cast<double>(m.n[i] - m.p) * m.scale / ext);
+        rs->lat_scale[i] = static_cast<float>(static_cast<double>(m.n[i] - m.p) / ext);
+        rs->grad_scale[i] = static_cast<float>(static_cast<double>(m.n[i] - m.p) * m.scale / ext / bs3);
     }
     rs->sx_scale = static_cast<float>(2.0 * a / W);
     rs->sx_off = static_cast<float>(-a);
@@ -232,8 +254,10 @@ mfadvr_status make_setup(mfadvr_ctx *ctx, const Model &m, const mfadvr_camera *c
     rs->tf_size = rp->tf_size;
     const double lo = std::isnan(rp->tf_lo) ? m.pmin : rp->tf_lo;
     const double hi = std::isnan(rp->tf_hi) ? m.pmax : rp->tf_hi;
-    rs->tf_lo = static_cast<float>(lo);
-    rs->tf_inv_range = hi > lo ? static_cast<float>(1.0 / (hi - lo)) : 0.0f;
+    const double last = rp->tf_size > 1 ? rp->tf_size - 1 : 1;
+    const double inv_range = hi > lo ? 1.0 / (hi - lo) : 0.0;
+    rs->tf_a = static_cast<float>(static_cast<double>(m.scale) / bs3 * inv_range * last);
+    rs->tf_b = static_cast<float>(-lo * inv_range * last);
     rs->shading = rp->shading;
     rs->ka = rp->ka;
     rs->kd = rp->kd;
@@ -296,7 +320,8 @@ mfadvr_status mfadvr_destroy(mfadvr_ctx *ctx)
         DeviceGuard g(ctx->device);
         cudaDeviceSynchronize();
         for (auto &kv : ctx->models)
-            if (kv.second.d_cp) cudaFree(kv.second.d_cp);
+            if (kv.second.d_quads) cudaFree(kv.second.d_quads);
+        if (ctx->counters) cudaFree(ctx->counters);
         ctx->st_in.release();
         ctx->st_out.release();
         ctx->st_aux.release();
@@ -329,6 +354,8 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
         return fail(ctx, MFADVR_EUNSUPPORTED, "degrees must be equal on the three axes");
 
     const uint64_t count = static_cast<uint64_t>(desc->ncp[0]) * desc->ncp[1] * desc->ncp[2];
+    if (count >= (uint64_t(1) << 31))
+        return fail(ctx, MFADVR_EUNSUPPORTED, "lattices of 2^31 or more control points are not supported");
     float pmin = INFINITY, pmax = -INFINITY, pabs = 0.0f;
     for (uint64_t i = 0; i < count; ++i) {
         const float v = desc->ctrl[i];
@@ -350,7 +377,7 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
     m.pmax = pmax;
     m.pabs = pabs;
     m.scale = (desc->storage == MFADVR_F32 || pabs == 0.0f) ? 1.0f : pabs;
-    m.bytes = count * dtype_size(m.dtype);
+    m.bytes = count * quad_size(m.dtype);
     if (ctx->budget && ctx->used + m.bytes > ctx->budget)
         return fail(ctx, MFADVR_ENOMEM, "model of %llu bytes exceeds the HBM budget (%llu of %llu used)",
                     static_cast<unsigned long long>(m.bytes), static_cast<unsigned long long>(ctx->used),
@@ -358,26 +385,23 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
 
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
-    cudaError_t e = cudaMalloc(&m.d_cp, m.bytes);
+    cudaError_t e = cudaMalloc(&m.d_quads, m.bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        m.d_quads = nullptr;
         return fail(ctx, MFADVR_ENOMEM, "cudaMalloc(%llu): %s", static_cast<unsigned long long>(m.bytes),
                     cudaGetErrorString(e));
     }
-    if (m.dtype == MFADVR_F32) {
-        e = cudaMemcpy(m.d_cp, desc->ctrl, m.bytes, cudaMemcpyHostToDevice);
-    } else {
-        void *tmp = nullptr;
-        e = cudaMalloc(&tmp, count * sizeof(float));
-        if (e == cudaSuccess) e = cudaMemcpy(tmp, desc->ctrl, count * sizeof(float), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess)
-            e = launch_quantize(static_cast<const float *>(tmp), m.d_cp, static_cast<int64_t>(count), m.dtype,
-                                1.0f / m.scale, nullptr);
-        if (e == cudaSuccess) e = cudaDeviceSynchronize();
-        if (tmp) cudaFree(tmp);
-    }
+    void *tmp = nullptr;
+    e = cudaMalloc(&tmp, count * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(tmp, desc->ctrl, count * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_build_quads(static_cast<const float *>(tmp), m.d_quads, m.n[0], m.n[1], m.n[2], m.dtype,
+                               1.0f / m.scale, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) {
-        cudaFree(m.d_cp);
+        cudaFree(m.d_quads);
         return cuda_fail(ctx, e, "model upload");
     }
     const int32_t id = ctx->next_id++;
@@ -394,7 +418,7 @@ mfadvr_status mfadvr_unload_model(mfadvr_ctx *ctx, int32_t model_id)
     if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
-    cudaFree(m->d_cp);
+    cudaFree(m->d_quads);
     ctx->used -= m->bytes;
     ctx->models.erase(model_id);
     return MFADVR_OK;
@@ -484,7 +508,9 @@ mfadvr_status mfadvr_render(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_came
     if (mfadvr_status st = stage_tf(ctx, params->tf_rgba, params->tf_size, false, &rs, s)) return st;
     rs.out = reinterpret_cast<float4 *>(rgba_dev);
     rs.nsamples = nsamples_dev;
-    cudaError_t e = launch_render(view_of(*m), rs, s);
+    int *counter = nullptr;
+    if (mfadvr_status st = next_counter(ctx, &counter)) return st;
+    cudaError_t e = launch_render(view_of(*m), rs, counter, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "render launch");
     return MFADVR_OK;
 }
@@ -509,7 +535,9 @@ mfadvr_status mfadvr_render_host(mfadvr_ctx *ctx, int32_t model_id, const mfadvr
     if (e != cudaSuccess) return cuda_fail(ctx, e, "staging allocation");
     rs.out = static_cast<float4 *>(ctx->st_out.ptr);
     rs.nsamples = nsamples_host ? reinterpret_cast<int32_t *>(static_cast<char *>(ctx->st_out.ptr) + img_b) : nullptr;
-    e = launch_render(view_of(*m), rs, s);
+    int *counter = nullptr;
+    if (mfadvr_status st = next_counter(ctx, &counter)) return st;
+    e = launch_render(view_of(*m), rs, counter, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(rgba_host, rs.out, img_b, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && nsamples_host)
         e = cudaMemcpyAsync(nsamples_host, rs.nsamples, ns_b, cudaMemcpyDeviceToHost, s);
