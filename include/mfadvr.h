@@ -169,6 +169,47 @@ MFADVR_API mfadvr_status mfadvr_render_host(mfadvr_ctx *ctx, int32_t model_id, c
                                  const mfadvr_render_params *params, float *rgba_host,
                                  int32_t *nsamples_host, void *stream);
 
+/* ---- Allocation-free render -------------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory during a render.  Examples are code recording
+ * into a CUDA stream capture, plug-in hosts whose device memory belongs to
+ * the host application's pool allocator, and real-time loops that cannot
+ * afford the device synchronisation an allocation implies.  mfadvr_create,
+ * mfadvr_load_model and mfadvr_render all allocate; this call does not.
+ *
+ * It renders like mfadvr_render from a lattice the caller keeps in its own
+ * device memory, with no context and no loaded model:
+ *  ctrl_dev:     DEVICE, ncp[0]*ncp[1]*ncp[2] FP32 control points (u fastest),
+ *                4-byte aligned; at most MFADVR_NOALLOC_MAX_POINTS of them
+ *                (larger lattices return MFADVR_ENOMEM).  Values must be
+ *                finite (they are not scanned).
+ *  degree, ncp, box_min, box_max: as in mfadvr_model_desc (clamped uniform
+ *                knots, FP32 storage).
+ *  params:       as for mfadvr_render, with tf_rgba a 16-byte aligned DEVICE
+ *                table of at least 2 entries, and tf_lo / tf_hi given (NaN is
+ *                refused: the lattice range is not computed).  Shading treats
+ *                only an exactly zero gradient as ambient-only.
+ *  rgba_dev, nsamples_dev, stream: as for mfadvr_render.
+ * Scratch: the quad layout of the lattice and the ray-tile counter live in
+ * one file-scope device array of 256 + 16 * MFADVR_NOALLOC_MAX_POINTS bytes
+ * (8 MiB + 256 B), which every GPU that loads the library holds until the
+ * process exits.  Every call rebuilds the quads and zeroes the counter on its
+ * stream before reading them, so no call reads what an earlier call left
+ * there; but all calls share that one array, so calls whose work overlaps
+ * on the GPU (different streams, or different host threads) race and
+ * corrupt each other's images.  Serialise them.
+ * Set-up: the first call on a device, with that device current, looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture on that device.  The work runs on the current
+ * device and is asynchronous on `stream`.  Errors are read with
+ * mfadvr_last_error(NULL). */
+#define MFADVR_NOALLOC_MAX_POINTS (1 << 19)
+MFADVR_API mfadvr_status mfadvr_render_lattice_noalloc(const float *ctrl_dev, const int32_t degree[3],
+                                                       const int32_t ncp[3], const float box_min[3],
+                                                       const float box_max[3], const mfadvr_camera *camera,
+                                                       const mfadvr_render_params *params, float *rgba_dev,
+                                                       int32_t *nsamples_dev, void *stream);
+
 /* Static text for a status code. */
 MFADVR_API const char *mfadvr_status_string(mfadvr_status status);
 

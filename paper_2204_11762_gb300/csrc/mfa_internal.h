@@ -60,4 +60,10 @@ cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, int *count
 cudaError_t launch_build_quads(const float *src, void *quads, int n0, int n1, int n2, int dtype, float inv_scale,
                                cudaStream_t stream);
 
+// Render setup for a caller-owned FP32 lattice outside any context, and the
+// context-free error sink (mfadvr_last_error(NULL)); both in mfadvr_api.cu.
+mfadvr_status setup_for_lattice(int p, const int n[3], const float box_min[3], const float box_max[3],
+                                const mfadvr_camera *cam, const mfadvr_render_params *rp, RenderSetup *rs);
+mfadvr_status fail_noctx(mfadvr_status st, const char *msg);
+
 }  // namespace mfadvr

@@ -294,6 +294,27 @@ mfadvr_status stage_tf(mfadvr_ctx *ctx, const float *tf, int size, bool tf_on_ho
 
 }  // namespace
 
+// Render setup for a lattice that lives outside any context (the
+// allocation-free entry point): FP32 values, scale 1, an explicit TF range,
+// and a shading threshold of zero because max|P| is not known.  Errors go to
+// the context-free last-error message.
+mfadvr_status mfadvr::setup_for_lattice(int p, const int n[3], const float box_min[3], const float box_max[3],
+                                         const mfadvr_camera *cam, const mfadvr_render_params *rp, RenderSetup *rs)
+{
+    Model m;
+    m.p = p;
+    m.dtype = MFADVR_F32;
+    m.scale = 1.0f;
+    for (int a = 0; a < 3; ++a) {
+        m.n[a] = n[a];
+        m.box_min[a] = box_min[a];
+        m.box_max[a] = box_max[a];
+    }
+    return make_setup(nullptr, m, cam, rp, rs);
+}
+
+mfadvr_status mfadvr::fail_noctx(mfadvr_status st, const char *msg) { return fail(nullptr, st, "%s", msg); }
+
 extern "C" {
 
 mfadvr_status mfadvr_create(mfadvr_ctx **out, int device, uint64_t hbm_budget_bytes)

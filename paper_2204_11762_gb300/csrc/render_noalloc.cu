@@ -1,0 +1,137 @@
+// mfadvr_render_lattice_noalloc: the render path for callers that cannot
+// allocate device memory.
+//
+// Some callers must not call cudaMalloc during a render:
+//  - code that records work into a CUDA stream capture, where an allocation
+//    is not part of the captured work;
+//  - plug-in hosts whose device memory is owned by the host application's
+//    pool allocator;
+//  - real-time loops, where the implicit device synchronisation of an
+//    allocation would stall a frame.
+// The regular path allocates: mfadvr_create / mfadvr_load_model put the model
+// in library-owned memory, and mfadvr_render allocates its ray-tile counter
+// ring on first use.  This entry point allocates nothing.  The caller passes
+// its own FP32 lattice, transfer function and outputs in device memory.  The
+// quad layout the render kernel reads and the ray-tile counter live in one
+// file-scope device array of fixed size, which every GPU that loads the
+// library holds until the process exits.
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
+#include "mfa_internal.h"
+#include "mfadvr.h"
+
+namespace {
+
+// [0, 256): the ray-tile counter; [256, 256 + 16 * MFADVR_NOALLOC_MAX_POINTS):
+// the FP32 quad array of the lattice.
+constexpr size_t kCounterBytes = 256;
+constexpr size_t kScratchBytes = kCounterBytes + 16ull * MFADVR_NOALLOC_MAX_POINTS;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+void *g_scratch_ptr[kMaxDevices] = {};
+
+bool device_pointer(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+mfadvr_status err(mfadvr_status st, const char *msg) { return mfadvr::fail_noctx(st, msg); }
+
+}  // namespace
+
+extern "C" MFADVR_API mfadvr_status mfadvr_render_lattice_noalloc(
+    const float *ctrl_dev, const int32_t degree[3], const int32_t ncp[3], const float box_min[3],
+    const float box_max[3], const mfadvr_camera *camera, const mfadvr_render_params *params, float *rgba_dev,
+    int32_t *nsamples_dev, void *stream)
+{
+    if (!degree || !ncp || !box_min || !box_max || !camera || !params)
+        return err(MFADVR_EINVAL, "degree, ncp, box, camera and params must not be NULL");
+    if (degree[0] != degree[1] || degree[0] != degree[2] || degree[0] < 1 || degree[0] > MFADVR_MAX_DEGREE)
+        return err(MFADVR_EUNSUPPORTED, "degrees must be equal on the three axes and in 1..MFADVR_MAX_DEGREE");
+    int n[3];
+    for (int a = 0; a < 3; ++a) {
+        if (ncp[a] < degree[a] + 1 || ncp[a] > (1 << 24)) return err(MFADVR_EINVAL, "ncp must be in degree+1..2^24");
+        if (!std::isfinite(box_min[a]) || !std::isfinite(box_max[a]) || !(box_max[a] > box_min[a]))
+            return err(MFADVR_EINVAL, "box_max must exceed box_min on every axis");
+        n[a] = ncp[a];
+    }
+    const unsigned long long points = static_cast<unsigned long long>(n[0]) * n[1] * n[2];
+    if (points > MFADVR_NOALLOC_MAX_POINTS) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "lattice of %llu control points exceeds the allocation-free scratch (at most %d)",
+                 points, MFADVR_NOALLOC_MAX_POINTS);
+        return err(MFADVR_ENOMEM, msg);
+    }
+    if (std::isnan(params->tf_lo) || std::isnan(params->tf_hi))
+        return err(MFADVR_EINVAL, "tf_lo and tf_hi must be given (the lattice range is not computed here)");
+    if (params->tf_size < 2)
+        return err(MFADVR_EINVAL, "tf_size must be at least 2 (a one-entry table would need a staged copy)");
+    if (reinterpret_cast<uintptr_t>(ctrl_dev) % 4 != 0 || reinterpret_cast<uintptr_t>(params->tf_rgba) % 16 != 0 ||
+        reinterpret_cast<uintptr_t>(rgba_dev) % 16 != 0 || reinterpret_cast<uintptr_t>(nsamples_dev) % 4 != 0)
+        return err(MFADVR_EINVAL, "ctrl, tf_rgba, rgba and nsamples must be aligned (4, 16, 16, 4 bytes)");
+
+    mfadvr::RenderSetup rs;
+    if (mfadvr_status st = mfadvr::setup_for_lattice(degree[0], n, box_min, box_max, camera, params, &rs)) return st;
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return err(MFADVR_ECUDA, "no usable current device");
+    if (!device_pointer(ctrl_dev) || !device_pointer(params->tf_rgba) || !device_pointer(rgba_dev) ||
+        (nsamples_dev && !device_pointer(nsamples_dev)))
+        return err(MFADVR_EINVAL, "ctrl, tf_rgba, rgba and nsamples must be device pointers");
+
+    // Set-up, once per device and with that device current: the device
+    // address of the scratch array (its host-side name is only a stand-in).
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_setup_mu);
+        if (!g_scratch_ptr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();
+                return err(MFADVR_ECUDA, "cudaGetSymbolAddress of the allocation-free scratch failed");
+            }
+            g_scratch_ptr[dev] = p;
+        }
+        scratch = g_scratch_ptr[dev];
+    }
+    int *counter = static_cast<int *>(scratch);
+    void *quads = static_cast<unsigned char *>(scratch) + kCounterBytes;
+
+    mfadvr::ModelView mv;
+    mv.quads = quads;
+    mv.p = degree[0];
+    mv.dtype = MFADVR_F32;
+    mv.scale = 1.0f;
+    mv.n01 = n[0] * n[1];
+    for (int a = 0; a < 3; ++a) {
+        mv.n[a] = n[a];
+        mv.m[a] = n[a] - degree[0];
+    }
+    rs.tf = reinterpret_cast<const float4 *>(params->tf_rgba);
+    rs.out = reinterpret_cast<float4 *>(rgba_dev);
+    rs.nsamples = nsamples_dev;
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // The quads are rebuilt and the counter zeroed (by the render launcher)
+    // on every call, so nothing a previous call left in the array is read.
+    e = mfadvr::launch_build_quads(ctrl_dev, quads, n[0], n[1], n[2], MFADVR_F32, 1.0f, s);
+    if (e == cudaSuccess) e = mfadvr::launch_render(mv, rs, counter, s);
+    if (e != cudaSuccess) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "allocation-free render launch: %s", cudaGetErrorString(e));
+        return err(MFADVR_ECUDA, msg);
+    }
+    return MFADVR_OK;
+}

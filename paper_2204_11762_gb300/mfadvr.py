@@ -28,7 +28,8 @@ MAX_TF_SIZE = 4096
 # Every symbol include/mfadvr.h declares.
 EXPORTS = ("mfadvr_create", "mfadvr_destroy", "mfadvr_load_model", "mfadvr_unload_model", "mfadvr_model_info",
            "mfadvr_eval_points", "mfadvr_eval_points_host", "mfadvr_render", "mfadvr_render_host",
-           "mfadvr_status_string", "mfadvr_last_error")
+           "mfadvr_status_string", "mfadvr_last_error", "mfadvr_render_lattice_noalloc")
+NOALLOC_MAX_POINTS = 1 << 19
 
 
 class MfadvrError(RuntimeError):
@@ -87,6 +88,10 @@ def load_library(build_if_missing: bool = True):
         fn = getattr(L, name)
         fn.argtypes = args
         fn.restype = i32
+    f3, i3 = ctypes.c_float * 3, ctypes.c_int32 * 3
+    L.mfadvr_render_lattice_noalloc.argtypes = [vp, P(i3), P(i3), P(f3), P(f3), P(Camera), P(RenderParams),
+                                                vp, vp, vp]
+    L.mfadvr_render_lattice_noalloc.restype = i32
     L.mfadvr_status_string.argtypes = [i32]
     L.mfadvr_status_string.restype = ctypes.c_char_p
     L.mfadvr_last_error.argtypes = [vp]
@@ -150,6 +155,23 @@ def make_params(prm: dict, tf_ptr: int, tf_size: int) -> RenderParams:
     r.ks = float(prm.get("ks", 0.2))
     r.shininess = float(prm.get("shininess", 10.0))
     return r
+
+
+def render_lattice_noalloc(ctrl_dev, degree: int, ncp, camera: dict, params: dict, tf_dev, tf_size, rgba_dev,
+                           nsamples_dev=None, box_min=(0.0, 0.0, 0.0), box_max=(1.0, 1.0, 1.0), stream=None):
+    """mfadvr_render_lattice_noalloc: render from a caller-owned FP32 device
+    lattice (u fastest, ncp = (n_u, n_v, n_w)) without any allocation."""
+    L = load_library()
+    i3, f3 = ctypes.c_int32 * 3, ctypes.c_float * 3
+    cam = make_camera(camera)
+    prm = make_params(params, _ptr(tf_dev), tf_size)
+    st = L.mfadvr_render_lattice_noalloc(_ptr(ctrl_dev), ctypes.byref(i3(*([int(degree)] * 3))),
+                                         ctypes.byref(i3(*[int(v) for v in ncp])),
+                                         ctypes.byref(f3(*[float(v) for v in box_min])),
+                                         ctypes.byref(f3(*[float(v) for v in box_max])), ctypes.byref(cam),
+                                         ctypes.byref(prm), _ptr(rgba_dev), _ptr(nsamples_dev), _stream(stream))
+    if st != OK:
+        raise MfadvrError(st, L.mfadvr_last_error(None).decode())
 
 
 class Context:

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared_symbols():
     text = open(os.path.join(ROOT, "include", "mfadvr.h")).read()
-    return sorted(set(re.findall(r"\b(mfadvr_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"MFADVR_API\s+[\w\s\*]*?\b(mfadvr_[a-z_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
