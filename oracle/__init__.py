@@ -81,7 +81,7 @@ def lib():
                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
         L.orc_render.argtypes = [P(Model), P(Camera), P(RenderParams), ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                 ctypes.c_void_p, ctypes.c_void_p]
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         _lib = L
     return _lib
 
@@ -157,7 +157,7 @@ def eval_points(ctrl, degree, uvw, *, brute=False, threads=None, with_spans=True
 def render(ctrl, degree, camera: dict, params: dict, *, box_min=(0, 0, 0), box_max=(1, 1, 1),
            row_step=1, threads=None, brute=False):
     """Algorithm 1 in FP64.  Returns dict with rgba (H, W, 4), nsamples,
-    nambig, rgba_alt and nsamples_alt (see mfa_oracle.c)."""
+    nambig, rgba_alt, ns_lo and ns_hi (see orc_render in mfa_oracle.c)."""
     m, keep = _model(ctrl, degree, box_min, box_max)
     cam = Camera()
     cam.kind = int(camera.get("kind", 1))
@@ -185,13 +185,14 @@ def render(ctrl, degree, camera: dict, params: dict, *, box_min=(0, 0, 0), box_m
     rgba = np.zeros((H, W, 4), dtype=np.float64)
     alt = np.zeros((H, W, 4), dtype=np.float64)
     ns = np.zeros((H, W), dtype=np.int32)
-    ns_alt = np.zeros((H, W), dtype=np.int32)
+    lo = np.zeros((H, W), dtype=np.int32)
+    hi = np.zeros((H, W), dtype=np.int32)
     amb = np.zeros((H, W), dtype=np.int32)
     threads = threads or (os.cpu_count() or 1)
     rc = lib().orc_render(ctypes.byref(m), ctypes.byref(cam), ctypes.byref(rp), int(row_step),
                           int(threads), int(bool(brute)), rgba.ctypes.data, ns.ctypes.data,
-                          amb.ctypes.data, alt.ctypes.data, ns_alt.ctypes.data)
+                          amb.ctypes.data, alt.ctypes.data, lo.ctypes.data, hi.ctypes.data)
     if rc != 0:
         raise ValueError("oracle: invalid render arguments")
     del keep, tf
-    return {"rgba": rgba, "nsamples": ns, "nambig": amb, "rgba_alt": alt, "nsamples_alt": ns_alt}
+    return {"rgba": rgba, "nsamples": ns, "nambig": amb, "rgba_alt": alt, "ns_lo": lo, "ns_hi": hi}

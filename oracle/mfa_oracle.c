@@ -300,10 +300,16 @@ typedef struct {
     double ka, kd, ks, shininess;
 } orc_render_params;
 
-/* Decision ties: the FP32 path may take the other branch where the exact
- * quantity sits this close to a threshold. */
-#define ORC_TIE_SAMPLES 1e-4  /* distance of (t_exit - t_enter)/step from an integer */
-#define ORC_TIE_OPACITY 1e-5  /* distance of the cumulative opacity from O_max */
+/* Decision ties: an FP32 implementation may take the other branch where the
+ * exact quantity sits this close to a threshold.
+ *  - (t_exit - t_enter)/step: ORC_TIE_SAMPLES plus a per-ray bound of the
+ *    FP32 rounding of the ray and the slab test (box_hit), which grows where
+ *    a direction component comes out of cancelling terms.
+ *  - cumulative opacity: each FP32 sample opacity 1 - (1 - a)^r carries an
+ *    absolute rounding error near 6e-8, and rays run to a few thousand
+ *    samples before the strict test A > O_max. */
+#define ORC_TIE_SAMPLES 2e-3  /* distance of (t_exit - t_enter)/step from an integer */
+#define ORC_TIE_OPACITY 2e-4  /* distance of the cumulative opacity from O_max */
 
 typedef struct {
     orc_ctx c;
@@ -313,7 +319,7 @@ typedef struct {
     double lo, hi, gthresh;
     int row_step, nthreads, brute;
     double *rgba, *rgba_alt;
-    int32_t *nsamples, *nambig, *nsamples_alt;
+    int32_t *nsamples, *nambig, *ns_lo, *ns_hi;
 } render_job;
 
 static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
@@ -329,9 +335,16 @@ static void normalize3(double a[3])
     a[0] /= l; a[1] /= l; a[2] /= l;
 }
 
+/* Relative rounding unit of FP32 with headroom for a few chained
+ * operations; it sizes the tie window of the sample count. */
+#define ORC_F32_EPS (8.0 / 16777216.0)
+
 /* Ray through the centre of pixel (x, y), row 0 at the top (the "Ray
- * Definition" step of Sec. 3.1; the camera model itself is a reading). */
-static void make_ray(const render_job *J, int x, int y, double o[3], double d[3])
+ * Definition" step of Sec. 3.1; the camera model itself is a reading).
+ * eo/ed (optional): per component, a bound on how far an FP32 evaluation of
+ * the same formulas can move the origin and the unit direction (the sums
+ * cancel, so the bound scales with the magnitudes of their terms). */
+static void make_ray(const render_job *J, int x, int y, double o[3], double d[3], double eo[3], double ed[3])
 {
     const orc_camera *cam = J->cam;
     double W = J->rp->width, H = J->rp->height;
@@ -342,24 +355,36 @@ static void make_ray(const render_job *J, int x, int y, double o[3], double d[3]
         for (int a = 0; a < 3; ++a) {
             o[a] = cam->eye[a] + sx * J->right[a] + sy * J->upv[a];
             d[a] = J->fwd[a];
+            if (eo) eo[a] = ORC_F32_EPS * (fabs(cam->eye[a]) + fabs(sx * J->right[a]) + fabs(sy * J->upv[a]));
+            if (ed) ed[a] = ORC_F32_EPS;
         }
     } else {
         double th = tan(cam->fovy_deg * (M_PI / 180.0) * 0.5);
         double sx = (2.0 * (x + 0.5) / W - 1.0) * th * aspect;
         double sy = (1.0 - 2.0 * (y + 0.5) / H) * th;
+        double mag[3];
         for (int a = 0; a < 3; ++a) {
             o[a] = cam->eye[a];
             d[a] = J->fwd[a] + sx * J->right[a] + sy * J->upv[a];
+            mag[a] = fabs(J->fwd[a]) + fabs(sx * J->right[a]) + fabs(sy * J->upv[a]);
         }
-        normalize3(d);
+        double l = sqrt(dot3(d, d));
+        for (int a = 0; a < 3; ++a) {
+            d[a] /= l;
+            if (eo) eo[a] = ORC_F32_EPS * fabs(cam->eye[a]);
+            if (ed) ed[a] = ORC_F32_EPS * (mag[a] / l + fabs(d[a]));
+        }
     }
 }
 
 /* Slab test against the world box; [t_enter, t_exit] with t_enter >= 0.
- * Returns 0 on a miss. */
-static int box_hit(const orc_model *m, const double o[3], const double d[3], double *t0, double *t1)
+ * Returns 0 on a miss.  With eo/ed given, e0/e1 bound how far FP32 can move
+ * t_enter and t_exit: t = (b - o)/d moves by (|eo| + eps|b - o|)/|d| +
+ * |t| |ed|/|d| on the slab that decides it. */
+static int box_hit(const orc_model *m, const double o[3], const double d[3], double *t0, double *t1,
+                   const double eo[3], const double ed[3], double *e0, double *e1)
 {
-    double a0 = 0.0, a1 = INFINITY;
+    double a0 = 0.0, a1 = INFINITY, b0 = 0.0, b1 = 0.0;
     for (int a = 0; a < 3; ++a) {
         if (d[a] == 0.0) {
             if (o[a] < m->box_min[a] || o[a] > m->box_max[a]) return 0;
@@ -367,12 +392,22 @@ static int box_hit(const orc_model *m, const double o[3], const double d[3], dou
         }
         double ta = (m->box_min[a] - o[a]) / d[a];
         double tb = (m->box_max[a] - o[a]) / d[a];
-        if (ta > tb) { double s = ta; ta = tb; tb = s; }
-        if (ta > a0) a0 = ta;
-        if (tb < a1) a1 = tb;
+        double ea = 0.0, eb = 0.0;
+        if (eo && ed) {
+            ea = (eo[a] + ORC_F32_EPS * fabs(m->box_min[a] - o[a])) / fabs(d[a]) + fabs(ta) * ed[a] / fabs(d[a]);
+            eb = (eo[a] + ORC_F32_EPS * fabs(m->box_max[a] - o[a])) / fabs(d[a]) + fabs(tb) * ed[a] / fabs(d[a]);
+        }
+        if (ta > tb) {
+            double s = ta; ta = tb; tb = s;
+            s = ea; ea = eb; eb = s;
+        }
+        if (ta > a0) { a0 = ta; b0 = ea; }
+        if (tb < a1) { a1 = tb; b1 = eb; }
     }
     if (!(a1 > a0)) return 0;
     *t0 = a0; *t1 = a1;
+    if (e0) *e0 = b0;
+    if (e1) *e1 = b1;
     return 1;
 }
 
@@ -397,33 +432,43 @@ static void tf_lookup(const render_job *J, double v, double rgba[4])
     }
 }
 
-/* March one ray.  flip = index of the tied decision to take the other way
- * (-1: none).  Returns the number of tied decisions met. */
-static int march(const render_job *J, int x, int y, int flip, double out[4], int32_t *ns)
+/* March one ray.  flip_n != 0 takes the sample-count decision the other way
+ * when it is tied.  Returns 1 if the sample count was tied, else 0.
+ * out/ns: the pixel and sample count of the exact FP64 march.
+ * [ns_lo, ns_hi]: the sample counts an implementation whose cumulative
+ * opacity stays within ORC_TIE_OPACITY of the exact one can stop at: from
+ * the first sample with A > O_max - tol to the first with A > O_max + tol
+ * (or the last sample). */
+static int march(const render_job *J, int x, int y, int flip_n, double out[4], int32_t *ns, int32_t *ns_lo,
+                 int32_t *ns_hi)
 {
     const orc_model *m = J->c.m;
     const orc_render_params *rp = J->rp;
     double o[3], d[3], t0, t1;
-    int ties = 0;
+    int tied = 0;
     out[0] = out[1] = out[2] = out[3] = 0.0;
-    *ns = 0;
-    make_ray(J, x, y, o, d);
-    if (!box_hit(m, o, d, &t0, &t1)) return 0;
+    *ns = *ns_lo = *ns_hi = 0;
+    double eo[3], ed[3], e0 = 0.0, e1 = 0.0;
+    make_ray(J, x, y, o, d, eo, ed);
+    if (!box_hit(m, o, d, &t0, &t1, eo, ed, &e0, &e1)) return 0;
 
     /* Samples t_k = t_enter + (k + 1/2) step, k = 0..N-1, N = floor(len/step):
-     * every sample lies inside the volume (Sample_First..Sample_Last). */
+     * every sample lies inside the volume (Sample_First..Sample_Last).  The
+     * count is tied when FP32 rounding of the ray and the slab test can move
+     * (t_exit - t_enter)/step across an integer. */
     double r = (t1 - t0) / rp->step;
     long N = (long)floor(r);
     double rn = floor(r + 0.5);
-    if (rn >= 1.0 && fabs(r - rn) < ORC_TIE_SAMPLES) {
-        if (flip == ties) N = (N == (long)rn) ? (long)rn - 1 : (long)rn;
-        ties++;
+    double window = ORC_TIE_SAMPLES + (e0 + e1) / rp->step;
+    if (rn >= 1.0 && fabs(r - rn) < window) {
+        if (flip_n) N = (N == (long)rn) ? (long)rn - 1 : (long)rn;
+        tied = 1;
     }
     double ratio = (rp->ref_step > 0.0) ? rp->step / rp->ref_step : 1.0;
     double ext[3];
     for (int a = 0; a < 3; ++a) ext[a] = m->box_max[a] - m->box_min[a];
     double C[3] = {0, 0, 0}, A = 0.0;
-    long k;
+    long k, stop = -1, lo = -1, hi = -1;
     for (k = 0; k < N; ++k) {
         double t = t0 + ((double)k + 0.5) * rp->step;
         double q[3], f[4], rgba[4];
@@ -452,17 +497,25 @@ static int march(const render_job *J, int x, int y, int flip, double out[4], int
         double w = (1.0 - A) * alpha;
         for (int c = 0; c < 3; ++c) C[c] += w * rgba[c];
         A += w;
-        /* Early ray termination: strictly above O_max. */
-        int stop = A > rp->max_opacity;
-        if (fabs(A - rp->max_opacity) < ORC_TIE_OPACITY) {
-            if (flip == ties) stop = !stop;
-            ties++;
+        /* Early ray termination: strictly above O_max.  The march goes on
+         * past the exact stop only to find where a tied stop could fall. */
+        if (lo < 0 && A > rp->max_opacity - ORC_TIE_OPACITY) lo = k + 1;
+        if (stop < 0 && A > rp->max_opacity) {
+            stop = k + 1;
+            out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = A;
         }
-        if (stop) { k++; break; }
+        if (A > rp->max_opacity + ORC_TIE_OPACITY) { hi = k + 1; break; }
     }
-    *ns = (int32_t)k;
-    out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = A;
-    return ties;
+    if (stop < 0) {
+        stop = N;
+        out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = A;
+    }
+    if (lo < 0) lo = stop;
+    if (hi < 0) hi = N;
+    *ns = (int32_t)stop;
+    *ns_lo = (int32_t)lo;
+    *ns_hi = (int32_t)hi;
+    return tied;
 }
 
 typedef struct { render_job *J; int tid; } render_arg;
@@ -477,31 +530,41 @@ static void *render_worker(void *arg)
         if ((rows_done++ % J->nthreads) != ra->tid) continue;
         for (int x = 0; x < W; ++x) {
             size_t px = (size_t)y * W + x;
-            int32_t ns;
-            int ties = march(J, x, y, -1, J->rgba + 4 * px, &ns);
+            int32_t ns, lo, hi;
+            int tied = march(J, x, y, 0, J->rgba + 4 * px, &ns, &lo, &hi);
             J->nsamples[px] = ns;
-            if (J->nambig) J->nambig[px] = ties;
-            if (J->rgba_alt) {
-                int32_t ns2 = ns;
-                if (ties > 0) march(J, x, y, 0, J->rgba_alt + 4 * px, &ns2);
-                else memcpy(J->rgba_alt + 4 * px, J->rgba + 4 * px, 4 * sizeof(double));
-                if (J->nsamples_alt) J->nsamples_alt[px] = ns2;
+            if (J->nambig) J->nambig[px] = tied;
+            if (tied) {
+                /* the other sample count: its pixel, and the union of ranges */
+                int32_t ns2, lo2, hi2;
+                march(J, x, y, 1, J->rgba_alt + 4 * px, &ns2, &lo2, &hi2);
+                if (lo2 < lo) lo = lo2;
+                if (hi2 > hi) hi = hi2;
+            } else {
+                memcpy(J->rgba_alt + 4 * px, J->rgba + 4 * px, 4 * sizeof(double));
             }
+            if (J->ns_lo) J->ns_lo[px] = lo;
+            if (J->ns_hi) J->ns_hi[px] = hi;
         }
     }
     return NULL;
 }
 
 /* Render W x H pixels (row-major, row 0 at the top), premultiplied RGBA.
- * Only rows y = 0, row_step, 2*row_step, ... are rendered.  nsamples: the
- * number of samples composited per pixel.  nambig (optional): the number of
- * tied decisions per pixel.  rgba_alt / nsamples_alt (optional): the same
- * pixel with its first tied decision taken the other way.  Returns 0 or -1. */
+ * Only rows y = 0, row_step, 2*row_step, ... are rendered.
+ *  nsamples: samples composited per pixel by the exact FP64 march;
+ *  nambig (optional): 1 where the sample count (t_exit - t_enter)/step is
+ *      tied, else 0;
+ *  rgba_alt: the pixel with a tied sample count taken the other way (equal
+ *      to rgba elsewhere);
+ *  ns_lo, ns_hi (optional): the range of sample counts an FP32 march can
+ *      stop at (tied sample count and tied early termination included).
+ * Returns 0 or -1. */
 int orc_render(const orc_model *m, const orc_camera *cam, const orc_render_params *rp,
                int row_step, int nthreads, int brute, double *rgba, int32_t *nsamples,
-               int32_t *nambig, double *rgba_alt, int32_t *nsamples_alt)
+               int32_t *nambig, double *rgba_alt, int32_t *ns_lo, int32_t *ns_hi)
 {
-    if (!m || !cam || !rp || !rgba || !nsamples) return -1;
+    if (!m || !cam || !rp || !rgba || !nsamples || !rgba_alt) return -1;
     if (rp->width <= 0 || rp->height <= 0 || !(rp->step > 0.0) || rp->tf_size < 1 || !rp->tf_rgba) return -1;
     render_job J;
     memset(&J, 0, sizeof J);
@@ -511,7 +574,7 @@ int orc_render(const orc_model *m, const orc_camera *cam, const orc_render_param
     J.nthreads = nthreads < 1 ? 1 : (nthreads > 256 ? 256 : nthreads);
     J.brute = brute;
     J.rgba = rgba; J.nsamples = nsamples; J.nambig = nambig;
-    J.rgba_alt = rgba_alt; J.nsamples_alt = nsamples_alt;
+    J.rgba_alt = rgba_alt; J.ns_lo = ns_lo; J.ns_hi = ns_hi;
 
     /* Camera frame: forward, right = up x forward, true up = forward x right. */
     for (int a = 0; a < 3; ++a) J.fwd[a] = cam->center[a] - cam->eye[a];

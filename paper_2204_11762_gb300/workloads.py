@@ -99,36 +99,30 @@ def value_noise_lattice(n, p, rng, octaves=5, persistence=0.5, lacunarity=2.0, b
     """Multi-octave value noise on [0,1]^3 at the Greville abscissae:
     octave o has base_cells * lacunarity^o cells per axis, hashed lattice
     values U[-1, 1], trilinear interpolation with smoothstep weights,
-    amplitude persistence^o.  Built slab by slab in float32."""
+    amplitude persistence^o.  The interpolation is separable, so each octave
+    is three small matrix products (one interpolation matrix per axis)."""
     n = tuple(int(v) for v in n)
-    xs = [a.astype(np.float32) for a in _grid(n, p)]
+    xs = _grid(n, p)
     out = np.zeros((n[2], n[1], n[0]), dtype=np.float32)
     amp = 1.0
     for o in range(octaves):
         cells = int(round(base_cells * lacunarity ** o))
         vals = rng.uniform(-1.0, 1.0, size=(cells + 1, cells + 1, cells + 1)).astype(np.float32)
-        idx, wts = [], []
+        W = []
         for d in range(3):
             s = xs[d] * cells
             i0 = np.minimum(np.floor(s).astype(np.int64), cells - 1)
             f = s - i0
-            idx.append(i0)
-            wts.append((f * f * (3.0 - 2.0 * f)).astype(np.float32))
-        ix, wx = idx[0], wts[0]
-        iy, wy = idx[1], wts[1]
-        for k in range(n[2]):
-            iz, wz = idx[2][k], wts[2][k]
-            acc = np.zeros((n[1], n[0]), dtype=np.float32)
-            for dz in (0, 1):
-                fz = wz if dz else (1.0 - wz)
-                plane = vals[iz + dz]
-                for dy in (0, 1):
-                    fy = (wy if dy else (1.0 - wy))[:, None]
-                    rows = plane[iy + dy]
-                    for dx in (0, 1):
-                        fx = (wx if dx else (1.0 - wx))[None, :]
-                        acc += fz * fy * fx * rows[:, ix + dx]
-            out[k] += np.float32(amp) * acc
+            w = f * f * (3.0 - 2.0 * f)
+            M = np.zeros((n[d], cells + 1), dtype=np.float32)
+            M[np.arange(n[d]), i0] = 1.0 - w
+            M[np.arange(n[d]), i0 + 1] = w
+            W.append(M)
+        # vals[c, b, a] (z, y, x) -> out[k, j, i]
+        t = vals @ W[0].T                                   # (c, b, i)
+        t = np.einsum("jb,cbi->cji", W[1], t, optimize=True)  # (c, j, i)
+        t = np.tensordot(W[2], t, axes=([1], [0]))           # (k, j, i)
+        out += np.float32(amp) * t.astype(np.float32)
         amp *= persistence
     return out
 
@@ -152,13 +146,16 @@ def transfer_function(rng, size=256, nodes=4, alpha_max=0.5):
 
 
 def sphere_camera(rng, radius=2.0, centre=(0.5, 0.5, 0.5), fovy_deg=60.0):
-    """Perspective camera on a seeded sphere about ``centre``, looking at it."""
+    """Perspective camera on a seeded sphere about ``centre``, looking at it.
+    Coordinates are rounded to FP32, the precision of the camera inputs, so
+    every consumer sees the same camera."""
     v = rng.normal(size=3)
     v /= np.linalg.norm(v)
     eye = np.asarray(centre) + radius * v
     up = (0.0, 0.0, 1.0) if abs(v[2]) < 0.99 else (0.0, 1.0, 0.0)
-    return {"kind": 1, "eye": tuple(float(x) for x in eye), "center": tuple(float(c) for c in centre),
-            "up": up, "fovy_deg": float(fovy_deg), "ortho_height": 1.0}
+    f32 = lambda xs: tuple(float(np.float32(x)) for x in xs)
+    return {"kind": 1, "eye": f32(eye), "center": f32(centre), "up": up, "fovy_deg": float(np.float32(fovy_deg)),
+            "ortho_height": 1.0}
 
 
 def axis_ortho_camera():

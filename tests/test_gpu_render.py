@@ -182,3 +182,22 @@ def test_render_invalid_arguments(ctx, torch_cuda):
         ctx.render(mid, {"kind": 1, "eye": (2, 2, 2)}, good, tf, 0, img)
     assert e.value.status == mfadvr.EINVAL
     ctx.unload_model(mid)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_full_size_value_noise_sampled_rows(ctx, torch_cuda, orc, storage):
+    """Degree 4, 512^3 value-noise model, 3840x2160 perspective frame at step
+    1/2048 with a 1024-entry TF, in the launch the benchmark times; every
+    216th row against the oracle (on the lattice the model stores)."""
+    from paper_2204_11762_gb300 import workloads
+    wl = workloads.value_noise_workload(512)
+    ctrl = wl["ctrl"]
+    mid = ctx.load_model(ctrl, wl["degree"], storage=storage)
+    img, ns = _render(ctx, torch_cuda, mid, wl["camera"], wl["params"], wl["tf"])
+    ctx.unload_model(mid)
+    deq = ctrl if storage == "f32" else dequantize(ctrl, storage)
+    prm = dict(wl["params"], tf=wl["tf"], tf_lo=float(ctrl.min()), tf_hi=float(ctrl.max()))
+    ref = orc.render(deq, wl["degree"], wl["camera"], prm, row_step=216)
+    rows = np.arange(0, wl["params"]["height"], 216)
+    assert_render_parity(img, ns, ref, rows=rows)
+    assert np.isfinite(img).all()

@@ -319,6 +319,20 @@ def test_beer_lambert_constant_field(orc, alpha, step, ert):
     assert (res["nambig"] >= 1).all()
     np.testing.assert_allclose(res["rgba"], np.broadcast_to(exp, res["rgba"].shape), atol=1e-12)
     assert (res["nsamples"] == Ns).all()
+    # tied early termination: an FP32 march may stop anywhere from the first
+    # sample with A > O_max - 2e-4 to the first with A > O_max + 2e-4; the
+    # tied sample count widens that by the other N
+    Ak = 1 - (1 - a) ** np.arange(1, Nfull + 2)
+    def first_above(th, N):
+        idx = np.nonzero(Ak[:N] > th)[0]
+        return int(idx[0]) + 1 if idx.size else N
+    lo = min(first_above(ert - 2e-4, n) for n in (Nfull - 1, Nfull, Nfull + 1))
+    hi = max(first_above(ert + 2e-4, n) for n in (Nfull - 1, Nfull, Nfull + 1))
+    assert (res["ns_lo"] >= lo).all() and (res["ns_lo"] <= Ns).all()
+    assert (res["ns_hi"] <= hi).all() and (res["ns_hi"] >= Ns).all()
+    if ert < 1.0 and Ns < Nfull:
+        assert (res["ns_lo"] == first_above(ert - 2e-4, Nfull)).all()
+        assert (res["ns_hi"] == first_above(ert + 2e-4, Nfull)).all()
 
 
 def test_opacity_correction_closed_form(orc):
