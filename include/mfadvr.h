@@ -169,6 +169,55 @@ MFADVR_API mfadvr_status mfadvr_render_host(mfadvr_ctx *ctx, int32_t model_id, c
                                  const mfadvr_render_params *params, float *rgba_host,
                                  int32_t *nsamples_host, void *stream);
 
+/* One image of a batched render: a loaded model seen by a camera. */
+typedef struct {
+    int32_t model_id;
+    mfadvr_camera camera;
+    mfadvr_render_params params; /* tf_rgba: 16-byte aligned DEVICE table, tf_size >= 2 */
+    float *rgba_dev;             /* height x width x 4 FP32, 16-byte aligned           */
+    int32_t *nsamples_dev;       /* height x width int32, or NULL                      */
+} mfadvr_render_job;
+
+#define MFADVR_MAX_BATCH 256
+
+/* Render njobs images (Algorithm 1 for each), of any loaded models, in one
+ * call.  Jobs are grouped by degree and storage type; each group is ONE
+ * launch of a persistent kernel whose warps take 32-ray tiles from a single
+ * queue over the concatenated tiles of the group's images (kernels are
+ * compiled per degree, so a batch of several degrees launches once per
+ * degree).  Each image equals what mfadvr_render gives for its job.
+ * 1 <= njobs <= MFADVR_MAX_BATCH.  Asynchronous on `stream`; the job table
+ * is copied before the call returns.  The context keeps a ring of 32 job
+ * tables and 1024 tile counters: more than 32 batches (or 1024 render
+ * launches) in flight at once on different streams would reuse one.
+ * EINVAL / ENOTFOUND as for mfadvr_render, per job. */
+MFADVR_API mfadvr_status mfadvr_render_batch(mfadvr_ctx *ctx, int32_t njobs, const mfadvr_render_job *jobs,
+                                             void *stream);
+
+/* Launch shape of the render kernels, chosen by the autotuner. */
+typedef struct {
+    int32_t tile_w;      /* ray tile of tile_w x 32/tile_w pixels: 1, 2, 4, 8, 16 or 32 */
+    int32_t ctas_per_sm; /* resident CTAs per SM (0: as many as fit)                  */
+    float ms;            /* measured render time of the chosen shape                  */
+} mfadvr_tuning;
+
+/* Time mfadvr_render of this job under each candidate launch shape (tile
+ * shapes x occupancy), keep the fastest in the context's tuning table under
+ * the key (degree, storage type, log2 of the lattice size, log2 of the image
+ * size), and return it in *best (may be NULL).  mfadvr_render and
+ * mfadvr_render_batch use the table for every matching key.  Synchronous;
+ * writes the job's outputs.  A "batching" knob of the paper's design space
+ * (Sec. 4.3: performance depends on degree, lattice and image size). */
+MFADVR_API mfadvr_status mfadvr_autotune(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_camera *camera,
+                                         const mfadvr_render_params *params, float *rgba_dev,
+                                         int32_t *nsamples_dev, void *stream, mfadvr_tuning *best);
+
+/* Write / read the tuning table as text, one "p dtype lattice_log2
+ * image_log2 tile_w ctas_per_sm ms" line per key.  Loading merges into the
+ * table.  EINVAL: unreadable file or malformed line. */
+MFADVR_API mfadvr_status mfadvr_tuning_save(mfadvr_ctx *ctx, const char *path);
+MFADVR_API mfadvr_status mfadvr_tuning_load(mfadvr_ctx *ctx, const char *path);
+
 /* ---- Allocation-free render -------------------------------------------
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory during a render.  Examples are code recording

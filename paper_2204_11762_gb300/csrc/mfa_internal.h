@@ -47,7 +47,21 @@ struct RenderSetup {
     float gthresh2;                     // |g|^2 <= gthresh2: ambient only
     float4 *out;                        // H x W
     int32_t *nsamples;                  // H x W or nullptr
+    int tile_w_log2;                    // ray tiles of 2^k x 32/2^k pixels (k = 0..5)
+    int ctas_per_sm;                    // resident CTAs per SM to launch (0: as many as fit)
 };
+
+// One image of a batched render: its model, settings and place in the
+// concatenated tile sequence of the launch (sorted by tile_begin).
+struct RenderJob {
+    ModelView mv;
+    RenderSetup rs;
+    int tile_begin;  // first tile of this job in the launch
+    int tiles_x;     // tiles per image row
+    int tiles;       // tiles of this job
+    int pad;
+};
+static_assert(sizeof(RenderJob) % 8 == 0, "RenderJob is copied in 8-byte words");
 
 // Kernel launchers (asynchronous on `stream`).
 cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t n, float4 *out,
@@ -55,6 +69,11 @@ cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t
 // `counter` is one device int the render kernel's warps take ray tiles from;
 // the launcher zeroes it on `stream` first.
 cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream);
+// Batched render of njobs jobs of degree p and storage dtype (jobs_dev in
+// device memory, sorted by tile_begin, total_tiles tiles in all); `counter`
+// is zeroed on `stream` first.
+cudaError_t launch_render_batch(int p, int dtype, const RenderJob *jobs_dev, int njobs, int total_tiles,
+                                int ctas_per_sm, int *counter, cudaStream_t stream);
 // Builds the quad array of an n0 x n1 x n2 FP32 lattice (device memory),
 // scaling by inv_scale and rounding to the storage type.
 cudaError_t launch_build_quads(const float *src, void *quads, int n0, int n1, int n2, int dtype, float inv_scale,

@@ -7,7 +7,9 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <algorithm>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "mfa_internal.h"
@@ -55,6 +57,10 @@ std::string g_create_err;
 
 }  // namespace
 
+// Tuning-table key: degree, storage type, log2 of the lattice size and of
+// the image size.
+using TuneKey = std::tuple<int, int, int, int>;
+
 struct mfadvr_ctx {
     int device = 0;
     uint64_t budget = 0, used = 0;
@@ -67,6 +73,13 @@ struct mfadvr_ctx {
     int *counters = nullptr;
     unsigned next_counter = 0;
     static constexpr unsigned kCounters = 1024;
+    // Batched renders: a ring of job tables (pinned host + device), each
+    // slot guarded by an event recorded after the launches that read it.
+    static constexpr unsigned kJobSlots = 32;
+    mfadvr::RenderJob *h_jobs = nullptr, *d_jobs = nullptr;
+    cudaEvent_t job_done[kJobSlots] = {};
+    unsigned next_jobs = 0;
+    std::map<TuneKey, mfadvr_tuning> tuning;
 };
 
 namespace {
@@ -265,6 +278,8 @@ mfadvr_status make_setup(mfadvr_ctx *ctx, const Model &m, const mfadvr_camera *c
     rs->shininess = rp->shininess;
     const double th = 1e-20 * m.pabs;
     rs->gthresh2 = static_cast<float>(th * th);
+    rs->tile_w_log2 = 3;  // 8 x 4 pixel tiles unless tuned
+    rs->ctas_per_sm = 0;
     return MFADVR_OK;
 }
 
@@ -290,6 +305,31 @@ mfadvr_status stage_tf(mfadvr_ctx *ctx, const float *tf, int size, bool tf_on_ho
     rs->tf = dst;
     rs->tf_size = n;
     return MFADVR_OK;
+}
+
+int ilog2_u64(uint64_t v)
+{
+    int r = 0;
+    while (v > 1) {
+        v >>= 1;
+        ++r;
+    }
+    return r;
+}
+
+TuneKey tune_key(const Model &m, int width, int height)
+{
+    const uint64_t pts = static_cast<uint64_t>(m.n[0]) * m.n[1] * m.n[2];
+    return TuneKey(m.p, m.dtype, ilog2_u64(pts), ilog2_u64(static_cast<uint64_t>(width) * height));
+}
+
+// Launch shape from the tuning table, if this key has been tuned.
+void apply_tuning(const mfadvr_ctx *ctx, const Model &m, RenderSetup *rs)
+{
+    auto it = ctx->tuning.find(tune_key(m, rs->width, rs->height));
+    if (it == ctx->tuning.end()) return;
+    rs->tile_w_log2 = ilog2_u64(static_cast<uint64_t>(it->second.tile_w));
+    rs->ctas_per_sm = it->second.ctas_per_sm;
 }
 
 }  // namespace
@@ -343,6 +383,10 @@ mfadvr_status mfadvr_destroy(mfadvr_ctx *ctx)
         for (auto &kv : ctx->models)
             if (kv.second.d_quads) cudaFree(kv.second.d_quads);
         if (ctx->counters) cudaFree(ctx->counters);
+        if (ctx->d_jobs) cudaFree(ctx->d_jobs);
+        if (ctx->h_jobs) cudaFreeHost(ctx->h_jobs);
+        for (auto &e : ctx->job_done)
+            if (e) cudaEventDestroy(e);
         ctx->st_in.release();
         ctx->st_out.release();
         ctx->st_aux.release();
@@ -517,6 +561,7 @@ mfadvr_status mfadvr_render(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_came
     if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
     RenderSetup rs;
     if (mfadvr_status st = make_setup(ctx, *m, camera, params, &rs)) return st;
+    apply_tuning(ctx, *m, &rs);
     if (!rgba_dev || reinterpret_cast<uintptr_t>(rgba_dev) % 16 != 0)
         return fail(ctx, MFADVR_EINVAL, "rgba must be a 16-byte aligned device pointer");
     if (reinterpret_cast<uintptr_t>(nsamples_dev) % 4 != 0)
@@ -545,6 +590,7 @@ mfadvr_status mfadvr_render_host(mfadvr_ctx *ctx, int32_t model_id, const mfadvr
     if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
     RenderSetup rs;
     if (mfadvr_status st = make_setup(ctx, *m, camera, params, &rs)) return st;
+    apply_tuning(ctx, *m, &rs);
     if (!rgba_host) return fail(ctx, MFADVR_EINVAL, "rgba must not be NULL");
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
@@ -564,6 +610,182 @@ mfadvr_status mfadvr_render_host(mfadvr_ctx *ctx, int32_t model_id, const mfadvr
         e = cudaMemcpyAsync(nsamples_host, rs.nsamples, ns_b, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "render_host");
+    return MFADVR_OK;
+}
+
+mfadvr_status mfadvr_render_batch(mfadvr_ctx *ctx, int32_t njobs, const mfadvr_render_job *jobs, void *stream)
+{
+    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
+    if (njobs < 1 || njobs > MFADVR_MAX_BATCH || !jobs)
+        return fail(ctx, MFADVR_EINVAL, "njobs must be in 1..%d and jobs not NULL", MFADVR_MAX_BATCH);
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
+    // every argument first, then device work
+    std::vector<RenderJob> table(njobs);
+    std::vector<int> order(njobs);
+    for (int i = 0; i < njobs; ++i) {
+        const mfadvr_render_job &jb = jobs[i];
+        Model *m = nullptr;
+        if (mfadvr_status st = find_model(ctx, jb.model_id, &m)) return st;
+        RenderSetup &rs = table[i].rs;
+        if (mfadvr_status st = make_setup(ctx, *m, &jb.camera, &jb.params, &rs)) return st;
+        apply_tuning(ctx, *m, &rs);
+        if (jb.params.tf_size < 2 || reinterpret_cast<uintptr_t>(jb.params.tf_rgba) % 16 != 0)
+            return fail(ctx, MFADVR_EINVAL, "job %d: tf_rgba must be 16-byte aligned with tf_size >= 2", i);
+        if (!jb.rgba_dev || reinterpret_cast<uintptr_t>(jb.rgba_dev) % 16 != 0 ||
+            reinterpret_cast<uintptr_t>(jb.nsamples_dev) % 4 != 0)
+            return fail(ctx, MFADVR_EINVAL, "job %d: rgba must be 16-byte and nsamples 4-byte aligned", i);
+        if (!is_device_ptr(jb.rgba_dev) || !is_device_ptr(jb.params.tf_rgba) ||
+            (jb.nsamples_dev && !is_device_ptr(jb.nsamples_dev)))
+            return fail(ctx, MFADVR_EINVAL, "job %d: rgba, tf_rgba and nsamples must be device pointers", i);
+        rs.tf = reinterpret_cast<const float4 *>(jb.params.tf_rgba);
+        rs.out = reinterpret_cast<float4 *>(jb.rgba_dev);
+        rs.nsamples = jb.nsamples_dev;
+        table[i].mv = view_of(*m);
+        order[i] = i;
+    }
+    if (!ctx->d_jobs) {
+        const size_t bytes = sizeof(RenderJob) * MFADVR_MAX_BATCH * mfadvr_ctx::kJobSlots;
+        cudaError_t e = cudaMalloc(&ctx->d_jobs, bytes);
+        if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_jobs, bytes);
+        for (unsigned k = 0; e == cudaSuccess && k < mfadvr_ctx::kJobSlots; ++k)
+            e = cudaEventCreateWithFlags(&ctx->job_done[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "job-table allocation");
+    }
+    // group by (degree, storage type); each group's tiles are concatenated
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return std::make_pair(table[a].mv.p, table[a].mv.dtype) < std::make_pair(table[b].mv.p, table[b].mv.dtype);
+    });
+    const unsigned slot = ctx->next_jobs++ % mfadvr_ctx::kJobSlots;
+    cudaError_t e = cudaEventSynchronize(ctx->job_done[slot]);  // the slot's previous launches are done
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "job-table slot wait");
+    RenderJob *hj = ctx->h_jobs + static_cast<size_t>(slot) * MFADVR_MAX_BATCH;
+    RenderJob *dj = ctx->d_jobs + static_cast<size_t>(slot) * MFADVR_MAX_BATCH;
+    struct Group { int p, dtype, first, count, tiles; };
+    std::vector<Group> groups;
+    for (int k = 0; k < njobs; ++k) {
+        RenderJob jb = table[order[k]];
+        if (groups.empty() || groups.back().p != jb.mv.p || groups.back().dtype != jb.mv.dtype)
+            groups.push_back({jb.mv.p, jb.mv.dtype, k, 0, 0});
+        Group &gr = groups.back();
+        const int tw = 1 << jb.rs.tile_w_log2, th = 32 / tw;
+        jb.tiles_x = (jb.rs.width + tw - 1) / tw;
+        jb.tiles = jb.tiles_x * ((jb.rs.height + th - 1) / th);
+        jb.tile_begin = gr.tiles;
+        jb.pad = 0;
+        gr.tiles += jb.tiles;
+        gr.count += 1;
+        hj[k] = jb;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    e = cudaMemcpyAsync(dj, hj, sizeof(RenderJob) * njobs, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "job-table copy");
+    for (const Group &gr : groups) {
+        int *counter = nullptr;
+        if (mfadvr_status st = next_counter(ctx, &counter)) return st;
+        e = launch_render_batch(gr.p, gr.dtype, dj + gr.first, gr.count, gr.tiles, 0, counter, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batched render launch");
+    }
+    e = cudaEventRecord(ctx->job_done[slot], s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "job-table slot event");
+    return MFADVR_OK;
+}
+
+mfadvr_status mfadvr_autotune(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_camera *camera,
+                              const mfadvr_render_params *params, float *rgba_dev, int32_t *nsamples_dev, void *stream,
+                              mfadvr_tuning *best)
+{
+    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
+    Model *m = nullptr;
+    if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
+    RenderSetup rs;
+    if (mfadvr_status st = make_setup(ctx, *m, camera, params, &rs)) return st;
+    if (!rgba_dev || reinterpret_cast<uintptr_t>(rgba_dev) % 16 != 0 ||
+        reinterpret_cast<uintptr_t>(nsamples_dev) % 4 != 0)
+        return fail(ctx, MFADVR_EINVAL, "rgba must be 16-byte and nsamples 4-byte aligned");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
+    if (!is_device_ptr(rgba_dev) || !is_device_ptr(params->tf_rgba) || (nsamples_dev && !is_device_ptr(nsamples_dev)))
+        return fail(ctx, MFADVR_EINVAL, "rgba, tf_rgba and nsamples must be device pointers");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (mfadvr_status st = stage_tf(ctx, params->tf_rgba, params->tf_size, false, &rs, s)) return st;
+    rs.out = reinterpret_cast<float4 *>(rgba_dev);
+    rs.nsamples = nsamples_dev;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "event creation");
+    const int tile_ws[] = {8, 4, 16, 2, 32, 1};
+    const int ctas[] = {0, 2};
+    mfadvr_tuning win{8, 0, INFINITY};
+    for (int tw : tile_ws) {
+        for (int c : ctas) {
+            rs.tile_w_log2 = ilog2_u64(static_cast<uint64_t>(tw));
+            rs.ctas_per_sm = c;
+            float ms_best = INFINITY;
+            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+                int *counter = nullptr;
+                if (mfadvr_status st = next_counter(ctx, &counter)) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return st;
+                }
+                e = cudaEventRecord(e0, s);
+                if (e == cudaSuccess) e = launch_render(view_of(*m), rs, counter, s);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0 && ms < ms_best) ms_best = ms;  // the first run warms up
+            }
+            if (e != cudaSuccess) break;
+            if (ms_best < win.ms) win = mfadvr_tuning{tw, c, ms_best};
+        }
+        if (e != cudaSuccess) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+    ctx->tuning[tune_key(*m, rs.width, rs.height)] = win;
+    if (best) *best = win;
+    return MFADVR_OK;
+}
+
+mfadvr_status mfadvr_tuning_save(mfadvr_ctx *ctx, const char *path)
+{
+    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
+    if (!path) return fail(ctx, MFADVR_EINVAL, "path must not be NULL");
+    FILE *f = fopen(path, "w");
+    if (!f) return fail(ctx, MFADVR_EINVAL, "cannot open %s for writing", path);
+    for (const auto &kv : ctx->tuning)
+        fprintf(f, "%d %d %d %d %d %d %.6f\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                std::get<3>(kv.first), kv.second.tile_w, kv.second.ctas_per_sm, kv.second.ms);
+    const bool ok = fclose(f) == 0;
+    return ok ? MFADVR_OK : fail(ctx, MFADVR_EINVAL, "cannot write %s", path);
+}
+
+mfadvr_status mfadvr_tuning_load(mfadvr_ctx *ctx, const char *path)
+{
+    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
+    if (!path) return fail(ctx, MFADVR_EINVAL, "path must not be NULL");
+    FILE *f = fopen(path, "r");
+    if (!f) return fail(ctx, MFADVR_EINVAL, "cannot open %s", path);
+    std::map<TuneKey, mfadvr_tuning> add;
+    char line[256];
+    int lineno = 0;
+    while (fgets(line, sizeof line, f)) {
+        ++lineno;
+        int p, dt, lp, li, tw, c;
+        float ms;
+        if (sscanf(line, "%d %d %d %d %d %d %f", &p, &dt, &lp, &li, &tw, &c, &ms) != 7 || tw < 1 || tw > 32 ||
+            (tw & (tw - 1)) != 0 || c < 0) {
+            fclose(f);
+            return fail(ctx, MFADVR_EINVAL, "%s:%d: malformed tuning line", path, lineno);
+        }
+        add[TuneKey(p, dt, lp, li)] = mfadvr_tuning{tw, c, ms};
+    }
+    fclose(f);
+    for (const auto &kv : add) ctx->tuning[kv.first] = kv.second;
     return MFADVR_OK;
 }
 

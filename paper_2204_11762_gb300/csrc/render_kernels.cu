@@ -1,4 +1,5 @@
-// mfadvr_render: the ray caster of Algorithm 1 as one fused kernel.
+// mfadvr_render: the ray caster of Algorithm 1 as one fused kernel, and its
+// batched form over many images and models.
 //
 // Per pixel: ray definition (Sec. 3.1), slab test against the world box
 // (Sample_First..Sample_Last), constant-distance samples, value and gradient
@@ -7,15 +8,19 @@
 // compositing (doColorCompositing) and early ray termination once the
 // cumulative opacity exceeds O_max.
 //
-// GPU mapping.  A persistent grid of warps takes 8x4-pixel ray tiles from a
-// global counter; every lane owns one ray and, when its ray ends (exit or
-// early termination), takes the next ray of the warp's tile pool, so lanes
-// stay busy however unequal the ray lengths are.  Each lane walks its ray in
-// lattice units (one FMA per axis per sample), keeps the control points of
-// its current span block in registers and reloads them (ceil((p+1)/2)^2 x
-// (p+1) vector loads from the quad array) only when a sample leaves the
-// span.  The contraction runs on packed FP32 FMAs; the transfer function
-// sits in shared memory.
+// GPU mapping.  A persistent grid of warps takes 32-ray tiles (tile_w x
+// 32/tile_w pixels) from a global counter; every lane owns one ray and, when
+// its ray ends (exit or early termination), takes the next ray of the warp's
+// tile pool, so lanes stay busy however unequal the ray lengths are.  Each
+// lane walks its ray in lattice units (one FMA per axis per sample), keeps
+// the control points of its current span block in registers and reloads
+// them (ceil((p+1)/2)^2 x (p+1) vector loads from the quad array) only when
+// a sample leaves the span.  The contraction runs on packed FP32 FMAs.
+//
+// The batched kernel runs the same per-ray code over the concatenated tiles
+// of many render jobs (one image of one model each).  A warp keeps its
+// current job's model and settings in a shared-memory slot and moves to the
+// next job's tiles only when all its lanes are idle.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -26,6 +31,7 @@ namespace mfadvr {
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kWarps = kThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ float clamp01f(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }
@@ -46,6 +52,225 @@ struct MinBlocks {
     static constexpr int value = P <= 3 ? 4 : 1;
 };
 
+// State of the ray a lane is marching.
+struct LaneRay {
+    int pix;
+    float X0[3], dX[3], dir[3];  // sample s sits at lattice coordinates X0 + s dX
+    float kf[3];                 // current span (local index) per axis, as float
+    int kk[3];                   // the same as int
+    int base;                    // quad index of the span block's first control point
+    bool interior;               // all three spans unclamped: uniform pieces apply
+    float sf, nsf;               // samples taken / samples on the ray
+    float Cr, Cg, Cb, A;         // premultiplied colour and opacity so far
+};
+
+template <int P>
+struct SpanCache {
+    static constexpr bool kOn = CacheCP<P>::value;
+    float2 v[kOn ? (P + 1) : 1][kOn ? Block<P>::JP : 1][kOn ? (P + 1) : 1];
+};
+
+// Pixel of ray slot `slot` (tile = slot / 32, lane-in-tile = slot % 32) for
+// tiles of 2^tw_log2 x 32/2^tw_log2 pixels, tiles_x tiles per image row.
+__device__ __forceinline__ void slot_pixel(int slot, int tiles_x, int tw_log2, int &px, int &py)
+{
+    const int tile = slot >> 5, l = slot & 31;
+    const int th_log2 = 5 - tw_log2;
+    px = ((tile % tiles_x) << tw_log2) + (l & ((1 << tw_log2) - 1));
+    py = ((tile / tiles_x) << th_log2) + (l >> tw_log2);
+}
+
+// Ray definition and slab test for pixel (px, py).  Returns true when the
+// ray has samples; otherwise writes the empty pixel and returns false.
+__device__ __forceinline__ bool start_ray(const RenderSetup &rs, int px, int py, LaneRay &ray)
+{
+    ray.pix = py * rs.width + px;
+    const float sx = fmaf(rs.sx_scale, static_cast<float>(px) + 0.5f, rs.sx_off);
+    const float sy = fmaf(rs.sy_scale, static_cast<float>(py) + 0.5f, rs.sy_off);
+    float o[3];
+    if (rs.kind == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o[a] = fmaf(sy, rs.up[a], fmaf(sx, rs.right[a], rs.eye[a]));
+            ray.dir[a] = rs.fwd[a];
+        }
+    } else {
+        float dd = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o[a] = rs.eye[a];
+            ray.dir[a] = fmaf(sy, rs.up[a], fmaf(sx, rs.right[a], rs.fwd[a]));
+            dd = fmaf(ray.dir[a], ray.dir[a], dd);
+        }
+        const float inv = 1.0f / sqrtf(dd);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ray.dir[a] *= inv;
+    }
+    // slab test: [t0, t1] inside the box, t0 >= 0
+    float t0 = 0.0f, t1 = INFINITY;
+    bool hit = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (ray.dir[a] == 0.0f) {
+            if (o[a] < rs.box_min[a] || o[a] > rs.box_max[a]) hit = false;
+        } else {
+            float ta = (rs.box_min[a] - o[a]) / ray.dir[a];
+            float tb = (rs.box_max[a] - o[a]) / ray.dir[a];
+            if (ta > tb) { const float s = ta; ta = tb; tb = s; }
+            t0 = fmaxf(t0, ta);
+            t1 = fminf(t1, tb);
+        }
+    }
+    ray.nsf = (hit && t1 > t0) ? floorf((t1 - t0) / rs.step) : 0.0f;
+    if (ray.nsf < 1.0f) {
+        rs.out[ray.pix] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (rs.nsamples) rs.nsamples[ray.pix] = 0;
+        return false;
+    }
+    const float tm = fmaf(0.5f, rs.step, t0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ray.X0[a] = (fmaf(tm, ray.dir[a], o[a]) - rs.box_min[a]) * rs.lat_scale[a];
+        ray.dX[a] = rs.step * ray.dir[a] * rs.lat_scale[a];
+        ray.kf[a] = -2.0f;  // forces a span lookup at the first sample
+    }
+    ray.sf = 0.f;
+    ray.Cr = ray.Cg = ray.Cb = ray.A = 0.f;
+    return true;
+}
+
+// Transfer-function lookups: `TfShared` reads (entry, next - entry) pairs the
+// kernel staged in shared memory; `TfGlobal` reads two entries of the
+// caller's table through the read-only cache.
+struct TfShared {
+    const float4 *t;
+    __device__ __forceinline__ void at(int i, float4 &a, float4 &d) const
+    {
+        a = t[2 * i];
+        d = t[2 * i + 1];
+    }
+};
+struct TfGlobal {
+    const float4 *t;
+    __device__ __forceinline__ void at(int i, float4 &a, float4 &d) const
+    {
+        a = __ldg(t + i);
+        const float4 b = __ldg(t + i + 1);
+        d = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
+    }
+};
+
+// One sample of the lane's ray: span bookkeeping (and a cache reload when the
+// span changed), basis, contraction, applyTFs, shading, compositing, early
+// termination.  Returns true when the ray is finished (pixel written).
+template <int P, typename T, typename Tf>
+__device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSetup &rs, const Tf &tf, LaneRay &ray,
+                                            SpanCache<P> &cache)
+{
+    constexpr int JP = Block<P>::JP;
+    constexpr bool kCache = SpanCache<P>::kOn;
+    float X[3], x[3];
+    bool moved = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float mfa = static_cast<float>(mv.m[a]);
+        X[a] = fminf(fmaxf(fmaf(ray.sf, ray.dX[a], ray.X0[a]), 0.0f), mfa);
+        x[a] = X[a] - ray.kf[a];
+        moved |= (x[a] < 0.0f) | (x[a] >= 1.0f);
+    }
+    if (moved) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            ray.kf[a] = fminf(floorf(X[a]), static_cast<float>(mv.m[a]) - 1.0f);
+            x[a] = X[a] - ray.kf[a];
+            ray.kk[a] = static_cast<int>(ray.kf[a]);
+        }
+        ray.base = ray.kk[0] + mv.n[0] * ray.kk[1] + mv.n01 * ray.kk[2];
+        ray.interior = span_interior<P>(ray.kk[0], mv.m[0]) && span_interior<P>(ray.kk[1], mv.m[1]) &&
+                       span_interior<P>(ray.kk[2], mv.m[2]);
+        if constexpr (kCache) {
+            float4 q[P + 1][JP][Block<P>::IQ];
+            load_block<P, T>(mv.quads, ray.base, mv.n[0], mv.n01, q);
+#pragma unroll
+            for (int k = 0; k <= P; ++k)
+#pragma unroll
+                for (int jp = 0; jp < JP; ++jp)
+#pragma unroll
+                    for (int i = 0; i <= P; ++i) cache.v[k][jp][i] = quad_pair<P>(q, k, jp, i);
+        }
+    }
+    float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
+    if (ray.interior) {
+        basis_uniform_scaled<P>(x[0], Nu, dNu);
+        basis_uniform_scaled<P>(x[1], Nv, dNv);
+        basis_uniform_scaled<P>(x[2], Nw, dNw);
+    } else {
+        basis<P>(x[0], ray.kk[0], mv.m[0], Nu, dNu);
+        basis<P>(x[1], ray.kk[1], mv.m[1], Nv, dNv);
+        basis<P>(x[2], ray.kk[2], mv.m[2], Nw, dNw);
+    }
+    float r[4];
+    if constexpr (kCache) {
+        contract_pairs<P>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return cache.v[k][jp][i]; }, r);
+    } else {
+        const int n0 = mv.n[0], n01 = mv.n01, base = ray.base;
+        contract_pairs<P>(Nu, dNu, Nv, dNv, Nw, dNw,
+                          [&](int k, int jp, int i) {
+                              const float4 qv = QuadLoad<T>::at(mv.quads, base + (i & ~1) + 2 * jp * n0 + k * n01);
+                              return (i & 1) ? make_float2(qv.z, qv.w) : make_float2(qv.x, qv.y);
+                          },
+                          r);
+    }
+
+    // ---- applyTFs: linear interpolation in the table -----------------------
+    const float xt = fminf(fmaxf(fmaf(r[0], rs.tf_a, rs.tf_b), 0.0f), static_cast<float>(rs.tf_size - 1));
+    const int it = min(static_cast<int>(xt), rs.tf_size - 2);
+    const float fr = xt - static_cast<float>(it);
+    float4 ta, td;
+    tf.at(it, ta, td);
+    float cr = fmaf(fr, td.x, ta.x);
+    float cg = fmaf(fr, td.y, ta.y);
+    float cb = fmaf(fr, td.z, ta.z);
+    float alpha = clamp01f(fmaf(fr, td.w, ta.w));
+    if (rs.correct_opacity) alpha = 1.0f - exp2f(log2f(1.0f - alpha) * rs.opacity_ratio);
+
+    // ---- shading: Blinn-Phong, headlight L = V = -d, two-sided -------------
+    if (rs.shading) {
+        const float gx = r[1] * rs.grad_scale[0];
+        const float gy = r[2] * rs.grad_scale[1];
+        const float gz = r[3] * rs.grad_scale[2];
+        const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+        if (g2 <= rs.gthresh2) {
+            cr *= rs.ka; cg *= rs.ka; cb *= rs.ka;
+        } else {
+            const float ndl =
+                fminf(fabsf(fmaf(gx, ray.dir[0], fmaf(gy, ray.dir[1], gz * ray.dir[2]))) * rsqrtf(g2), 1.0f);
+            const float spec = rs.ks * __powf(ndl, rs.shininess);
+            const float diff = fmaf(rs.kd, ndl, rs.ka);
+            cr = clamp01f(fmaf(cr, diff, spec));
+            cg = clamp01f(fmaf(cg, diff, spec));
+            cb = clamp01f(fmaf(cb, diff, spec));
+        }
+    }
+
+    // ---- front-to-back compositing + early ray termination ----------------
+    const float wgt = (1.0f - ray.A) * alpha;
+    ray.Cr = fmaf(wgt, cr, ray.Cr);
+    ray.Cg = fmaf(wgt, cg, ray.Cg);
+    ray.Cb = fmaf(wgt, cb, ray.Cb);
+    ray.A += wgt;
+    ray.sf += 1.0f;
+    if (ray.A > rs.max_opacity || ray.sf >= ray.nsf) {
+        rs.out[ray.pix] = make_float4(ray.Cr, ray.Cg, ray.Cb, ray.A);
+        if (rs.nsamples) rs.nsamples[ray.pix] = static_cast<int>(ray.sf);
+        return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// One image
+// ---------------------------------------------------------------------------
 template <int P, typename T>
 __global__ void __launch_bounds__(kThreads, MinBlocks<P>::value)
     render_kernel(ModelView mv, RenderSetup rs, int *__restrict__ counter)
@@ -60,33 +285,23 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P>::value)
         s_tf[2 * i + 1] = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
     }
     __syncthreads();
+    const TfShared tf{s_tf};
 
-    constexpr int JP = Block<P>::JP;
-    constexpr bool kCache = CacheCP<P>::value;
     const int lane = threadIdx.x & 31;
     const unsigned lane_lt = (1u << lane) - 1u;
-    const int tiles_x = (rs.width + 7) >> 3;
-    const int total = tiles_x * ((rs.height + 3) >> 2) * 32;  // ray slots, some outside the image
-    const float mf[3] = {static_cast<float>(mv.m[0]), static_cast<float>(mv.m[1]), static_cast<float>(mv.m[2])};
-    const float tf_last = static_cast<float>(rs.tf_size - 1);
+    const int tw_log2 = rs.tile_w_log2;
+    const int tiles_x = (rs.width + (1 << tw_log2) - 1) >> tw_log2;
+    const int tiles_y = (rs.height + (32 >> tw_log2) - 1) >> (5 - tw_log2);
+    const int total = tiles_x * tiles_y * 32;  // ray slots, some outside the image
 
     int pool_next = 0, pool_end = 0;
     bool exhausted = false;
     bool idle = true;
-
-    // state of the lane's ray
-    int pix = 0;
-    float X0[3], dX[3], dir[3];
-    float kf[3];
-    int kk[3];
-    int base = 0;
-    bool interior = false;  // all three spans unclamped: uniform pieces apply
-    float sf = 0.f, nsf = 0.f;
-    float Cr = 0.f, Cg = 0.f, Cb = 0.f, A = 0.f;
-    float2 cache[kCache ? (P + 1) : 1][kCache ? JP : 1][kCache ? (P + 1) : 1];
+    LaneRay ray;
+    SpanCache<P> cache;
 
     for (;;) {
-        // ---- hand rays to idle lanes ------------------------------------
+        // ---- hand rays to idle lanes ----------------------------------------
         const unsigned need = __ballot_sync(kFull, idle);
         if (need) {
             if (pool_next >= pool_end && !exhausted) {
@@ -99,169 +314,88 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P>::value)
             const int avail = pool_end - pool_next;
             const int rank = __popc(need & lane_lt);
             if (idle && rank < avail) {
-                const int slot = pool_next + rank;
-                const int tile = slot >> 5, l = slot & 31;
-                const int px = (tile % tiles_x) * 8 + (l & 7);
-                const int py = (tile / tiles_x) * 4 + (l >> 3);
-                if (px < rs.width && py < rs.height) {
-                    pix = py * rs.width + px;
-                    // ray definition
-                    const float sx = fmaf(rs.sx_scale, static_cast<float>(px) + 0.5f, rs.sx_off);
-                    const float sy = fmaf(rs.sy_scale, static_cast<float>(py) + 0.5f, rs.sy_off);
-                    float o[3];
-                    if (rs.kind == 0) {
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            o[a] = fmaf(sy, rs.up[a], fmaf(sx, rs.right[a], rs.eye[a]));
-                            dir[a] = rs.fwd[a];
-                        }
-                    } else {
-                        float dd = 0.f;
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            o[a] = rs.eye[a];
-                            dir[a] = fmaf(sy, rs.up[a], fmaf(sx, rs.right[a], rs.fwd[a]));
-                            dd = fmaf(dir[a], dir[a], dd);
-                        }
-                        const float inv = 1.0f / sqrtf(dd);
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) dir[a] *= inv;
-                    }
-                    // slab test: [t0, t1] inside the box, t0 >= 0
-                    float t0 = 0.0f, t1 = INFINITY;
-                    bool hit = true;
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        if (dir[a] == 0.0f) {
-                            if (o[a] < rs.box_min[a] || o[a] > rs.box_max[a]) hit = false;
-                        } else {
-                            float ta = (rs.box_min[a] - o[a]) / dir[a];
-                            float tb = (rs.box_max[a] - o[a]) / dir[a];
-                            if (ta > tb) { const float s = ta; ta = tb; tb = s; }
-                            t0 = fmaxf(t0, ta);
-                            t1 = fminf(t1, tb);
-                        }
-                    }
-                    nsf = (hit && t1 > t0) ? floorf((t1 - t0) / rs.step) : 0.0f;
-                    if (nsf >= 1.0f) {
-                        // sample s sits at lattice coordinates X0 + s * dX
-                        const float tm = fmaf(0.5f, rs.step, t0);
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            X0[a] = (fmaf(tm, dir[a], o[a]) - rs.box_min[a]) * rs.lat_scale[a];
-                            dX[a] = rs.step * dir[a] * rs.lat_scale[a];
-                            kf[a] = -2.0f;  // forces a span lookup at the first sample
-                        }
-                        sf = 0.f;
-                        Cr = Cg = Cb = A = 0.f;
-                        idle = false;
-                    } else {
-                        rs.out[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (rs.nsamples) rs.nsamples[pix] = 0;
-                    }
-                }
+                int px, py;
+                slot_pixel(pool_next + rank, tiles_x, tw_log2, px, py);
+                if (px < rs.width && py < rs.height) idle = !start_ray(rs, px, py, ray);
             }
             pool_next += min(avail, __popc(need));
             if (exhausted && __all_sync(kFull, idle)) break;
         }
         if (idle) continue;
-
-        // ---- one sample -------------------------------------------------
-        float X[3], x[3];
-        bool moved = false;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            X[a] = fminf(fmaxf(fmaf(sf, dX[a], X0[a]), 0.0f), mf[a]);
-            x[a] = X[a] - kf[a];
-            moved |= (x[a] < 0.0f) | (x[a] >= 1.0f);
-        }
-        if (moved) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                kf[a] = fminf(floorf(X[a]), mf[a] - 1.0f);
-                x[a] = X[a] - kf[a];
-                kk[a] = static_cast<int>(kf[a]);
-            }
-            base = kk[0] + mv.n[0] * kk[1] + mv.n01 * kk[2];
-            interior = span_interior<P>(kk[0], mv.m[0]) && span_interior<P>(kk[1], mv.m[1]) &&
-                       span_interior<P>(kk[2], mv.m[2]);
-            if constexpr (kCache) {
-                float4 q[P + 1][JP][Block<P>::IQ];
-                load_block<P, T>(mv.quads, base, mv.n[0], mv.n01, q);
-#pragma unroll
-                for (int k = 0; k <= P; ++k)
-#pragma unroll
-                    for (int jp = 0; jp < JP; ++jp)
-#pragma unroll
-                        for (int i = 0; i <= P; ++i) cache[k][jp][i] = quad_pair<P>(q, k, jp, i);
-            }
-        }
-        float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
-        if (interior) {
-            basis_uniform_scaled<P>(x[0], Nu, dNu);
-            basis_uniform_scaled<P>(x[1], Nv, dNv);
-            basis_uniform_scaled<P>(x[2], Nw, dNw);
-        } else {
-            basis<P>(x[0], kk[0], mv.m[0], Nu, dNu);
-            basis<P>(x[1], kk[1], mv.m[1], Nv, dNv);
-            basis<P>(x[2], kk[2], mv.m[2], Nw, dNw);
-        }
-        float r[4];
-        if constexpr (kCache) {
-            contract_pairs<P>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return cache[k][jp][i]; }, r);
-        } else {
-            const int n0 = mv.n[0], n01 = mv.n01;
-            contract_pairs<P>(Nu, dNu, Nv, dNv, Nw, dNw,
-                              [&](int k, int jp, int i) {
-                                  const float4 qv = QuadLoad<T>::at(mv.quads, base + (i & ~1) + 2 * jp * n0 + k * n01);
-                                  return (i & 1) ? make_float2(qv.z, qv.w) : make_float2(qv.x, qv.y);
-                              },
-                              r);
-        }
-
-        // ---- applyTFs: linear interpolation in the table ---------------
-        const float xt = fminf(fmaxf(fmaf(r[0], rs.tf_a, rs.tf_b), 0.0f), tf_last);
-        const int it = min(static_cast<int>(xt), rs.tf_size - 2);
-        const float fr = xt - static_cast<float>(it);
-        const float4 ta = s_tf[2 * it], td = s_tf[2 * it + 1];
-        float cr = fmaf(fr, td.x, ta.x);
-        float cg = fmaf(fr, td.y, ta.y);
-        float cb = fmaf(fr, td.z, ta.z);
-        float alpha = clamp01f(fmaf(fr, td.w, ta.w));
-        if (rs.correct_opacity) alpha = 1.0f - exp2f(log2f(1.0f - alpha) * rs.opacity_ratio);
-
-        // ---- shading: Blinn-Phong, headlight L = V = -d, two-sided -----
-        if (rs.shading) {
-            const float gx = r[1] * rs.grad_scale[0];
-            const float gy = r[2] * rs.grad_scale[1];
-            const float gz = r[3] * rs.grad_scale[2];
-            const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-            if (g2 <= rs.gthresh2) {
-                cr *= rs.ka; cg *= rs.ka; cb *= rs.ka;
-            } else {
-                const float ndl =
-                    fminf(fabsf(fmaf(gx, dir[0], fmaf(gy, dir[1], gz * dir[2]))) * rsqrtf(g2), 1.0f);
-                const float spec = rs.ks * __powf(ndl, rs.shininess);
-                const float diff = fmaf(rs.kd, ndl, rs.ka);
-                cr = clamp01f(fmaf(cr, diff, spec));
-                cg = clamp01f(fmaf(cg, diff, spec));
-                cb = clamp01f(fmaf(cb, diff, spec));
-            }
-        }
-
-        // ---- front-to-back compositing + early ray termination ----------
-        const float wgt = (1.0f - A) * alpha;
-        Cr = fmaf(wgt, cr, Cr);
-        Cg = fmaf(wgt, cg, Cg);
-        Cb = fmaf(wgt, cb, Cb);
-        A += wgt;
-        sf += 1.0f;
-        if (A > rs.max_opacity || sf >= nsf) {
-            rs.out[pix] = make_float4(Cr, Cg, Cb, A);
-            if (rs.nsamples) rs.nsamples[pix] = static_cast<int>(sf);
-            idle = true;
-        }
+        if (sample_step<P, T>(mv, rs, tf, ray, cache)) idle = true;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Many images (render jobs) of one degree and storage type
+// ---------------------------------------------------------------------------
+template <int P, typename T>
+__global__ void __launch_bounds__(kThreads, MinBlocks<P>::value)
+    render_batch_kernel(const RenderJob *__restrict__ jobs, int njobs, int total_tiles, int *__restrict__ counter)
+{
+    __shared__ RenderJob s_job[kWarps];  // the current job of each warp
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lane_lt = (1u << lane) - 1u;
+    RenderJob &J = s_job[warp];
+
+    int cur = -1;   // current job
+    int held = -1;  // a fetched tile not yet handed out
+    int pool_next = 0, pool_end = 0;
+    bool exhausted = false;
+    bool idle = true;
+    LaneRay ray;
+    SpanCache<P> cache;
+
+    for (;;) {
+        const unsigned need = __ballot_sync(kFull, idle);
+        if (need) {
+            if (pool_next >= pool_end && held < 0 && !exhausted) {
+                int t = 0;
+                if (lane == 0) t = atomicAdd(counter, 1);
+                t = __shfl_sync(kFull, t, 0);
+                if (t >= total_tiles) exhausted = true;
+                else held = t;
+            }
+            if (held >= 0 && pool_next >= pool_end) {
+                // the job owning the tile: jobs are sorted by tile_begin
+                int j = 0;
+                while (j + 1 < njobs && __ldg(&jobs[j + 1].tile_begin) <= held) ++j;
+                if (j != cur && need == kFull) {
+                    // all lanes idle: take the new job's model and settings
+                    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(jobs + j);
+                    unsigned long long *dst = reinterpret_cast<unsigned long long *>(&J);
+                    for (int w = lane; w < static_cast<int>(sizeof(RenderJob) / 8); w += 32) dst[w] = src[w];
+                    __syncwarp();
+                    cur = j;
+                }
+                if (j == cur) {
+                    pool_next = (held - J.tile_begin) * 32;
+                    pool_end = pool_next + 32;
+                    held = -1;
+                }
+            }
+            const int avail = pool_end - pool_next;
+            const int rank = __popc(need & lane_lt);
+            if (idle && rank < avail) {
+                int px, py;
+                slot_pixel(pool_next + rank, J.tiles_x, J.rs.tile_w_log2, px, py);
+                if (px < J.rs.width && py < J.rs.height) idle = !start_ray(J.rs, px, py, ray);
+            }
+            pool_next += min(avail, __popc(need));
+            if (exhausted && held < 0 && __all_sync(kFull, idle)) break;
+        }
+        if (idle) continue;
+        const TfGlobal tf{J.rs.tf};
+        if (sample_step<P, T>(J.mv, J.rs, tf, ray, cache)) idle = true;
+    }
+}
+
+int sm_count()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
 }
 
 template <int P, typename T>
@@ -273,16 +407,16 @@ cudaError_t launch_render_t(const ModelView &mv, const RenderSetup &rs, int *cou
                                              static_cast<int>(smem));
         if (e != cudaSuccess) return e;
     }
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<P, T>, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
+    if (rs.ctas_per_sm > 0 && rs.ctas_per_sm < per_sm) per_sm = rs.ctas_per_sm;
     // no more warps than ray tiles
-    const int64_t tiles = static_cast<int64_t>((rs.width + 7) / 8) * ((rs.height + 3) / 4);
-    int64_t blocks = static_cast<int64_t>(sms) * per_sm;
-    const int64_t need = (tiles + (kThreads / 32) - 1) / (kThreads / 32);
+    const int tw = 1 << rs.tile_w_log2, th = 32 / tw;
+    const int64_t tiles = static_cast<int64_t>((rs.width + tw - 1) / tw) * ((rs.height + th - 1) / th);
+    int64_t blocks = static_cast<int64_t>(sm_count()) * per_sm;
+    const int64_t need = (tiles + kWarps - 1) / kWarps;
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
     if (e != cudaSuccess) return e;
@@ -290,29 +424,74 @@ cudaError_t launch_render_t(const ModelView &mv, const RenderSetup &rs, int *cou
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_render_dtype(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream)
+template <int P, typename T>
+cudaError_t launch_batch_t(const RenderJob *jobs, int njobs, int total_tiles, int ctas_per_sm, int *counter,
+                           cudaStream_t stream)
 {
-    switch (mv.p) {
-    case 1: return launch_render_t<1, T>(mv, rs, counter, stream);
-    case 2: return launch_render_t<2, T>(mv, rs, counter, stream);
-    case 3: return launch_render_t<3, T>(mv, rs, counter, stream);
-    case 4: return launch_render_t<4, T>(mv, rs, counter, stream);
-    case 5: return launch_render_t<5, T>(mv, rs, counter, stream);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_batch_kernel<P, T>, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    int64_t blocks = static_cast<int64_t>(sm_count()) * per_sm;
+    const int64_t need = (static_cast<int64_t>(total_tiles) + kWarps - 1) / kWarps;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) return cudaSuccess;
+    e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return e;
+    render_batch_kernel<P, T><<<static_cast<int>(blocks), kThreads, 0, stream>>>(jobs, njobs, total_tiles, counter);
+    return cudaGetLastError();
+}
+
+template <int P, typename T>
+struct RenderOne {
+    static cudaError_t run(const ModelView *mv, const RenderSetup *rs, int *counter, cudaStream_t s)
+    {
+        return launch_render_t<P, T>(*mv, *rs, counter, s);
+    }
+};
+template <int P, typename T>
+struct RenderBatch {
+    static cudaError_t run(const RenderJob *jobs, int njobs, int total_tiles, int ctas_per_sm, int *counter,
+                           cudaStream_t s)
+    {
+        return launch_batch_t<P, T>(jobs, njobs, total_tiles, ctas_per_sm, counter, s);
+    }
+};
+
+// Instantiates F<P, T>::run for the model's degree and storage type.
+template <template <int, typename> class F, typename... A>
+cudaError_t dispatch(int p, int dtype, A... args)
+{
+#define MFADVR_DTYPE_CASES(PP)                                   \
+    switch (dtype) {                                             \
+    case MFADVR_F32: return F<PP, float>::run(args...);          \
+    case MFADVR_F16: return F<PP, __half>::run(args...);         \
+    case MFADVR_BF16: return F<PP, __nv_bfloat16>::run(args...); \
+    default: return cudaErrorInvalidValue;                       \
+    }
+    switch (p) {
+    case 1: MFADVR_DTYPE_CASES(1)
+    case 2: MFADVR_DTYPE_CASES(2)
+    case 3: MFADVR_DTYPE_CASES(3)
+    case 4: MFADVR_DTYPE_CASES(4)
+    case 5: MFADVR_DTYPE_CASES(5)
     default: return cudaErrorInvalidValue;
     }
+#undef MFADVR_DTYPE_CASES
 }
 
 }  // namespace
 
 cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream)
 {
-    switch (mv.dtype) {
-    case MFADVR_F32: return launch_render_dtype<float>(mv, rs, counter, stream);
-    case MFADVR_F16: return launch_render_dtype<__half>(mv, rs, counter, stream);
-    case MFADVR_BF16: return launch_render_dtype<__nv_bfloat16>(mv, rs, counter, stream);
-    default: return cudaErrorInvalidValue;
-    }
+    return dispatch<RenderOne>(mv.p, mv.dtype, &mv, &rs, counter, stream);
+}
+
+cudaError_t launch_render_batch(int p, int dtype, const RenderJob *jobs_dev, int njobs, int total_tiles,
+                                int ctas_per_sm, int *counter, cudaStream_t stream)
+{
+    return dispatch<RenderBatch>(p, dtype, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, stream);
 }
 
 }  // namespace mfadvr

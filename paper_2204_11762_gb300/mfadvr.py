@@ -28,7 +28,9 @@ MAX_TF_SIZE = 4096
 # Every symbol include/mfadvr.h declares.
 EXPORTS = ("mfadvr_create", "mfadvr_destroy", "mfadvr_load_model", "mfadvr_unload_model", "mfadvr_model_info",
            "mfadvr_eval_points", "mfadvr_eval_points_host", "mfadvr_render", "mfadvr_render_host",
-           "mfadvr_status_string", "mfadvr_last_error", "mfadvr_render_lattice_noalloc")
+           "mfadvr_status_string", "mfadvr_last_error", "mfadvr_render_lattice_noalloc", "mfadvr_render_batch",
+           "mfadvr_autotune", "mfadvr_tuning_save", "mfadvr_tuning_load")
+MAX_BATCH = 256
 NOALLOC_MAX_POINTS = 1 << 19
 
 
@@ -55,6 +57,15 @@ class RenderParams(ctypes.Structure):
                 ("tf_size", ctypes.c_int32), ("tf_lo", ctypes.c_float), ("tf_hi", ctypes.c_float),
                 ("shading", ctypes.c_int32), ("ka", ctypes.c_float), ("kd", ctypes.c_float),
                 ("ks", ctypes.c_float), ("shininess", ctypes.c_float)]
+
+
+class RenderJob(ctypes.Structure):
+    _fields_ = [("model_id", ctypes.c_int32), ("camera", Camera), ("params", RenderParams),
+                ("rgba_dev", ctypes.c_void_p), ("nsamples_dev", ctypes.c_void_p)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 _lib = None
@@ -88,6 +99,14 @@ def load_library(build_if_missing: bool = True):
         fn = getattr(L, name)
         fn.argtypes = args
         fn.restype = i32
+    L.mfadvr_render_batch.argtypes = [vp, i32, P(RenderJob), vp]
+    L.mfadvr_render_batch.restype = i32
+    L.mfadvr_autotune.argtypes = [vp, i32, P(Camera), P(RenderParams), vp, vp, vp, P(Tuning)]
+    L.mfadvr_autotune.restype = i32
+    L.mfadvr_tuning_save.argtypes = [vp, ctypes.c_char_p]
+    L.mfadvr_tuning_save.restype = i32
+    L.mfadvr_tuning_load.argtypes = [vp, ctypes.c_char_p]
+    L.mfadvr_tuning_load.restype = i32
     f3, i3 = ctypes.c_float * 3, ctypes.c_int32 * 3
     L.mfadvr_render_lattice_noalloc.argtypes = [vp, P(i3), P(i3), P(f3), P(f3), P(Camera), P(RenderParams),
                                                 vp, vp, vp]
@@ -270,3 +289,31 @@ class Context:
         self._check(self._L.mfadvr_render_host(self._h, int(model_id), ctypes.byref(cam), ctypes.byref(prm),
                                                _ptr(rgba), _ptr(nsamples), _stream(stream)))
         return rgba
+
+    # -- batches and tuning -----------------------------------------------
+    def render_batch(self, jobs, stream=None):
+        """jobs: dicts with model_id, camera, params, tf_dev, tf_size,
+        rgba_dev and optionally nsamples_dev (mfadvr_render_batch)."""
+        arr = (RenderJob * len(jobs))()
+        for k, j in enumerate(jobs):
+            arr[k].model_id = int(j["model_id"])
+            arr[k].camera = make_camera(j["camera"])
+            arr[k].params = make_params(j["params"], _ptr(j["tf_dev"]), j["tf_size"])
+            arr[k].rgba_dev = _ptr(j["rgba_dev"])
+            arr[k].nsamples_dev = _ptr(j.get("nsamples_dev"))
+        self._check(self._L.mfadvr_render_batch(self._h, len(jobs), arr, _stream(stream)))
+
+    def autotune(self, model_id, camera: dict, params: dict, tf_dev, tf_size, rgba_dev, nsamples_dev=None,
+                 stream=None) -> dict:
+        cam = make_camera(camera)
+        prm = make_params(params, _ptr(tf_dev), tf_size)
+        t = Tuning()
+        self._check(self._L.mfadvr_autotune(self._h, int(model_id), ctypes.byref(cam), ctypes.byref(prm),
+                                            _ptr(rgba_dev), _ptr(nsamples_dev), _stream(stream), ctypes.byref(t)))
+        return {"tile_w": t.tile_w, "ctas_per_sm": t.ctas_per_sm, "ms": t.ms}
+
+    def tuning_save(self, path: str):
+        self._check(self._L.mfadvr_tuning_save(self._h, os.fsencode(path)))
+
+    def tuning_load(self, path: str):
+        self._check(self._L.mfadvr_tuning_load(self._h, os.fsencode(path)))

@@ -72,6 +72,8 @@ int main(void) {
          offsetof(mfadvr_model_desc, storage), sizeof(mfadvr_camera));
   printf("%zu %zu %zu\n", sizeof(mfadvr_render_params), offsetof(mfadvr_render_params, tf_rgba),
          offsetof(mfadvr_render_params, shininess));
+  printf("%zu %zu %zu %zu\n", sizeof(mfadvr_render_job), offsetof(mfadvr_render_job, params),
+         offsetof(mfadvr_render_job, rgba_dev), sizeof(mfadvr_tuning));
   return 0;
 }
 '''
@@ -82,7 +84,8 @@ int main(void) {
         subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         out = subprocess.check_output([exe]).decode().split()
     got = [int(x) for x in out]
-    M, Cm, R = mfadvr.ModelDesc, mfadvr.Camera, mfadvr.RenderParams
+    M, Cm, R, J = mfadvr.ModelDesc, mfadvr.Camera, mfadvr.RenderParams, mfadvr.RenderJob
     exp = [ctypes.sizeof(M), M.ctrl.offset, M.storage.offset, ctypes.sizeof(Cm),
-           ctypes.sizeof(R), R.tf_rgba.offset, R.shininess.offset]
+           ctypes.sizeof(R), R.tf_rgba.offset, R.shininess.offset,
+           ctypes.sizeof(J), J.params.offset, J.rgba_dev.offset, ctypes.sizeof(mfadvr.Tuning)]
     assert got == exp
