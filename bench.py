@@ -47,9 +47,10 @@ def _args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
-    ap.add_argument("--workload", default="gauss128", choices=["gauss128", "noise512"],
+    ap.add_argument("--workload", default="gauss128", choices=["gauss128", "noise512", "multi16"],
                     help="gauss128: 128^3 degree-3 render + 2^24 points (default); "
-                         "noise512: 512^3 degree-4 render at 3840x2160")
+                         "noise512: 512^3 degree-4 render at 3840x2160; "
+                         "multi16: one batched render of 16 models of degree 2-5")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 16-bit storage comparison")
@@ -459,6 +460,100 @@ def run_noise512(args, wl):
         dist.destroy_process_group()
 
 
+def run_multi16(args, jobs):
+    """One mfadvr_render_batch call over 16 models (degrees 2-5, lattices
+    64..256 per axis, images 512^2..2048^2), launch shapes from the
+    autotuner, under FP32, FP16 and BF16 storage; errors against the FP64
+    oracle on bounded samples (4096 points per model for value/gradient,
+    every 128th row of every image for pixels)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2204_11762_gb300 import mfadvr
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    steps = max(3, min(args.steps, 20))
+    rng = np.random.default_rng(7)
+    pts = [rng.uniform(0, 1, size=(4096, 3)).astype(np.float32) for _ in jobs]
+    ref_eval, ref_img = [], []
+    for j, pp in zip(jobs, pts):
+        r, _ = oracle.eval_points(j["ctrl"], j["degree"], pp)
+        ref_eval.append(r)
+        ref_img.append(oracle.render(j["ctrl"], j["degree"], j["camera"], dict(j["params"], tf=j["tf"]),
+                                     row_step=128))
+    results = {}
+    for st in ("f32", "f16", "bf16"):
+        ctx = mfadvr.Context(local)
+        batch, tunes = [], []
+        for j in jobs:
+            W, H = j["params"]["width"], j["params"]["height"]
+            mid = ctx.load_model(j["ctrl"], j["degree"], storage=st)
+            e = {"model_id": mid, "camera": j["camera"], "params": j["params"],
+                 "tf_dev": torch.from_numpy(j["tf"]).to(dev), "tf_size": j["tf"].shape[0],
+                 "rgba_dev": torch.empty((H, W, 4), device=dev),
+                 "nsamples_dev": torch.empty((H, W), dtype=torch.int32, device=dev)}
+            tunes.append(ctx.autotune(mid, e["camera"], e["params"], e["tf_dev"], e["tf_size"], e["rgba_dev"],
+                                      e["nsamples_dev"], stream=stream))
+            batch.append(e)
+        for _ in range(3):
+            flush.zero_()
+            ctx.render_batch(batch, stream=stream)
+        torch.cuda.synchronize(dev)
+        samples = sum(int(e["nsamples_dev"].sum(dtype=torch.int64).item()) for e in batch)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            ctx.render_batch(batch, stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        # errors against the FP64 oracle of the FP32 lattice
+        verr, gerr, perr = [], [], []
+        for j, e, pp, r, ri in zip(jobs, batch, pts, ref_eval, ref_img):
+            d_p = torch.from_numpy(pp).to(dev)
+            d_o = torch.empty((pp.shape[0], 4), device=dev)
+            ctx.eval_points(e["model_id"], d_p, pp.shape[0], d_o, None, stream=stream)
+            torch.cuda.synchronize(dev)
+            got = d_o.cpu().numpy().astype(np.float64)
+            pabs = float(np.abs(j["ctrl"]).max())
+            m = max(int(x) - j["degree"] for x in j["ncp"])
+            verr.append(np.abs(got[:, 0] - r[:, 0]) / pabs)
+            gerr.append(np.abs(got[:, 1:] - r[:, 1:]).max(axis=1) / (pabs * m))
+            img = e["rgba_dev"].cpu().numpy()[::128]
+            perr.append(np.abs(img - ri["rgba"][::128]).max(axis=-1).ravel())
+        v, g, px = np.concatenate(verr), np.concatenate(gerr), np.concatenate(perr)
+        results[st] = {"samples": samples, "ms_mean": statistics.mean(ms), "ms_p50": statistics.median(ms),
+                       "samples_per_s": samples / (statistics.mean(ms) / 1000.0),
+                       "err_value": {"max": float(v.max()), "rms": float(np.sqrt((v ** 2).mean()))},
+                       "err_grad": {"max": float(g.max()), "rms": float(np.sqrt((g ** 2).mean()))},
+                       "err_pixel": {"max": float(px.max()), "rms": float(np.sqrt((px ** 2).mean()))},
+                       "tuning": [f"{t['tile_w']}x{32 // t['tile_w']}/{t['ctas_per_sm']}" for t in tunes]}
+        ctx.close()
+        del batch
+    f32 = results["f32"]
+    line = {"metric": METRIC, "value": f32["samples_per_s"], "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": 3, "ms_per_step": f32["ms_mean"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "multi16: one batched render of 16 models (degree 2-5, lattices 64..256 per "
+                                   "axis, Gaussian sums), images 512^2..2048^2, step 1/1024, autotuned shapes",
+                       "models": [f"p{j['degree']} {j['ncp'][0]}x{j['ncp'][1]}x{j['ncp'][2]} "
+                                  f"{j['params']['width']}^2" for j in jobs],
+                       "errors": "value/|P|max, gradient/(|P|max m), pixel abs; vs FP64 oracle of the FP32 "
+                                 "lattice; 4096 points per model, every 128th row"},
+            "gpu_launches": 4 * steps, "storage": results,
+            "mixed_precision": {st: {"samples_per_s": results[st]["samples_per_s"],
+                                     "vs_f32": results[st]["samples_per_s"] / f32["samples_per_s"]}
+                                for st in ("f16", "bf16")}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     from paper_2204_11762_gb300 import workloads
@@ -468,6 +563,13 @@ def main():
                                                                    "default workload only"}))
             return
         run_noise512(args, workloads.value_noise_workload(512))
+        return
+    if args.workload == "multi16":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm is timed on the "
+                                                                   "default workload only"}))
+            return
+        run_multi16(args, workloads.multi_model_workload())
         return
     wl = workloads.gaussian_sum_workload()
     if args.impl == "reference":

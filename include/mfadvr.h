@@ -218,6 +218,44 @@ MFADVR_API mfadvr_status mfadvr_autotune(mfadvr_ctx *ctx, int32_t model_id, cons
 MFADVR_API mfadvr_status mfadvr_tuning_save(mfadvr_ctx *ctx, const char *path);
 MFADVR_API mfadvr_status mfadvr_tuning_load(mfadvr_ctx *ctx, const char *path);
 
+/* ---- Serving: continuous batching ---------------------------------------
+ * A serving loop (one host thread per context) takes render requests at any
+ * time and keeps the GPU busy with them: each scheduling step admits the
+ * oldest queued requests while their output images fit the frame-buffer
+ * budget (and the batch and in-flight limits), packs them into one batched
+ * launch per degree and storage type (as mfadvr_render_batch), replays that
+ * launch sequence through a CUDA graph kept per group signature and stream,
+ * and marks the requests done when the batch completes.  Requests arriving
+ * while batches run join the next step, on another stream, so their work
+ * overlaps the batches in flight.  Each image equals mfadvr_render of its
+ * job.  While the loop runs, call only mfadvr_submit / mfadvr_wait /
+ * mfadvr_serve_stats / mfadvr_serve_stop on the context, from any threads;
+ * models must stay loaded until their requests are done. */
+typedef struct {
+    uint64_t frame_budget_bytes; /* output bytes (rgba + nsamples) in flight; 0: 1 GiB.
+                                    An idle loop admits one request even if it is larger. */
+    int32_t max_batch;           /* requests per scheduling step, 0..MFADVR_MAX_BATCH (0: 64) */
+    int32_t max_in_flight;       /* batches on the GPU at once, 0..8 (0: 2) */
+} mfadvr_serve_config;
+
+/* Start the serving loop.  EBUSY if it runs already. */
+MFADVR_API mfadvr_status mfadvr_serve_start(mfadvr_ctx *ctx, const mfadvr_serve_config *config);
+/* Finish every queued and running request, then stop the loop. */
+MFADVR_API mfadvr_status mfadvr_serve_stop(mfadvr_ctx *ctx);
+/* Queue one render request (validated now, as mfadvr_render_batch does per
+ * job); *ticket identifies it.  The job's buffers must stay valid until the
+ * request is done. */
+MFADVR_API mfadvr_status mfadvr_submit(mfadvr_ctx *ctx, const mfadvr_render_job *job, uint64_t *ticket);
+/* Wait until the request is done: timeout_us < 0 waits without limit, 0
+ * polls.  On MFADVR_OK the ticket is released and *latency_us (may be NULL)
+ * holds the time from submission to the completion of its batch.
+ * ETIMEOUT: not done yet (the ticket stays valid).  ENOTFOUND: unknown or
+ * already released ticket.  ECUDA: its batch failed on the GPU. */
+MFADVR_API mfadvr_status mfadvr_wait(mfadvr_ctx *ctx, uint64_t ticket, int64_t timeout_us, int64_t *latency_us);
+/* Counters of the loop: batched launches, graph updates, graph instantiations. */
+MFADVR_API mfadvr_status mfadvr_serve_stats(mfadvr_ctx *ctx, uint64_t *launches, uint64_t *graph_updates,
+                                            uint64_t *graph_instantiations);
+
 /* ---- Allocation-free render -------------------------------------------
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory during a render.  Examples are code recording

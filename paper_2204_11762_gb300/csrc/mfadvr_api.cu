@@ -12,77 +12,22 @@
 #include <tuple>
 #include <vector>
 
+#include "ctx.h"
 #include "mfa_internal.h"
 #include "mfadvr.h"
 
 using namespace mfadvr;
+using namespace mfadvr::api;
 
 namespace {
-
-struct Model {
-    void *d_quads = nullptr;  // quad layout, see mfa_basis.cuh
-    uint64_t bytes = 0;
-    int p = 0;
-    int n[3] = {0, 0, 0};
-    int dtype = MFADVR_F32;
-    float scale = 1.0f;
-    float pmin = 0.0f, pmax = 0.0f, pabs = 0.0f;
-    float box_min[3] = {0, 0, 0}, box_max[3] = {1, 1, 1};
-};
-
-// Device buffer owned by the context, grown on demand (host-buffer calls).
-struct Staging {
-    void *ptr = nullptr;
-    size_t bytes = 0;
-    cudaError_t reserve(size_t need)
-    {
-        if (need <= bytes) return cudaSuccess;
-        if (ptr) cudaFree(ptr);
-        ptr = nullptr;
-        bytes = 0;
-        cudaError_t e = cudaMalloc(&ptr, need);
-        if (e == cudaSuccess) bytes = need;
-        return e;
-    }
-    void release()
-    {
-        if (ptr) cudaFree(ptr);
-        ptr = nullptr;
-        bytes = 0;
-    }
-};
 
 std::mutex g_create_mu;
 std::string g_create_err;
 
 }  // namespace
 
-// Tuning-table key: degree, storage type, log2 of the lattice size and of
-// the image size.
-using TuneKey = std::tuple<int, int, int, int>;
-
-struct mfadvr_ctx {
-    int device = 0;
-    uint64_t budget = 0, used = 0;
-    std::map<int32_t, Model> models;
-    int32_t next_id = 0;
-    std::string err;
-    Staging st_in, st_out, st_aux;
-    // Ray-tile counters of render launches: each call takes the next slot of
-    // the ring, so calls queued on different streams do not share one.
-    int *counters = nullptr;
-    unsigned next_counter = 0;
-    static constexpr unsigned kCounters = 1024;
-    // Batched renders: a ring of job tables (pinned host + device), each
-    // slot guarded by an event recorded after the launches that read it.
-    static constexpr unsigned kJobSlots = 32;
-    mfadvr::RenderJob *h_jobs = nullptr, *d_jobs = nullptr;
-    cudaEvent_t job_done[kJobSlots] = {};
-    unsigned next_jobs = 0;
-    std::map<TuneKey, mfadvr_tuning> tuning;
-};
-
-namespace {
+namespace mfadvr {
+namespace api {
 
 mfadvr_status fail(mfadvr_ctx *ctx, mfadvr_status st, const char *fmt, ...)
 {
@@ -103,22 +48,6 @@ mfadvr_status cuda_fail(mfadvr_ctx *ctx, cudaError_t e, const char *what)
 {
     return fail(ctx, MFADVR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
-
-// Makes ctx->device current for the duration of a call and restores the
-// caller's device afterwards.
-struct DeviceGuard {
-    int prev = -1;
-    cudaError_t err = cudaSuccess;
-    explicit DeviceGuard(int dev)
-    {
-        err = cudaGetDevice(&prev);
-        if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
-    }
-    ~DeviceGuard()
-    {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
 // True for device or managed memory; host pointers (registered or not) and
 // foreign pointers are refused before any launch reads them.
@@ -324,6 +253,53 @@ TuneKey tune_key(const Model &m, int width, int height)
 }
 
 // Launch shape from the tuning table, if this key has been tuned.
+mfadvr_status make_job(mfadvr_ctx *ctx, const mfadvr_render_job &jb, int index, RenderJob *out)
+{
+    Model *m = nullptr;
+    if (mfadvr_status st = find_model(ctx, jb.model_id, &m)) return st;
+    RenderSetup &rs = out->rs;
+    if (mfadvr_status st = make_setup(ctx, *m, &jb.camera, &jb.params, &rs)) return st;
+    apply_tuning(ctx, *m, &rs);
+    if (jb.params.tf_size < 2 || reinterpret_cast<uintptr_t>(jb.params.tf_rgba) % 16 != 0)
+        return fail(ctx, MFADVR_EINVAL, "job %d: tf_rgba must be 16-byte aligned with tf_size >= 2", index);
+    if (!jb.rgba_dev || reinterpret_cast<uintptr_t>(jb.rgba_dev) % 16 != 0 ||
+        reinterpret_cast<uintptr_t>(jb.nsamples_dev) % 4 != 0)
+        return fail(ctx, MFADVR_EINVAL, "job %d: rgba must be 16-byte and nsamples 4-byte aligned", index);
+    if (!is_device_ptr(jb.rgba_dev) || !is_device_ptr(jb.params.tf_rgba) ||
+        (jb.nsamples_dev && !is_device_ptr(jb.nsamples_dev)))
+        return fail(ctx, MFADVR_EINVAL, "job %d: rgba, tf_rgba and nsamples must be device pointers", index);
+    rs.tf = reinterpret_cast<const float4 *>(jb.params.tf_rgba);
+    rs.out = reinterpret_cast<float4 *>(jb.rgba_dev);
+    rs.nsamples = jb.nsamples_dev;
+    out->mv = view_of(*m);
+    return MFADVR_OK;
+}
+
+std::vector<BatchGroup> pack_jobs(const RenderJob *jobs, int n, RenderJob *dst)
+{
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return std::make_pair(jobs[a].mv.p, jobs[a].mv.dtype) < std::make_pair(jobs[b].mv.p, jobs[b].mv.dtype);
+    });
+    std::vector<BatchGroup> groups;
+    for (int k = 0; k < n; ++k) {
+        RenderJob jb = jobs[order[k]];
+        if (groups.empty() || groups.back().p != jb.mv.p || groups.back().dtype != jb.mv.dtype)
+            groups.push_back({jb.mv.p, jb.mv.dtype, k, 0, 0});
+        BatchGroup &gr = groups.back();
+        const int tw = 1 << jb.rs.tile_w_log2, th = 32 / tw;
+        jb.tiles_x = (jb.rs.width + tw - 1) / tw;
+        jb.tiles = jb.tiles_x * ((jb.rs.height + th - 1) / th);
+        jb.tile_begin = gr.tiles;
+        jb.pad = 0;
+        gr.tiles += jb.tiles;
+        gr.count += 1;
+        dst[k] = jb;
+    }
+    return groups;
+}
+
 void apply_tuning(const mfadvr_ctx *ctx, const Model &m, RenderSetup *rs)
 {
     auto it = ctx->tuning.find(tune_key(m, rs->width, rs->height));
@@ -332,7 +308,8 @@ void apply_tuning(const mfadvr_ctx *ctx, const Model &m, RenderSetup *rs)
     rs->ctas_per_sm = it->second.ctas_per_sm;
 }
 
-}  // namespace
+}  // namespace api
+}  // namespace mfadvr
 
 // Render setup for a lattice that lives outside any context (the
 // allocation-free entry point): FP32 values, scale 1, an explicit TF range,
@@ -377,6 +354,7 @@ mfadvr_status mfadvr_create(mfadvr_ctx **out, int device, uint64_t hbm_budget_by
 mfadvr_status mfadvr_destroy(mfadvr_ctx *ctx)
 {
     if (!ctx) return MFADVR_OK;
+    stop_server(ctx);
     {
         DeviceGuard g(ctx->device);
         cudaDeviceSynchronize();
@@ -622,28 +600,8 @@ mfadvr_status mfadvr_render_batch(mfadvr_ctx *ctx, int32_t njobs, const mfadvr_r
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
     // every argument first, then device work
     std::vector<RenderJob> table(njobs);
-    std::vector<int> order(njobs);
-    for (int i = 0; i < njobs; ++i) {
-        const mfadvr_render_job &jb = jobs[i];
-        Model *m = nullptr;
-        if (mfadvr_status st = find_model(ctx, jb.model_id, &m)) return st;
-        RenderSetup &rs = table[i].rs;
-        if (mfadvr_status st = make_setup(ctx, *m, &jb.camera, &jb.params, &rs)) return st;
-        apply_tuning(ctx, *m, &rs);
-        if (jb.params.tf_size < 2 || reinterpret_cast<uintptr_t>(jb.params.tf_rgba) % 16 != 0)
-            return fail(ctx, MFADVR_EINVAL, "job %d: tf_rgba must be 16-byte aligned with tf_size >= 2", i);
-        if (!jb.rgba_dev || reinterpret_cast<uintptr_t>(jb.rgba_dev) % 16 != 0 ||
-            reinterpret_cast<uintptr_t>(jb.nsamples_dev) % 4 != 0)
-            return fail(ctx, MFADVR_EINVAL, "job %d: rgba must be 16-byte and nsamples 4-byte aligned", i);
-        if (!is_device_ptr(jb.rgba_dev) || !is_device_ptr(jb.params.tf_rgba) ||
-            (jb.nsamples_dev && !is_device_ptr(jb.nsamples_dev)))
-            return fail(ctx, MFADVR_EINVAL, "job %d: rgba, tf_rgba and nsamples must be device pointers", i);
-        rs.tf = reinterpret_cast<const float4 *>(jb.params.tf_rgba);
-        rs.out = reinterpret_cast<float4 *>(jb.rgba_dev);
-        rs.nsamples = jb.nsamples_dev;
-        table[i].mv = view_of(*m);
-        order[i] = i;
-    }
+    for (int i = 0; i < njobs; ++i)
+        if (mfadvr_status st = make_job(ctx, jobs[i], i, &table[i])) return st;
     if (!ctx->d_jobs) {
         const size_t bytes = sizeof(RenderJob) * MFADVR_MAX_BATCH * mfadvr_ctx::kJobSlots;
         cudaError_t e = cudaMalloc(&ctx->d_jobs, bytes);
@@ -652,35 +610,16 @@ mfadvr_status mfadvr_render_batch(mfadvr_ctx *ctx, int32_t njobs, const mfadvr_r
             e = cudaEventCreateWithFlags(&ctx->job_done[k], cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "job-table allocation");
     }
-    // group by (degree, storage type); each group's tiles are concatenated
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        return std::make_pair(table[a].mv.p, table[a].mv.dtype) < std::make_pair(table[b].mv.p, table[b].mv.dtype);
-    });
     const unsigned slot = ctx->next_jobs++ % mfadvr_ctx::kJobSlots;
     cudaError_t e = cudaEventSynchronize(ctx->job_done[slot]);  // the slot's previous launches are done
     if (e != cudaSuccess) return cuda_fail(ctx, e, "job-table slot wait");
     RenderJob *hj = ctx->h_jobs + static_cast<size_t>(slot) * MFADVR_MAX_BATCH;
     RenderJob *dj = ctx->d_jobs + static_cast<size_t>(slot) * MFADVR_MAX_BATCH;
-    struct Group { int p, dtype, first, count, tiles; };
-    std::vector<Group> groups;
-    for (int k = 0; k < njobs; ++k) {
-        RenderJob jb = table[order[k]];
-        if (groups.empty() || groups.back().p != jb.mv.p || groups.back().dtype != jb.mv.dtype)
-            groups.push_back({jb.mv.p, jb.mv.dtype, k, 0, 0});
-        Group &gr = groups.back();
-        const int tw = 1 << jb.rs.tile_w_log2, th = 32 / tw;
-        jb.tiles_x = (jb.rs.width + tw - 1) / tw;
-        jb.tiles = jb.tiles_x * ((jb.rs.height + th - 1) / th);
-        jb.tile_begin = gr.tiles;
-        jb.pad = 0;
-        gr.tiles += jb.tiles;
-        gr.count += 1;
-        hj[k] = jb;
-    }
+    std::vector<BatchGroup> groups = pack_jobs(table.data(), njobs, hj);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     e = cudaMemcpyAsync(dj, hj, sizeof(RenderJob) * njobs, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "job-table copy");
-    for (const Group &gr : groups) {
+    for (const BatchGroup &gr : groups) {
         int *counter = nullptr;
         if (mfadvr_status st = next_counter(ctx, &counter)) return st;
         e = launch_render_batch(gr.p, gr.dtype, dj + gr.first, gr.count, gr.tiles, 0, counter, s);

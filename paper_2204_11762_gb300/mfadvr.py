@@ -29,7 +29,8 @@ MAX_TF_SIZE = 4096
 EXPORTS = ("mfadvr_create", "mfadvr_destroy", "mfadvr_load_model", "mfadvr_unload_model", "mfadvr_model_info",
            "mfadvr_eval_points", "mfadvr_eval_points_host", "mfadvr_render", "mfadvr_render_host",
            "mfadvr_status_string", "mfadvr_last_error", "mfadvr_render_lattice_noalloc", "mfadvr_render_batch",
-           "mfadvr_autotune", "mfadvr_tuning_save", "mfadvr_tuning_load")
+           "mfadvr_autotune", "mfadvr_tuning_save", "mfadvr_tuning_load", "mfadvr_serve_start", "mfadvr_serve_stop",
+           "mfadvr_submit", "mfadvr_wait", "mfadvr_serve_stats")
 MAX_BATCH = 256
 NOALLOC_MAX_POINTS = 1 << 19
 
@@ -62,6 +63,11 @@ class RenderParams(ctypes.Structure):
 class RenderJob(ctypes.Structure):
     _fields_ = [("model_id", ctypes.c_int32), ("camera", Camera), ("params", RenderParams),
                 ("rgba_dev", ctypes.c_void_p), ("nsamples_dev", ctypes.c_void_p)]
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("frame_budget_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_int32),
+                ("max_in_flight", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):
@@ -107,6 +113,13 @@ def load_library(build_if_missing: bool = True):
     L.mfadvr_tuning_save.restype = i32
     L.mfadvr_tuning_load.argtypes = [vp, ctypes.c_char_p]
     L.mfadvr_tuning_load.restype = i32
+    L.mfadvr_serve_start.argtypes = [vp, P(ServeConfig)]
+    L.mfadvr_serve_stop.argtypes = [vp]
+    L.mfadvr_submit.argtypes = [vp, P(RenderJob), P(u64)]
+    L.mfadvr_wait.argtypes = [vp, u64, i64, P(i64)]
+    L.mfadvr_serve_stats.argtypes = [vp, P(u64), P(u64), P(u64)]
+    for name in ("mfadvr_serve_start", "mfadvr_serve_stop", "mfadvr_submit", "mfadvr_wait", "mfadvr_serve_stats"):
+        getattr(L, name).restype = i32
     f3, i3 = ctypes.c_float * 3, ctypes.c_int32 * 3
     L.mfadvr_render_lattice_noalloc.argtypes = [vp, P(i3), P(i3), P(f3), P(f3), P(Camera), P(RenderParams),
                                                 vp, vp, vp]
@@ -289,6 +302,40 @@ class Context:
         self._check(self._L.mfadvr_render_host(self._h, int(model_id), ctypes.byref(cam), ctypes.byref(prm),
                                                _ptr(rgba), _ptr(nsamples), _stream(stream)))
         return rgba
+
+    # -- serving ----------------------------------------------------------
+    def serve_start(self, frame_budget_bytes=0, max_batch=0, max_in_flight=0):
+        cfg = ServeConfig(int(frame_budget_bytes), int(max_batch), int(max_in_flight))
+        self._check(self._L.mfadvr_serve_start(self._h, ctypes.byref(cfg)))
+
+    def serve_stop(self):
+        self._check(self._L.mfadvr_serve_stop(self._h))
+
+    def submit(self, job: dict) -> int:
+        """Queue one render request (same dict as render_batch jobs)."""
+        j = RenderJob()
+        j.model_id = int(job["model_id"])
+        j.camera = make_camera(job["camera"])
+        j.params = make_params(job["params"], _ptr(job["tf_dev"]), job["tf_size"])
+        j.rgba_dev = _ptr(job["rgba_dev"])
+        j.nsamples_dev = _ptr(job.get("nsamples_dev"))
+        t = ctypes.c_uint64()
+        self._check(self._L.mfadvr_submit(self._h, ctypes.byref(j), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        """Latency in microseconds once done; None on timeout."""
+        lat = ctypes.c_int64()
+        st = self._L.mfadvr_wait(self._h, int(ticket), int(timeout_us), ctypes.byref(lat))
+        if st == ETIMEOUT:
+            return None
+        self._check(st)
+        return lat.value
+
+    def serve_stats(self) -> dict:
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(self._L.mfadvr_serve_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"launches": a.value, "graph_updates": b.value, "graph_instantiations": c.value}
 
     # -- batches and tuning -----------------------------------------------
     def render_batch(self, jobs, stream=None):

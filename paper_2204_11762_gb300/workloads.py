@@ -222,3 +222,23 @@ def value_noise_workload(n=512):
     return {"name": f"noise{n}_p4_persp3840x2160", "degree": p, "ctrl": ctrl, "tf": tf, "camera": cam,
             "params": {"width": 3840, "height": 2160, "step": 1.0 / 2048, "max_opacity": 0.99,
                        "ref_step": REF_STEP, "shading": 1}}
+
+
+def multi_model_workload(count=16, seed_index=3, step=1.0 / 1024):
+    """``count`` render jobs for one batched launch: degrees drawn from
+    {2, 3, 4, 5}, lattices drawn per axis from 64..256 (anisotropic), each a
+    sum of 20 Gaussians as in gaussian_sum_workload; square images of side
+    512, 1024 or 2048; seeded cameras and 256-entry TFs."""
+    rng = np.random.default_rng(seed_for(seed_index))
+    jobs = []
+    for _ in range(count):
+        p = int(rng.choice([2, 3, 4, 5]))
+        n = tuple(int(v) for v in rng.integers(64, 257, size=3))
+        side = int(rng.choice([512, 1024, 2048]))
+        ctrl = gaussian_sum_lattice(n, p, rng)
+        tf = transfer_function(rng, 256)
+        cam = sphere_camera(rng)
+        jobs.append({"degree": p, "ncp": n, "ctrl": ctrl, "tf": tf, "camera": cam,
+                     "params": {"width": side, "height": side, "step": step, "max_opacity": 0.99,
+                                "ref_step": REF_STEP, "shading": 1}})
+    return jobs
