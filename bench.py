@@ -47,13 +47,17 @@ def _args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
-    ap.add_argument("--workload", default="gauss128", choices=["gauss128", "noise512", "multi16"],
+    ap.add_argument("--workload", default="gauss128", choices=["gauss128", "noise512", "multi16", "serve48"],
                     help="gauss128: 128^3 degree-3 render + 2^24 points (default); "
                          "noise512: 512^3 degree-4 render at 3840x2160; "
-                         "multi16: one batched render of 16 models of degree 2-5")
+                         "multi16: one batched render of 16 models of degree 2-5; "
+                         "serve48: 2000 Poisson requests over 48 resident models through the serving loop")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 16-bit storage comparison")
+    ap.add_argument("--serve-step", type=float, default=1.0 / 256, help="serve48: sample step")
+    ap.add_argument("--serve-batch", type=int, default=32, help="serve48: requests per scheduling step")
+    ap.add_argument("--serve-flights", type=int, default=3, help="serve48: batches in flight")
     return ap.parse_args()
 
 
@@ -554,6 +558,154 @@ def run_multi16(args, jobs):
         print(json.dumps(line), flush=True)
 
 
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(q * len(xs)))]
+
+
+def run_serve48(args, wl):
+    """Real-time replay of a Poisson request stream (2000 requests at 200/s,
+    48 resident models of degree 3-4, images 256^2..2048^2) through the
+    serving loop, with FP16 models (and FP32, to separate batching from
+    storage), against serial plain-FP32 rendering of the same stream
+    (queueing simulated from the measured render times)."""
+    import torch
+
+    from paper_2204_11762_gb300 import mfadvr
+
+    mods, reqs, prm = wl
+    prm = dict(prm, step=args.serve_step)
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = mfadvr.Context(local)
+    tfs = [torch.from_numpy(m["tf"]).to(dev) for m in mods]
+    pool = 8
+    bufs = {side: [(torch.empty((side, side, 4), device=dev), torch.empty((side, side), dtype=torch.int32, device=dev))
+                   for _ in range(pool)] for side in sorted({r["side"] for r in reqs})}
+
+    def job(r, ids, rgba, ns):
+        return {"model_id": ids[r["model"]], "camera": r["camera"],
+                "params": dict(prm, width=r["side"], height=r["side"]), "tf_dev": tfs[r["model"]],
+                "tf_size": 256, "rgba_dev": rgba, "nsamples_dev": ns}
+
+    def served(storage):
+        ids = [ctx.load_model(m["ctrl"], m["degree"], storage=storage) for m in mods]
+        ctx.serve_start(frame_budget_bytes=2 << 30, max_batch=args.serve_batch, max_in_flight=args.serve_flights)
+        # the clock sampler starts before the warm-up: its first nvidia-smi
+        # start-up on a box can hold the driver for seconds
+        clocks = ClockSampler(local)
+        clocks.start()
+        for k in range(len(mods)):  # warm-up: graphs, every model once
+            r = dict(reqs[0], model=k, side=256)
+            ctx.wait(ctx.submit(job(r, ids, *bufs[256][k % pool])))
+        warm = []  # and an unmeasured burst of the stream's first requests (every size and buffer)
+        for i, r in enumerate(reqs[:300]):
+            warm.append(ctx.submit(job(r, ids, *bufs[r["side"]][i % pool])))
+            if len(warm) >= pool:
+                ctx.wait(warm.pop(0))
+        for t in warm:
+            ctx.wait(t)
+        samples = torch.zeros((), dtype=torch.int64, device=dev)
+        for side in bufs:  # the client's own reduction kernels load before the replay
+            samples += bufs[side][0][1].sum(dtype=torch.int64) * 0
+        torch.cuda.synchronize(dev)
+        owner = {side: [None] * pool for side in bufs}
+        used = {side: 0 for side in bufs}
+        submit_t, lat = {}, {}
+        t0 = time.perf_counter()
+        for i, r in enumerate(reqs):
+            target = t0 + r["arrival"]
+            while True:
+                dt = target - time.perf_counter()
+                if dt <= 0:
+                    break
+                if dt > 0.0015:
+                    time.sleep(dt - 0.001)
+            side = r["side"]
+            slot = used[side] % pool
+            used[side] += 1
+            prev = owner[side][slot]
+            rgba, ns = bufs[side][slot]
+            if prev is not None:  # the buffer's previous request must be done
+                lat[prev] = ctx.wait(submit_t[prev][1]) / 1e6 + (submit_t[prev][0] - reqs[prev]["arrival"])
+                samples += ns.sum(dtype=torch.int64)
+            submit_t[i] = (time.perf_counter() - t0, ctx.submit(job(r, ids, rgba, ns)))
+            owner[side][slot] = i
+        for side in bufs:
+            for slot, prev in enumerate(owner[side]):
+                if prev is not None and prev not in lat:
+                    lat[prev] = ctx.wait(submit_t[prev][1]) / 1e6 + (submit_t[prev][0] - reqs[prev]["arrival"])
+                    samples += bufs[side][slot][1].sum(dtype=torch.int64)
+        clk = clocks.stop()
+        stats = ctx.serve_stats()
+        ctx.serve_stop()
+        torch.cuda.synchronize(dev)
+        for m in ids:
+            ctx.unload_model(m)
+        n = int(samples.item())
+        lats = [lat[i] for i in range(len(reqs))]
+        makespan = max(reqs[i]["arrival"] + lats[i] for i in range(len(reqs))) - reqs[0]["arrival"]
+        per_s = {}
+        for r, l in zip(reqs, lats):
+            per_s.setdefault(int(r["arrival"]), []).append(l)
+        client_wait = max(submit_t[i][0] - reqs[i]["arrival"] for i in range(len(reqs)))
+        return {"latency_ms_p99_by_arrival_second": [round(1000 * _pct(per_s[k], 0.99), 1) for k in sorted(per_s)],
+                "client_submit_delay_ms_max": 1000 * client_wait,
+                "latency_ms_p50": 1000 * _pct(lats, 0.50), "latency_ms_p99": 1000 * _pct(lats, 0.99),
+                "latency_ms_max": 1000 * max(lats), "samples": n, "makespan_s": makespan,
+                "samples_per_s": n / makespan, "frames_per_s": len(reqs) / makespan, "clocks": clk, **stats}
+
+    srv16 = served("f16")
+    srv32 = served("f32")
+
+    # serial plain FP32: each request rendered alone, in arrival order
+    ids32 = [ctx.load_model(m["ctrl"], m["degree"]) for m in mods]
+    stream = torch.cuda.current_stream(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in reqs]
+    acc = torch.zeros((), dtype=torch.int64, device=dev)
+    for k in range(len(mods)):  # warm-up
+        j = job(dict(reqs[0], model=k, side=256), ids32, *bufs[256][0])
+        ctx.render(j["model_id"], j["camera"], j["params"], j["tf_dev"], 256, j["rgba_dev"], j["nsamples_dev"])
+    for (a, b), r in zip(ev, reqs):
+        rgba, ns = bufs[r["side"]][0]
+        j = job(r, ids32, rgba, ns)
+        a.record(stream)
+        ctx.render(j["model_id"], j["camera"], j["params"], j["tf_dev"], 256, rgba, ns, stream=stream)
+        b.record(stream)
+        acc += ns.sum(dtype=torch.int64)
+    torch.cuda.synchronize(dev)
+    dur = [a.elapsed_time(b) / 1000.0 for a, b in ev]
+    serial_samples = int(acc.item())
+    done, slat = 0.0, []
+    for r, d in zip(reqs, dur):
+        done = max(done, r["arrival"]) + d
+        slat.append(done - r["arrival"])
+    serial_makespan = done - reqs[0]["arrival"]
+    ctx.close()
+    line = {"metric": METRIC, "value": srv16["samples_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": len(reqs), "warmup": len(mods), "ms_per_step": 1000 * srv16["makespan_s"] / len(reqs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (storage f16)",
+            "data": "synthetic",
+            "config": {"workload": f"serve48: 2000 requests, Poisson 200/s, 48 resident models (degree 3-4, "
+                                   f"lattices 96^3..384^3, FP16), images {{256,512,1024,2048}}^2, "
+                                   f"step {args.serve_step:g}",
+                       "frame_budget_bytes": 2 << 30, "max_batch": args.serve_batch,
+                       "max_in_flight": args.serve_flights,
+                       "resident_model_bytes_f16": sum(8 * m["ncp"][0] ** 3 for m in mods),
+                       "offered_load": sum(dur) / (reqs[-1]["arrival"] - reqs[0]["arrival"])},
+            "served_f16": srv16, "served_f32": srv32,
+            "serial_f32": {"latency_ms_p50": 1000 * _pct(slat, 0.50), "latency_ms_p99": 1000 * _pct(slat, 0.99),
+                           "latency_ms_max": 1000 * max(slat), "samples": serial_samples,
+                           "gpu_busy_s": sum(dur), "makespan_s": serial_makespan,
+                           "samples_per_s": serial_samples / serial_makespan,
+                           "busy_samples_per_s": serial_samples / sum(dur),
+                           "frames_per_s": len(reqs) / serial_makespan},
+            "gpu_launches": srv16["launches"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     from paper_2204_11762_gb300 import workloads
@@ -563,6 +715,13 @@ def main():
                                                                    "default workload only"}))
             return
         run_noise512(args, workloads.value_noise_workload(512))
+        return
+    if args.workload == "serve48":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm is timed on the "
+                                                                   "default workload only"}))
+            return
+        run_serve48(args, workloads.serving_workload())
         return
     if args.workload == "multi16":
         if args.impl == "reference":

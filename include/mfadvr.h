@@ -256,6 +256,24 @@ MFADVR_API mfadvr_status mfadvr_wait(mfadvr_ctx *ctx, uint64_t ticket, int64_t t
 MFADVR_API mfadvr_status mfadvr_serve_stats(mfadvr_ctx *ctx, uint64_t *launches, uint64_t *graph_updates,
                                             uint64_t *graph_instantiations);
 
+/* One batch of the serving loop, times in microseconds since
+ * mfadvr_serve_start: a trace of the scheduler. */
+typedef struct {
+    int64_t oldest_submit_us; /* submission of the batch's oldest request     */
+    int64_t t_admit_us;       /* admission                                      */
+    int64_t t_launched_us;    /* the launch call returned                       */
+    int64_t t_done_us;        /* completion seen by the loop                    */
+    int32_t jobs;             /* requests in the batch                          */
+    int32_t groups;           /* launches (degree x storage groups)             */
+    int32_t stream;           /* stream index                                   */
+    int32_t queued_after;     /* requests still queued after admission          */
+} mfadvr_serve_trace_record;
+
+/* Copy the most recent completed batches (at most `capacity`, oldest first;
+ * the loop keeps the last 4096) into records; *count receives how many. */
+MFADVR_API mfadvr_status mfadvr_serve_trace(mfadvr_ctx *ctx, mfadvr_serve_trace_record *records, int32_t capacity,
+                                            int32_t *count);
+
 /* ---- Allocation-free render -------------------------------------------
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory during a render.  Examples are code recording

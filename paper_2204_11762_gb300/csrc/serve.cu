@@ -59,6 +59,7 @@ struct Server {
         size_t bytes = 0;
         cudaEvent_t done = nullptr;
         unsigned slot = 0;
+        mfadvr_serve_trace_record rec{};
     };
     using Signature = std::vector<std::pair<int, int>>;
 
@@ -78,21 +79,23 @@ struct Server {
     unsigned next_flight = 0;
 
     cudaStream_t streams[kMaxFlights] = {};
-    RenderJob *h_jobs = nullptr, *d_jobs = nullptr;
-    cudaEvent_t slot_done[kSlots] = {};
+    RenderJob *h_jobs = nullptr, *d_jobs = nullptr;  // kSlots job tables
     unsigned next_slot = 0;
     int *counters = nullptr;
     unsigned next_counter = 0;
     std::map<std::pair<Signature, int>, cudaGraphExec_t> graphs;
     std::atomic<uint64_t> launches{0}, graph_updates{0}, graph_instantiations{0};
+    // the last kTrace batches, oldest first once the ring wraps
+    static constexpr size_t kTrace = 4096;
+    std::vector<mfadvr_serve_trace_record> trace;
+    size_t trace_next = 0;
+    int64_t t_origin = 0;
 
     // Packs `batch` into the next job-table slot and launches it on stream k
     // through the graph of its group signature.  Called without the lock.
-    cudaError_t launch(const std::vector<Request> &batch, int k, unsigned *slot_out, cudaEvent_t ev)
+    cudaError_t launch(const std::vector<Request> &batch, int k, unsigned slot, cudaEvent_t ev, int *ngroups)
     {
-        const unsigned slot = next_slot++ % kSlots;
-        cudaError_t e = cudaEventSynchronize(slot_done[slot]);
-        if (e != cudaSuccess) return e;
+        cudaError_t e = cudaSuccess;
         RenderJob *hj = h_jobs + static_cast<size_t>(slot) * MFADVR_MAX_BATCH;
         RenderJob *dj = d_jobs + static_cast<size_t>(slot) * MFADVR_MAX_BATCH;
         std::vector<RenderJob> src(batch.size());
@@ -100,6 +103,7 @@ struct Server {
         std::vector<BatchGroup> groups = pack_jobs(src.data(), static_cast<int>(src.size()), hj);
         Signature sig;
         for (const BatchGroup &g : groups) sig.emplace_back(g.p, g.dtype);
+        *ngroups = static_cast<int>(groups.size());
 
         cudaStream_t s = streams[k];
         cudaGraph_t graph = nullptr;
@@ -142,10 +146,8 @@ struct Server {
         }
         cudaGraphDestroy(graph);
         e = cudaGraphLaunch(it->second, s);
-        if (e == cudaSuccess) e = cudaEventRecord(slot_done[slot], s);
         if (e == cudaSuccess) e = cudaEventRecord(ev, s);
         ++launches;
-        *slot_out = slot;
         return e;
     }
 
@@ -170,6 +172,10 @@ struct Server {
                 }
                 if (q != cudaSuccess) cudaGetLastError();
                 in_use -= it->bytes;
+                it->rec.t_done_us = t - t_origin;
+                if (trace.size() < kTrace) trace.push_back(it->rec);
+                else trace[trace_next % kTrace] = it->rec;
+                ++trace_next;
                 cudaEventDestroy(it->done);
                 it = flights.erase(it);
                 cv_done.notify_all();
@@ -189,6 +195,10 @@ struct Server {
                 if (!batch.empty()) {
                     Flight f;
                     f.bytes = bytes;
+                    f.rec.t_admit_us = now_us() - t_origin;
+                    f.rec.jobs = static_cast<int32_t>(batch.size());
+                    f.rec.queued_after = static_cast<int32_t>(pending.size());
+                    f.rec.oldest_submit_us = tickets[batch.front().id].t_submit - t_origin;
                     for (const Request &r : batch) {
                         f.ids.push_back(r.id);
                         tickets[r.id].state = 1;
@@ -196,9 +206,18 @@ struct Server {
                     in_use += bytes;
                     const int k = static_cast<int>(next_flight++ % static_cast<unsigned>(max_flights));
                     cudaError_t e = cudaEventCreateWithFlags(&f.done, cudaEventDisableTiming);
+                    f.rec.stream = k;
+                    // a job-table slot no batch in flight reads (kSlots > kMaxFlights)
+                    bool busy[kSlots] = {};
+                    for (const Flight &o : flights) busy[o.slot] = true;
+                    while (busy[next_slot % kSlots]) ++next_slot;
+                    f.slot = next_slot++ % kSlots;
                     lk.unlock();
-                    if (e == cudaSuccess) e = launch(batch, k, &f.slot, f.done);
+                    int groups = 0;
+                    if (e == cudaSuccess) e = launch(batch, k, f.slot, f.done, &groups);
                     lk.lock();
+                    f.rec.groups = groups;
+                    f.rec.t_launched_us = now_us() - t_origin;
                     if (e != cudaSuccess) {
                         cudaGetLastError();
                         const int64_t t = now_us();
@@ -240,8 +259,6 @@ void stop_server(mfadvr_ctx *ctx)
     for (auto &kv : sv->graphs) cudaGraphExecDestroy(kv.second);
     for (auto &s : sv->streams)
         if (s) cudaStreamDestroy(s);
-    for (auto &e : sv->slot_done)
-        if (e) cudaEventDestroy(e);
     if (sv->d_jobs) cudaFree(sv->d_jobs);
     if (sv->h_jobs) cudaFreeHost(sv->h_jobs);
     if (sv->counters) cudaFree(sv->counters);
@@ -280,13 +297,13 @@ mfadvr_status mfadvr_serve_start(mfadvr_ctx *ctx, const mfadvr_serve_config *cfg
     if (e == cudaSuccess) e = cudaMalloc(&sv->counters, sizeof(int) * kCounters);
     for (int k = 0; e == cudaSuccess && k < kMaxFlights; ++k)
         e = cudaStreamCreateWithFlags(&sv->streams[k], cudaStreamNonBlocking);
-    for (unsigned k = 0; e == cudaSuccess && k < kSlots; ++k)
-        e = cudaEventCreateWithFlags(&sv->slot_done[k], cudaEventDisableTiming);
     ctx->server = sv;
     if (e != cudaSuccess) {
         stop_server(ctx);
         return cuda_fail(ctx, e, "serving-loop setup");
     }
+    sv->t_origin = now_us();
+    sv->trace.reserve(Server::kTrace);
     sv->thread = std::thread([sv] { sv->run(); });
     return MFADVR_OK;
 }
@@ -355,6 +372,26 @@ mfadvr_status mfadvr_serve_stats(mfadvr_ctx *ctx, uint64_t *launches, uint64_t *
     if (launches) *launches = sv->launches.load();
     if (graph_updates) *graph_updates = sv->graph_updates.load();
     if (graph_instantiations) *graph_instantiations = sv->graph_instantiations.load();
+    return MFADVR_OK;
+}
+
+
+
+mfadvr_status mfadvr_serve_trace(mfadvr_ctx *ctx, mfadvr_serve_trace_record *records, int32_t capacity,
+                                 int32_t *count)
+{
+    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
+    Server *sv = ctx->server;
+    if (!sv) return fail(ctx, MFADVR_EINVAL, "the serving loop is not running");
+    if (!count || capacity < 0 || (capacity > 0 && !records))
+        return fail(ctx, MFADVR_EINVAL, "count must not be NULL and records must hold capacity entries");
+    std::lock_guard<std::mutex> g(sv->mu);
+    const size_t n = sv->trace.size();
+    const size_t take = std::min(n, static_cast<size_t>(capacity));
+    // oldest first: when the ring has wrapped, it starts at trace_next % kTrace
+    const size_t start = (sv->trace_next > Server::kTrace) ? sv->trace_next % Server::kTrace : 0;
+    for (size_t i = 0; i < take; ++i) records[i] = sv->trace[(start + (n - take) + i) % n];
+    *count = static_cast<int32_t>(take);
     return MFADVR_OK;
 }
 

@@ -30,7 +30,7 @@ EXPORTS = ("mfadvr_create", "mfadvr_destroy", "mfadvr_load_model", "mfadvr_unloa
            "mfadvr_eval_points", "mfadvr_eval_points_host", "mfadvr_render", "mfadvr_render_host",
            "mfadvr_status_string", "mfadvr_last_error", "mfadvr_render_lattice_noalloc", "mfadvr_render_batch",
            "mfadvr_autotune", "mfadvr_tuning_save", "mfadvr_tuning_load", "mfadvr_serve_start", "mfadvr_serve_stop",
-           "mfadvr_submit", "mfadvr_wait", "mfadvr_serve_stats")
+           "mfadvr_submit", "mfadvr_wait", "mfadvr_serve_stats", "mfadvr_serve_trace")
 MAX_BATCH = 256
 NOALLOC_MAX_POINTS = 1 << 19
 
@@ -68,6 +68,12 @@ class RenderJob(ctypes.Structure):
 class ServeConfig(ctypes.Structure):
     _fields_ = [("frame_budget_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_int32),
                 ("max_in_flight", ctypes.c_int32)]
+
+
+class ServeTraceRecord(ctypes.Structure):
+    _fields_ = [("oldest_submit_us", ctypes.c_int64), ("t_admit_us", ctypes.c_int64),
+                ("t_launched_us", ctypes.c_int64), ("t_done_us", ctypes.c_int64), ("jobs", ctypes.c_int32),
+                ("groups", ctypes.c_int32), ("stream", ctypes.c_int32), ("queued_after", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):
@@ -118,7 +124,9 @@ def load_library(build_if_missing: bool = True):
     L.mfadvr_submit.argtypes = [vp, P(RenderJob), P(u64)]
     L.mfadvr_wait.argtypes = [vp, u64, i64, P(i64)]
     L.mfadvr_serve_stats.argtypes = [vp, P(u64), P(u64), P(u64)]
-    for name in ("mfadvr_serve_start", "mfadvr_serve_stop", "mfadvr_submit", "mfadvr_wait", "mfadvr_serve_stats"):
+    L.mfadvr_serve_trace.argtypes = [vp, P(ServeTraceRecord), i32, P(i32)]
+    for name in ("mfadvr_serve_start", "mfadvr_serve_stop", "mfadvr_submit", "mfadvr_wait", "mfadvr_serve_stats",
+                 "mfadvr_serve_trace"):
         getattr(L, name).restype = i32
     f3, i3 = ctypes.c_float * 3, ctypes.c_int32 * 3
     L.mfadvr_render_lattice_noalloc.argtypes = [vp, P(i3), P(i3), P(f3), P(f3), P(Camera), P(RenderParams),
@@ -336,6 +344,13 @@ class Context:
         a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
         self._check(self._L.mfadvr_serve_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return {"launches": a.value, "graph_updates": b.value, "graph_instantiations": c.value}
+
+    def serve_trace(self, capacity: int = 4096) -> list:
+        """The most recent completed batches of the serving loop, oldest first."""
+        buf = (ServeTraceRecord * capacity)()
+        n = ctypes.c_int32()
+        self._check(self._L.mfadvr_serve_trace(self._h, buf, capacity, ctypes.byref(n)))
+        return [{f: getattr(buf[i], f) for f, _ in ServeTraceRecord._fields_} for i in range(n.value)]
 
     # -- batches and tuning -----------------------------------------------
     def render_batch(self, jobs, stream=None):

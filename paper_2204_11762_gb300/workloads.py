@@ -78,13 +78,12 @@ def gaussian_sum_lattice(n, p, rng, count=20):
     n = tuple(int(v) for v in n)
     xs = _grid(n, p)
     centres, sigmas, amps = gaussian_sum_params(rng, count)
-    out = np.zeros((n[2], n[1], n[0]), dtype=np.float64)
-    for g in range(count):
-        fx = np.exp(-((xs[0] - centres[g, 0]) ** 2) / (2 * sigmas[g, 0] ** 2))
-        fy = np.exp(-((xs[1] - centres[g, 1]) ** 2) / (2 * sigmas[g, 1] ** 2))
-        fz = np.exp(-((xs[2] - centres[g, 2]) ** 2) / (2 * sigmas[g, 2] ** 2))
-        out += amps[g] * fz[:, None, None] * fy[None, :, None] * fx[None, None, :]
-    return out.astype(np.float32)
+    # 1-D factors per Gaussian: F_d[g, :] along axis d
+    F = [np.exp(-((xs[d][None, :] - centres[:, d:d + 1]) ** 2) / (2 * sigmas[:, d:d + 1] ** 2)) for d in range(3)]
+    # out[k, j, i] = sum_g a_g Fz[g, k] Fy[g, j] Fx[g, i]: one matrix product
+    kj = (amps[:, None, None] * F[2][:, :, None] * F[1][:, None, :]).reshape(count, -1)
+    out = kj.T @ F[0]
+    return out.reshape(n[2], n[1], n[0]).astype(np.float32)
 
 
 def field_lattice(field, n, p, lo=-1.0, hi=1.0):
@@ -242,3 +241,26 @@ def multi_model_workload(count=16, seed_index=3, step=1.0 / 1024):
                      "params": {"width": side, "height": side, "step": step, "max_opacity": 0.99,
                                 "ref_step": REF_STEP, "shading": 1}})
     return jobs
+
+
+def serving_workload(models=48, requests=2000, rate=200.0, sizes=(256, 512, 1024, 2048), step=1.0 / 512,
+                     seed_index=4):
+    """Resident models and a request stream for the serving loop: ``models``
+    models of degree 3 or 4 with cubic lattices drawn from 96..384 per side
+    (Gaussian sums), each with its own 256-entry TF; ``requests`` requests
+    arriving as a Poisson process of ``rate`` per second, each drawing its
+    model uniformly, its square image side from ``sizes`` and a camera on the
+    radius-2 sphere.  Returns (models, requests); a request is a dict with
+    arrival time (s), model index, side and camera."""
+    rng = np.random.default_rng(seed_for(seed_index))
+    mods = []
+    for _ in range(models):
+        p = int(rng.choice([3, 4]))
+        n = int(rng.integers(96, 385))
+        mods.append({"degree": p, "ncp": (n, n, n), "ctrl": gaussian_sum_lattice((n, n, n), p, rng),
+                     "tf": transfer_function(rng, 256)})
+    t = np.cumsum(rng.exponential(1.0 / rate, size=requests))
+    reqs = [{"arrival": float(t[i]), "model": int(rng.integers(0, models)), "side": int(rng.choice(sizes)),
+             "camera": sphere_camera(rng)} for i in range(requests)]
+    params = {"step": step, "max_opacity": 0.99, "ref_step": REF_STEP, "shading": 1}
+    return mods, reqs, params
