@@ -55,7 +55,7 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 16-bit storage comparison")
-    ap.add_argument("--serve-step", type=float, default=1.0 / 256, help="serve48: sample step")
+    ap.add_argument("--serve-step", type=float, default=1.0 / 512, help="serve48: sample step")
     ap.add_argument("--serve-batch", type=int, default=32, help="serve48: requests per scheduling step")
     ap.add_argument("--serve-flights", type=int, default=3, help="serve48: batches in flight")
     return ap.parse_args()
