@@ -117,53 +117,130 @@ __device__ __forceinline__ void basis_uniform_scaled(float x, float N[P + 1], fl
     }
 }
 
-// Any span (including the clamped ones near the ends): the Cox-de Boor
-// triangle with left/right differences (the published form, Piegl & Tiller,
-// The NURBS Book, Sec. 2.2-2.3) on the integer knots kappa(j).
+// ---------------------------------------------------------------------------
+// Pieces on every span.  The span-local knots kappa(j), j = 1-P..P, depend on
+// the span only through how close it is to the two clamped ends:
+//   a = max(0, P-1-k) knots cut off on the left  (kappa(j) >= -(P-1-a)),
+//   b = max(0, k+P-m) knots cut off on the right (kappa(j) <= P-b),
+// so P x P knot patterns cover all spans of all lattices, pattern (0, 0)
+// being the uniform one.  Each pattern's P+1 basis functions are fixed
+// polynomials of the local coordinate; their monomial coefficients come from
+// the Cox-de Boor recurrence run on polynomials at compile time, with the
+// convention 0/0 = 0 for the empty supports of the clamped ends.
+// ---------------------------------------------------------------------------
 template <int P>
-__device__ __forceinline__ void basis_general(float x, int k, int m, float N[P + 1], float dN[P + 1])
+struct SpanPieces {
+    float c[P * P][P + 1][P + 1];  // pattern a*P + b: BasisScale<P> N_r(x) = sum_e c[.][r][e] x^e
+};
+
+template <int P>
+constexpr SpanPieces<P> make_span_pieces(double scale)
 {
-    float left[P + 1], right[P + 1];
-#pragma unroll
-    for (int j = 1; j <= P; ++j) {
-        left[j] = x - static_cast<float>(min(max(k + 1 - j, 0), m) - k);
-        right[j] = static_cast<float>(min(max(k + j, 0), m) - k) - x;
-    }
-    float Nq[P + 1];
-    float Nlow[P + 1];  // degree P-1 values, for the derivatives
-    Nq[0] = 1.0f;
-#pragma unroll
-    for (int q = 1; q <= P; ++q) {
-        if (q == P) {
-#pragma unroll
-            for (int r = 0; r < P; ++r) Nlow[r] = Nq[r];
+    SpanPieces<P> out{};
+    for (int a = 0; a < P; ++a) {
+        for (int b = 0; b < P; ++b) {
+            double kap[2 * P] = {};  // kap[j + P - 1] = kappa(j)
+            for (int j = 1 - P; j <= P; ++j) {
+                int v = j < -(P - 1 - a) ? -(P - 1 - a) : j;
+                kap[j + P - 1] = v > P - b ? P - b : v;
+            }
+            double B[P + 1][P + 1][P + 1] = {};  // [q][r][e]: N_{s-q+r, q}
+            B[0][0][0] = 1.0;
+            for (int q = 1; q <= P; ++q) {
+                for (int r = 0; r <= q; ++r) {
+                    const int i = r - q;
+                    if (r > 0) {  // (x - kappa(i)) / (kappa(i+q) - kappa(i)) N_{s+i, q-1}
+                        const double k0 = kap[i + P - 1], den = kap[i + q + P - 1] - k0;
+                        if (den != 0.0)
+                            for (int e = 0; e < q; ++e) {
+                                B[q][r][e + 1] += B[q - 1][r - 1][e] / den;
+                                B[q][r][e] -= k0 * B[q - 1][r - 1][e] / den;
+                            }
+                    }
+                    if (r < q) {  // (kappa(i+q+1) - x) / (kappa(i+q+1) - kappa(i+1)) N_{s+i+1, q-1}
+                        const double k1 = kap[i + q + P], den = k1 - kap[i + P];
+                        if (den != 0.0)
+                            for (int e = 0; e < q; ++e) {
+                                B[q][r][e] += k1 * B[q - 1][r][e] / den;
+                                B[q][r][e + 1] -= B[q - 1][r][e] / den;
+                            }
+                    }
+                }
+            }
+            for (int r = 0; r <= P; ++r)
+                for (int e = 0; e <= P; ++e) out.c[a * P + b][r][e] = static_cast<float>(scale * B[P][r][e]);
         }
-        float saved = 0.0f;
-#pragma unroll
-        for (int r = 0; r < q; ++r) {
-            const float tmp = Nq[r] * __frcp_rn(right[r + 1] + left[q - r]);
-            Nq[r] = fmaf(right[r + 1], tmp, saved);
-            saved = left[q - r] * tmp;
-        }
-        Nq[q] = saved;
     }
-    // N'_{i,P} = P (N_{i,P-1}/(t_{i+P}-t_i) - N_{i+1,P-1}/(t_{i+P+1}-t_{i+1}))
-    // for i = s-P+r, r = 0..P.  In kappa units the two knot differences are
-    // kappa(r) - kappa(r-P) and kappa(r+1) - kappa(r+1-P); N_{i,P-1} is
-    // Nlow[r-1] and N_{i+1,P-1} is Nlow[r].
+    return out;
+}
+
+// Compile-time pins of the tables: pattern (0, 0) is the uniform pieces, and
+// every pattern sums to BasisScale<P> (partition of unity: the constant term
+// sums to the scale, higher terms cancel).
+template <int P>
+constexpr bool span_pieces_consistent(double scale)
+{
+    constexpr UniformPieces<P> U = make_uniform_pieces<P>();
+    const SpanPieces<P> S = make_span_pieces<P>(scale);
+    for (int r = 0; r <= P; ++r)
+        for (int e = 0; e <= P; ++e) {
+            const double d = S.c[0][r][e] - scale * U.c[r][e];
+            if (d > 1e-6 || d < -1e-6) return false;
+        }
+    for (int pat = 0; pat < P * P; ++pat)
+        for (int e = 0; e <= P; ++e) {
+            double sum = 0.0;
+            for (int r = 0; r <= P; ++r) sum += S.c[pat][r][e];
+            const double want = e == 0 ? scale : 0.0;
+            if (sum - want > 1e-5 || sum - want < -1e-5) return false;
+        }
+    return true;
+}
+
+struct AllSpanPieces {
+    SpanPieces<1> p1;
+    SpanPieces<2> p2;
+    SpanPieces<3> p3;
+    SpanPieces<4> p4;
+    SpanPieces<5> p5;
+};
+static_assert(span_pieces_consistent<1>(1.0) && span_pieces_consistent<2>(1.0) && span_pieces_consistent<3>(6.0) &&
+                  span_pieces_consistent<4>(1.0) && span_pieces_consistent<5>(1.0),
+              "span piece tables disagree with the uniform pieces or the partition of unity");
+
+static __constant__ AllSpanPieces kSpanPieces = {
+    make_span_pieces<1>(BasisScale<1>::value), make_span_pieces<2>(BasisScale<2>::value),
+    make_span_pieces<3>(BasisScale<3>::value), make_span_pieces<4>(BasisScale<4>::value),
+    make_span_pieces<5>(BasisScale<5>::value)};
+
+template <int P>
+__device__ __forceinline__ const SpanPieces<P> &span_pieces()
+{
+    if constexpr (P == 1) return kSpanPieces.p1;
+    else if constexpr (P == 2) return kSpanPieces.p2;
+    else if constexpr (P == 3) return kSpanPieces.p3;
+    else if constexpr (P == 4) return kSpanPieces.p4;
+    else return kSpanPieces.p5;
+}
+
+// Basis (times BasisScale<P>) and local derivative on span k of an axis
+// with m spans, from the piece table of the span's knot pattern: Horner's
+// rule for the value and its derivative together.
+template <int P>
+__device__ __forceinline__ void basis_table(float x, int k, int m, float N[P + 1], float dN[P + 1])
+{
+    const int a = max(0, P - 1 - k), b = max(0, k + P - m);
+    const float(&c)[P + 1][P + 1] = span_pieces<P>().c[a * P + b];
 #pragma unroll
     for (int r = 0; r <= P; ++r) {
-        float dv = 0.0f;
-        if (r > 0) {
-            const float den = static_cast<float>(min(max(k + r, 0), m) - min(max(k + r - P, 0), m));
-            dv = Nlow[r - 1] * __frcp_rn(den);
+        float v = c[r][P], d = 0.0f;
+#pragma unroll
+        for (int e = P - 1; e >= 0; --e) {
+            d = fmaf(d, x, v);
+            v = fmaf(v, x, c[r][e]);
         }
-        if (r < P) {
-            const float den = static_cast<float>(min(max(k + r + 1, 0), m) - min(max(k + r + 1 - P, 0), m));
-            dv -= Nlow[r] * __frcp_rn(den);
-        }
-        N[r] = Nq[r];
-        dN[r] = static_cast<float>(P) * dv;
+        N[r] = v;
+        dN[r] = d;
     }
 }
 
@@ -175,23 +252,13 @@ __device__ __forceinline__ bool span_interior(int k, int m)
     return k >= P - 1 && k <= m - P;
 }
 
-// Basis on span k of an axis with m spans, times BasisScale<P>: uniform
-// pieces on unclamped spans, the general triangle otherwise.
+// Basis on span k of an axis with m spans, times BasisScale<P>: the uniform
+// closed form on unclamped spans, the piece table otherwise.
 template <int P>
 __device__ __forceinline__ void basis(float x, int k, int m, float N[P + 1], float dN[P + 1])
 {
-    if (span_interior<P>(k, m)) {
-        basis_uniform_scaled<P>(x, N, dN);
-    } else {
-        basis_general<P>(x, k, m, N, dN);
-        if constexpr (BasisScale<P>::value != 1.0f) {
-#pragma unroll
-            for (int r = 0; r <= P; ++r) {
-                N[r] *= BasisScale<P>::value;
-                dN[r] *= BasisScale<P>::value;
-            }
-        }
-    }
+    if (span_interior<P>(k, m)) basis_uniform_scaled<P>(x, N, dN);
+    else basis_table<P>(x, k, m, N, dN);
 }
 
 // Exact k = floor(u*m) for FP32 u in [0, 1], clamped to [0, m-1].  The FP32

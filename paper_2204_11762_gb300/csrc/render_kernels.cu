@@ -60,8 +60,9 @@ struct LaneRay {
     int kk[3];                   // the same as int
     int base;                    // quad index of the span block's first control point
     bool interior;               // all three spans unclamped: uniform pieces apply
-    float sf, nsf;               // samples taken / samples on the ray
+    float sf, nsf;               // samples contracted / samples on the ray
     float Cr, Cg, Cb, A;         // premultiplied colour and opacity so far
+    float r[4];                  // query of sample sf - 1, not yet composited
 };
 
 template <int P>
@@ -136,6 +137,8 @@ __device__ __forceinline__ bool start_ray(const RenderSetup &rs, int px, int py,
     }
     ray.sf = 0.f;
     ray.Cr = ray.Cg = ray.Cb = ray.A = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) ray.r[c] = 0.f;
     return true;
 }
 
@@ -160,29 +163,52 @@ struct TfGlobal {
     }
 };
 
-// One sample of the lane's ray: span bookkeeping (and a cache reload when the
-// span changed), basis, contraction, applyTFs, shading, compositing, early
-// termination.  Returns true when the ray is finished (pixel written).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// One iteration of the lane's ray, software-pipelined over two samples:
+// the span bookkeeping (with a cache reload when the span changed), basis
+// and contraction of sample sf, and the applyTFs, shading and compositing
+// of sample sf - 1, whose query the previous iteration left in ray.r.  The
+// two halves are independent, so the compiler interleaves the contraction's
+// FMAs with the serial TF / shading / compositing chain.  Early termination
+// is decided on the composited sample; the query of sample sf is then
+// dropped, as is the one past the last sample.  Returns true when the ray
+// is finished (pixel written).
 template <int P, typename T, typename Tf>
 __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSetup &rs, const Tf &tf, LaneRay &ray,
                                             SpanCache<P> &cache)
 {
     constexpr int JP = Block<P>::JP;
     constexpr bool kCache = SpanCache<P>::kOn;
-    float X[3], x[3];
+    const float s = ray.sf;
+
+    // ---- span of sample s; positions are clamped to the lattice only when
+    // the span changes (a sample outside [0, m] always leaves its span) ------
+    float x[3];
     bool moved = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float mfa = static_cast<float>(mv.m[a]);
-        X[a] = fminf(fmaxf(fmaf(ray.sf, ray.dX[a], ray.X0[a]), 0.0f), mfa);
-        x[a] = X[a] - ray.kf[a];
+        x[a] = fmaf(s, ray.dX[a], ray.X0[a]) - ray.kf[a];
         moved |= (x[a] < 0.0f) | (x[a] >= 1.0f);
     }
     if (moved) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            ray.kf[a] = fminf(floorf(X[a]), static_cast<float>(mv.m[a]) - 1.0f);
-            x[a] = X[a] - ray.kf[a];
+            const float mfa = static_cast<float>(mv.m[a]);
+            const float X = fminf(fmaxf(fmaf(s, ray.dX[a], ray.X0[a]), 0.0f), mfa);
+            ray.kf[a] = fminf(floorf(X), mfa - 1.0f);
+            x[a] = X - ray.kf[a];
             ray.kk[a] = static_cast<int>(ray.kf[a]);
         }
         ray.base = ray.kk[0] + mv.n[0] * ray.kk[1] + mv.n01 * ray.kk[2];
@@ -199,30 +225,19 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
                     for (int i = 0; i <= P; ++i) cache.v[k][jp][i] = quad_pair<P>(q, k, jp, i);
         }
     }
+    // uniform pieces, replaced from the piece table on clamped spans
     float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
-    if (ray.interior) {
-        basis_uniform_scaled<P>(x[0], Nu, dNu);
-        basis_uniform_scaled<P>(x[1], Nv, dNv);
-        basis_uniform_scaled<P>(x[2], Nw, dNw);
-    } else {
-        basis<P>(x[0], ray.kk[0], mv.m[0], Nu, dNu);
-        basis<P>(x[1], ray.kk[1], mv.m[1], Nv, dNv);
-        basis<P>(x[2], ray.kk[2], mv.m[2], Nw, dNw);
-    }
-    float r[4];
-    if constexpr (kCache) {
-        contract_pairs<P>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return cache.v[k][jp][i]; }, r);
-    } else {
-        const int n0 = mv.n[0], n01 = mv.n01, base = ray.base;
-        contract_pairs<P>(Nu, dNu, Nv, dNv, Nw, dNw,
-                          [&](int k, int jp, int i) {
-                              const float4 qv = QuadLoad<T>::at(mv.quads, base + (i & ~1) + 2 * jp * n0 + k * n01);
-                              return (i & 1) ? make_float2(qv.z, qv.w) : make_float2(qv.x, qv.y);
-                          },
-                          r);
+    basis_uniform_scaled<P>(x[0], Nu, dNu);
+    basis_uniform_scaled<P>(x[1], Nv, dNv);
+    basis_uniform_scaled<P>(x[2], Nw, dNw);
+    if (!ray.interior) {
+        if (!span_interior<P>(ray.kk[0], mv.m[0])) basis_table<P>(x[0], ray.kk[0], mv.m[0], Nu, dNu);
+        if (!span_interior<P>(ray.kk[1], mv.m[1])) basis_table<P>(x[1], ray.kk[1], mv.m[1], Nv, dNv);
+        if (!span_interior<P>(ray.kk[2], mv.m[2])) basis_table<P>(x[2], ray.kk[2], mv.m[2], Nw, dNw);
     }
 
-    // ---- applyTFs: linear interpolation in the table -----------------------
+    // ---- applyTFs on sample s - 1: linear interpolation in the table -------
+    const float r[4] = {ray.r[0], ray.r[1], ray.r[2], ray.r[3]};
     const float xt = fminf(fmaxf(fmaf(r[0], rs.tf_a, rs.tf_b), 0.0f), static_cast<float>(rs.tf_size - 1));
     const int it = min(static_cast<int>(xt), rs.tf_size - 2);
     const float fr = xt - static_cast<float>(it);
@@ -232,37 +247,52 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
     float cg = fmaf(fr, td.y, ta.y);
     float cb = fmaf(fr, td.z, ta.z);
     float alpha = clamp01f(fmaf(fr, td.w, ta.w));
-    if (rs.correct_opacity) alpha = 1.0f - exp2f(log2f(1.0f - alpha) * rs.opacity_ratio);
+    const float corrected = 1.0f - ex2_approx(lg2_approx(1.0f - alpha) * rs.opacity_ratio);
+    alpha = rs.correct_opacity ? corrected : alpha;
+    alpha = s > 0.0f ? alpha : 0.0f;  // no sample before the first
 
     // ---- shading: Blinn-Phong, headlight L = V = -d, two-sided -------------
-    if (rs.shading) {
+    {
         const float gx = r[1] * rs.grad_scale[0];
         const float gy = r[2] * rs.grad_scale[1];
         const float gz = r[3] * rs.grad_scale[2];
         const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-        if (g2 <= rs.gthresh2) {
-            cr *= rs.ka; cg *= rs.ka; cb *= rs.ka;
-        } else {
-            const float ndl =
-                fminf(fabsf(fmaf(gx, ray.dir[0], fmaf(gy, ray.dir[1], gz * ray.dir[2]))) * rsqrtf(g2), 1.0f);
-            const float spec = rs.ks * __powf(ndl, rs.shininess);
-            const float diff = fmaf(rs.kd, ndl, rs.ka);
-            cr = clamp01f(fmaf(cr, diff, spec));
-            cg = clamp01f(fmaf(cg, diff, spec));
-            cb = clamp01f(fmaf(cb, diff, spec));
-        }
+        const float ndl =
+            fminf(fabsf(fmaf(gx, ray.dir[0], fmaf(gy, ray.dir[1], gz * ray.dir[2]))) * rsqrtf(g2), 1.0f);
+        const float spec = rs.ks * __powf(ndl, rs.shininess);
+        const float diff = fmaf(rs.kd, ndl, rs.ka);
+        const bool flat = g2 <= rs.gthresh2;
+        const bool lit = rs.shading != 0;
+        cr = lit ? (flat ? cr * rs.ka : clamp01f(fmaf(cr, diff, spec))) : cr;
+        cg = lit ? (flat ? cg * rs.ka : clamp01f(fmaf(cg, diff, spec))) : cg;
+        cb = lit ? (flat ? cb * rs.ka : clamp01f(fmaf(cb, diff, spec))) : cb;
     }
 
-    // ---- front-to-back compositing + early ray termination ----------------
+    // ---- front-to-back compositing of sample s - 1 -------------------------
     const float wgt = (1.0f - ray.A) * alpha;
     ray.Cr = fmaf(wgt, cr, ray.Cr);
     ray.Cg = fmaf(wgt, cg, ray.Cg);
     ray.Cb = fmaf(wgt, cb, ray.Cb);
     ray.A += wgt;
-    ray.sf += 1.0f;
-    if (ray.A > rs.max_opacity || ray.sf >= ray.nsf) {
+
+    // ---- query of sample s (composited by the next iteration) -------------
+    if constexpr (kCache) {
+        contract_pairs<P>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return cache.v[k][jp][i]; }, ray.r);
+    } else {
+        const int n0 = mv.n[0], n01 = mv.n01, base = ray.base;
+        contract_pairs<P>(Nu, dNu, Nv, dNv, Nw, dNw,
+                          [&](int k, int jp, int i) {
+                              const float4 qv = QuadLoad<T>::at(mv.quads, base + (i & ~1) + 2 * jp * n0 + k * n01);
+                              return (i & 1) ? make_float2(qv.z, qv.w) : make_float2(qv.x, qv.y);
+                          },
+                          ray.r);
+    }
+    ray.sf = s + 1.0f;
+
+    // ---- early ray termination / end of the ray: s samples composited ------
+    if (s > 0.0f && (ray.A > rs.max_opacity || s >= ray.nsf)) {
         rs.out[ray.pix] = make_float4(ray.Cr, ray.Cg, ray.Cb, ray.A);
-        if (rs.nsamples) rs.nsamples[ray.pix] = static_cast<int>(ray.sf);
+        if (rs.nsamples) rs.nsamples[ray.pix] = static_cast<int>(s);
         return true;
     }
     return false;
