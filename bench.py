@@ -445,7 +445,7 @@ def run_noise512(args, wl):
             "config": {"workload": "noise512_p4: 3840x2160 perspective render (60 deg, step 1/2048, O_max 0.99, "
                                    "TF 1024, opacity ref 1/16, shading)",
                        "model": "MFA degree 4, 512^3 control points (5-octave value noise), clamped uniform knots",
-                       "l2": "flushed between steps; the 2 GiB FP32 quad array exceeds L2"},
+                       "l2": "flushed between steps; the 4 GiB FP32 row array exceeds L2"},
             "gpu_launches": steps,
             "frames_per_s": world * 1000.0 / r_ms,
             "render": {"samples_per_frame": r["samples"], "ms_mean": r_ms, "ms_p50": statistics.median(r["ms"]),

@@ -295,10 +295,11 @@ MFADVR_API mfadvr_status mfadvr_serve_trace(mfadvr_ctx *ctx, mfadvr_serve_trace_
  *                refused: the lattice range is not computed).  Shading treats
  *                only an exactly zero gradient as ambient-only.
  *  rgba_dev, nsamples_dev, stream: as for mfadvr_render.
- * Scratch: the quad layout of the lattice and the ray-tile counter live in
- * one file-scope device array of 256 + 16 * MFADVR_NOALLOC_MAX_POINTS bytes
- * (8 MiB + 256 B), which every GPU that loads the library holds until the
- * process exits.  Every call rebuilds the quads and zeroes the counter on its
+ * Scratch: the row layout of the lattice (8 FP32 values per control point)
+ * and the ray-tile counter live in one file-scope device array of
+ * 256 + 32 * MFADVR_NOALLOC_MAX_POINTS bytes (16 MiB + 256 B), which every GPU
+ * that loads the library holds until the process exits.  Every call rebuilds
+ * the rows and zeroes the counter on its
  * stream before reading them, so no call reads what an earlier call left
  * there; but all calls share that one array, so calls whose work overlaps
  * on the GPU (different streams, or different host threads) race and

@@ -16,7 +16,7 @@ namespace mfadvr {
 namespace api {
 
 struct Model {
-    void *d_quads = nullptr;  // quad layout, see mfa_basis.cuh
+    void *d_rows = nullptr;   // row layout, see mfa_basis.cuh
     uint64_t bytes = 0;
     int p = 0;
     int n[3] = {0, 0, 0};

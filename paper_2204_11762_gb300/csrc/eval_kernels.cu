@@ -1,12 +1,13 @@
 // mfadvr_eval_points: value and first derivatives of the MFA model at
 // arbitrary parameter points (queryValueMFA + queryGradientMFA of
 // Algorithm 1, computed together as Sec. 3.1 describes), and the kernel that
-// builds a model's quad array.
+// builds a model's row array.
 //
 // One thread per point, grid-stride over a grid sized to the SM count.  The
 // span index is exact integer work (see span_exact); basis and contraction
-// run in FP32 on the FMA pipe; the span block is (p+1) x ceil((p+1)/2)^2
-// vector loads from the quad array (L2-resident for the point workloads).
+// run in FP32 on the FMA pipe; the span block is (p+1) x ceil((p+1)/2) x
+// ceil((p+1)/4) vector loads from the row array (L2-resident for the point
+// workloads), one L2 sector each in FP32.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -43,22 +44,19 @@ __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const fl
         float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
         if constexpr (P <= 3) {
             // the whole block in flight before the basis is evaluated
-            float4 q[P + 1][Block<P>::JP][Block<P>::IQ];
-            load_block<P, T>(mv.quads, base, n0, n01, q);
+            Row q[P + 1][Block<P>::JP][Block<P>::IR];
+            load_block<P, T>(mv.rows, base, n0, n01, q);
             basis<P>(fmaf(u, mf0, -static_cast<float>(k0)), k0, mv.m[0], Nu, dNu);
             basis<P>(fmaf(v, mf1, -static_cast<float>(k1)), k1, mv.m[1], Nv, dNv);
             basis<P>(fmaf(w, mf2, -static_cast<float>(k2)), k2, mv.m[2], Nw, dNw);
             contract_pairs<P>(Nu, dNu, Nv, dNv, Nw, dNw,
-                              [&](int k, int jp, int i) { return quad_pair<P>(q, k, jp, i); }, r);
+                              [&](int k, int jp, int i) { return block_pair<P>(q, k, jp, i); }, r);
         } else {
             basis<P>(fmaf(u, mf0, -static_cast<float>(k0)), k0, mv.m[0], Nu, dNu);
             basis<P>(fmaf(v, mf1, -static_cast<float>(k1)), k1, mv.m[1], Nv, dNv);
             basis<P>(fmaf(w, mf2, -static_cast<float>(k2)), k2, mv.m[2], Nw, dNw);
             contract_pairs<P>(Nu, dNu, Nv, dNv, Nw, dNw,
-                              [&](int k, int jp, int i) {
-                                  const float4 qv = QuadLoad<T>::at(mv.quads, base + (i & ~1) + 2 * jp * n0 + k * n01);
-                                  return (i & 1) ? make_float2(qv.z, qv.w) : make_float2(qv.x, qv.y);
-                              },
+                              [&](int k, int jp, int i) { return row_pair<T>(mv.rows, base, n0, n01, k, jp, i); },
                               r);
         }
         out[idx] = make_float4(r[0] * sv, r[1] * s0, r[2] * s1, r[3] * s2);
@@ -100,39 +98,45 @@ cudaError_t launch_eval_dtype(const ModelView &mv, const float *params, int64_t 
     }
 }
 
-__device__ __forceinline__ void store_quad(float4 *q, int64_t i, float a, float b, float c, float d)
+__device__ __forceinline__ unsigned pack2(float a, float b, __half)
 {
-    q[i] = make_float4(a, b, c, d);
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const unsigned *>(&h);
 }
-__device__ __forceinline__ void store_quad(uint2 *q, int64_t i, float a, float b, float c, float d, __half)
+__device__ __forceinline__ unsigned pack2(float a, float b, __nv_bfloat16)
 {
-    const __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
-    q[i] = make_uint2(*reinterpret_cast<const unsigned *>(&lo), *reinterpret_cast<const unsigned *>(&hi));
-}
-__device__ __forceinline__ void store_quad(uint2 *q, int64_t i, float a, float b, float c, float d, __nv_bfloat16)
-{
-    const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
-    q[i] = make_uint2(*reinterpret_cast<const unsigned *>(&lo), *reinterpret_cast<const unsigned *>(&hi));
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const unsigned *>(&h);
 }
 
-// One thread per lattice point (i, j, k): gathers P(i..i+1, j..j+1, k),
-// zero past the lattice, scales by inv_scale, rounds to the storage type.
+// One thread per lattice point (i, j, k): gathers P(i..i+3, j..j+1, k) as
+// (j, j+1) pairs, zero past the lattice, scales by inv_scale, rounds to the
+// storage type.
 template <typename T>
-__global__ void build_quads_kernel(const float *__restrict__ src, void *__restrict__ dst, int n0, int n1, int n2,
-                                   float inv_scale)
+__global__ void build_rows_kernel(const float *__restrict__ src, void *__restrict__ dst, int n0, int n1, int n2,
+                                  float inv_scale)
 {
     const int64_t total = static_cast<int64_t>(n0) * n1 * n2;
     for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
          e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int i = static_cast<int>(e % n0);
         const int j = static_cast<int>((e / n0) % n1);
-        const bool ri = i + 1 < n0, rj = j + 1 < n1;
-        const float a = src[e] * inv_scale;
-        const float b = rj ? src[e + n0] * inv_scale : 0.0f;
-        const float c = ri ? src[e + 1] * inv_scale : 0.0f;
-        const float d = (ri && rj) ? src[e + n0 + 1] * inv_scale : 0.0f;
-        if constexpr (sizeof(T) == 4) store_quad(static_cast<float4 *>(dst), e, a, b, c, d);
-        else store_quad(static_cast<uint2 *>(dst), e, a, b, c, d, T());
+        const bool rj = j + 1 < n1;
+        float v[8];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            const bool ri = i + d < n0;
+            v[2 * d] = ri ? src[e + d] * inv_scale : 0.0f;
+            v[2 * d + 1] = (ri && rj) ? src[e + d + n0] * inv_scale : 0.0f;
+        }
+        if constexpr (sizeof(T) == 4) {
+            float4 *q = static_cast<float4 *>(dst) + 2 * e;
+            q[0] = make_float4(v[0], v[1], v[2], v[3]);
+            q[1] = make_float4(v[4], v[5], v[6], v[7]);
+        } else {
+            static_cast<uint4 *>(dst)[e] =
+                make_uint4(pack2(v[0], v[1], T()), pack2(v[2], v[3], T()), pack2(v[4], v[5], T()), pack2(v[6], v[7], T()));
+        }
     }
 }
 
@@ -150,21 +154,21 @@ cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t
     }
 }
 
-cudaError_t launch_build_quads(const float *src, void *quads, int n0, int n1, int n2, int dtype, float inv_scale,
-                               cudaStream_t stream)
+cudaError_t launch_build_rows(const float *src, void *rows, int n0, int n1, int n2, int dtype, float inv_scale,
+                              cudaStream_t stream)
 {
     const int64_t total = static_cast<int64_t>(n0) * n1 * n2;
     if (total <= 0) return cudaSuccess;
     const int blocks = static_cast<int>((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
     switch (dtype) {
     case MFADVR_F32:
-        build_quads_kernel<float><<<blocks, 256, 0, stream>>>(src, quads, n0, n1, n2, inv_scale);
+        build_rows_kernel<float><<<blocks, 256, 0, stream>>>(src, rows, n0, n1, n2, inv_scale);
         break;
     case MFADVR_F16:
-        build_quads_kernel<__half><<<blocks, 256, 0, stream>>>(src, quads, n0, n1, n2, inv_scale);
+        build_rows_kernel<__half><<<blocks, 256, 0, stream>>>(src, rows, n0, n1, n2, inv_scale);
         break;
     case MFADVR_BF16:
-        build_quads_kernel<__nv_bfloat16><<<blocks, 256, 0, stream>>>(src, quads, n0, n1, n2, inv_scale);
+        build_rows_kernel<__nv_bfloat16><<<blocks, 256, 0, stream>>>(src, rows, n0, n1, n2, inv_scale);
         break;
     default: return cudaErrorInvalidValue;
     }

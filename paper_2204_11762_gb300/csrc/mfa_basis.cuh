@@ -274,48 +274,65 @@ __device__ __forceinline__ int span_exact(float u, int m, float mf)
 }
 
 // ---------------------------------------------------------------------------
-// Quad layout of the control points.  Entry (i, j, k) of the quad array holds
-//   {P(i,j,k), P(i,j+1,k), P(i+1,j,k), P(i+1,j+1,k)}
-// (zero where i+1 or j+1 runs past the lattice), so the (p+1) x (p+1) block
-// of a k-slice under any span is ceil((p+1)/2)^2 aligned vector loads, and
-// each load yields two (P(i,j), P(i,j+1)) pairs ready for packed FMAs.
-// FP32 entries are 16 bytes, FP16/BF16 entries 8 bytes.
+// Row layout of the control points.  Entry (i, j, k) of the row array holds
+// the 4 x 2 points P(i+d, j+e, k), d = 0..3, e = 0..1, as the four pairs
+//   (P(i+d, j, k), P(i+d, j+1, k)),   d = 0..3
+// (zero where i+d or j+1 runs past the lattice).  A (p+1) x (p+1) k-slice of
+// the block under a span is then ceil((p+1)/2) x ceil((p+1)/4) entries, and
+// every entry yields pairs ready for packed FMAs.  FP32 entries are 32 bytes
+// (one 256-bit load, one L2 sector); FP16/BF16 entries 16 bytes.
 // ---------------------------------------------------------------------------
+struct Row {
+    float2 p[4];
+};
+
 template <typename T>
-struct QuadLoad;
+struct RowLoad;
 template <>
-struct QuadLoad<float> {
-    static __device__ __forceinline__ float4 at(const void *q, int idx)
+struct RowLoad<float> {
+    static __device__ __forceinline__ Row at(const void *rows, int idx)
     {
-        return __ldg(static_cast<const float4 *>(q) + idx);
+        const float *a = static_cast<const float *>(rows) + 8 * static_cast<int64_t>(idx);
+        Row r;
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(r.p[0].x), "=f"(r.p[0].y), "=f"(r.p[1].x), "=f"(r.p[1].y), "=f"(r.p[2].x), "=f"(r.p[2].y),
+              "=f"(r.p[3].x), "=f"(r.p[3].y)
+            : "l"(a));
+        return r;
     }
 };
 template <>
-struct QuadLoad<__half> {
-    static __device__ __forceinline__ float4 at(const void *q, int idx)
+struct RowLoad<__half> {
+    static __device__ __forceinline__ Row at(const void *rows, int idx)
     {
-        const uint2 raw = __ldg(static_cast<const uint2 *>(q) + idx);
-        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
-        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
-        return make_float4(a.x, a.y, b.x, b.y);
+        const uint4 raw = __ldg(static_cast<const uint4 *>(rows) + idx);
+        Row r;
+        r.p[0] = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
+        r.p[1] = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
+        r.p[2] = __half22float2(*reinterpret_cast<const __half2 *>(&raw.z));
+        r.p[3] = __half22float2(*reinterpret_cast<const __half2 *>(&raw.w));
+        return r;
     }
 };
 template <>
-struct QuadLoad<__nv_bfloat16> {
-    static __device__ __forceinline__ float4 at(const void *q, int idx)
+struct RowLoad<__nv_bfloat16> {
+    static __device__ __forceinline__ Row at(const void *rows, int idx)
     {
-        const uint2 raw = __ldg(static_cast<const uint2 *>(q) + idx);
-        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.x));
-        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.y));
-        return make_float4(a.x, a.y, b.x, b.y);
+        const uint4 raw = __ldg(static_cast<const uint4 *>(rows) + idx);
+        Row r;
+        r.p[0] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.x));
+        r.p[1] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.y));
+        r.p[2] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.z));
+        r.p[3] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.w));
+        return r;
     }
 };
 
-// Pairs per j-column and quads per i-row of a span block.
+// Pairs per j-column and row entries per i-run of a span block.
 template <int P>
 struct Block {
     static constexpr int JP = (P + 2) / 2;  // j pairs (the last one padded when P is even)
-    static constexpr int IQ = (P + 2) / 2;  // quads along i
+    static constexpr int IR = (P + 4) / 4;  // row entries along i
 };
 
 // Sum-factorised contraction of the (P+1)^3 control points under a span
@@ -366,27 +383,33 @@ __device__ __forceinline__ void contract_pairs(const float Nu[P + 1], const floa
     r[3] = fw;
 }
 
-// Loads the quads of the span block whose first control point is quad index
-// `base` (= i0 + n0*(j0 + n1*k0)) into q[k][jp][iq].
+// Loads the row entries of the span block whose first control point is
+// entry index `base` (= i0 + n0*(j0 + n1*k0)) into q[k][jp][ir].
 template <int P, typename T>
-__device__ __forceinline__ void load_block(const void *quads, int base, int n0, int n01,
-                                           float4 (&q)[P + 1][Block<P>::JP][Block<P>::IQ])
+__device__ __forceinline__ void load_block(const void *rows, int base, int n0, int n01,
+                                           Row (&q)[P + 1][Block<P>::JP][Block<P>::IR])
 {
 #pragma unroll
     for (int k = 0; k <= P; ++k)
 #pragma unroll
         for (int jp = 0; jp < Block<P>::JP; ++jp)
 #pragma unroll
-            for (int iq = 0; iq < Block<P>::IQ; ++iq)
-                q[k][jp][iq] = QuadLoad<T>::at(quads, base + 2 * iq + 2 * jp * n0 + k * n01);
+            for (int ir = 0; ir < Block<P>::IR; ++ir)
+                q[k][jp][ir] = RowLoad<T>::at(rows, base + 4 * ir + 2 * jp * n0 + k * n01);
 }
 
+// Pair (P(i0+i, j0+2jp, k0+k), P(i0+i, j0+2jp+1, k0+k)) of a loaded block.
 template <int P>
-__device__ __forceinline__ float2 quad_pair(const float4 (&q)[P + 1][Block<P>::JP][Block<P>::IQ], int k, int jp,
-                                            int i)
+__device__ __forceinline__ float2 block_pair(const Row (&q)[P + 1][Block<P>::JP][Block<P>::IR], int k, int jp, int i)
 {
-    const float4 v = q[k][jp][i >> 1];
-    return (i & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+    return q[k][jp][i >> 2].p[i & 3];
+}
+
+// The same pair read from the row array directly (no block in registers).
+template <typename T>
+__device__ __forceinline__ float2 row_pair(const void *rows, int base, int n0, int n01, int k, int jp, int i)
+{
+    return RowLoad<T>::at(rows, base + (i & ~3) + 2 * jp * n0 + k * n01).p[i & 3];
 }
 
 }  // namespace mfadvr

@@ -13,10 +13,10 @@ namespace mfadvr {
 constexpr float basis_scale_host(int p) { return p == 3 ? 6.0f : 1.0f; }
 
 // A resident model as the kernels see it.  The control points live in the
-// quad layout (see mfa_basis.cuh): entry (i, j, k) at i + n[0]*(j + n[1]*k)
-// holds {P(i,j,k), P(i,j+1,k), P(i+1,j,k), P(i+1,j+1,k)} in the storage type.
+// row layout (see mfa_basis.cuh): entry (i, j, k) at i + n[0]*(j + n[1]*k)
+// holds the pairs (P(i+d,j,k), P(i+d,j+1,k)), d = 0..3, in the storage type.
 struct ModelView {
-    const void *quads;
+    const void *rows;
     int n[3];       // control points per axis
     int n01;        // n[0] * n[1]
     int m[3];       // knot spans per axis, m = n - p
@@ -74,10 +74,12 @@ cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, int *count
 // is zeroed on `stream` first.
 cudaError_t launch_render_batch(int p, int dtype, const RenderJob *jobs_dev, int njobs, int total_tiles,
                                 int ctas_per_sm, int *counter, cudaStream_t stream);
-// Builds the quad array of an n0 x n1 x n2 FP32 lattice (device memory),
+// Bytes of one row-layout entry (8 control points) in a storage type.
+constexpr size_t row_entry_bytes(int dtype) { return dtype == MFADVR_F32 ? 32 : 16; }
+// Builds the row array of an n0 x n1 x n2 FP32 lattice (device memory),
 // scaling by inv_scale and rounding to the storage type.
-cudaError_t launch_build_quads(const float *src, void *quads, int n0, int n1, int n2, int dtype, float inv_scale,
-                               cudaStream_t stream);
+cudaError_t launch_build_rows(const float *src, void *rows, int n0, int n1, int n2, int dtype, float inv_scale,
+                              cudaStream_t stream);
 
 // Render setup for a caller-owned FP32 lattice outside any context, and the
 // context-free error sink (mfadvr_last_error(NULL)); both in mfadvr_api.cu.

@@ -67,7 +67,7 @@ bool finite3(const float v[3]) { return std::isfinite(v[0]) && std::isfinite(v[1
 ModelView view_of(const Model &m)
 {
     ModelView v;
-    v.quads = m.d_quads;
+    v.rows = m.d_rows;
     v.n01 = m.n[0] * m.n[1];
     v.p = m.p;
     v.dtype = m.dtype;
@@ -79,7 +79,6 @@ ModelView view_of(const Model &m)
     return v;
 }
 
-size_t quad_size(int dtype) { return dtype == MFADVR_F32 ? 16 : 8; }
 
 mfadvr_status next_counter(mfadvr_ctx *ctx, int **out)
 {
@@ -359,7 +358,7 @@ mfadvr_status mfadvr_destroy(mfadvr_ctx *ctx)
         DeviceGuard g(ctx->device);
         cudaDeviceSynchronize();
         for (auto &kv : ctx->models)
-            if (kv.second.d_quads) cudaFree(kv.second.d_quads);
+            if (kv.second.d_rows) cudaFree(kv.second.d_rows);
         if (ctx->counters) cudaFree(ctx->counters);
         if (ctx->d_jobs) cudaFree(ctx->d_jobs);
         if (ctx->h_jobs) cudaFreeHost(ctx->h_jobs);
@@ -420,7 +419,7 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
     m.pmax = pmax;
     m.pabs = pabs;
     m.scale = (desc->storage == MFADVR_F32 || pabs == 0.0f) ? 1.0f : pabs;
-    m.bytes = count * quad_size(m.dtype);
+    m.bytes = count * row_entry_bytes(m.dtype);
     if (ctx->budget && ctx->used + m.bytes > ctx->budget)
         return fail(ctx, MFADVR_ENOMEM, "model of %llu bytes exceeds the HBM budget (%llu of %llu used)",
                     static_cast<unsigned long long>(m.bytes), static_cast<unsigned long long>(ctx->used),
@@ -428,10 +427,10 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
 
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
-    cudaError_t e = cudaMalloc(&m.d_quads, m.bytes);
+    cudaError_t e = cudaMalloc(&m.d_rows, m.bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        m.d_quads = nullptr;
+        m.d_rows = nullptr;
         return fail(ctx, MFADVR_ENOMEM, "cudaMalloc(%llu): %s", static_cast<unsigned long long>(m.bytes),
                     cudaGetErrorString(e));
     }
@@ -439,12 +438,12 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
     e = cudaMalloc(&tmp, count * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(tmp, desc->ctrl, count * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = launch_build_quads(static_cast<const float *>(tmp), m.d_quads, m.n[0], m.n[1], m.n[2], m.dtype,
-                               1.0f / m.scale, nullptr);
+        e = launch_build_rows(static_cast<const float *>(tmp), m.d_rows, m.n[0], m.n[1], m.n[2], m.dtype,
+                              1.0f / m.scale, nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) {
-        cudaFree(m.d_quads);
+        cudaFree(m.d_rows);
         return cuda_fail(ctx, e, "model upload");
     }
     const int32_t id = ctx->next_id++;
@@ -461,7 +460,7 @@ mfadvr_status mfadvr_unload_model(mfadvr_ctx *ctx, int32_t model_id)
     if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
-    cudaFree(m->d_quads);
+    cudaFree(m->d_rows);
     ctx->used -= m->bytes;
     ctx->models.erase(model_id);
     return MFADVR_OK;

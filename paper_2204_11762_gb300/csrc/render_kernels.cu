@@ -14,8 +14,9 @@
 // tile pool, so lanes stay busy however unequal the ray lengths are.  Each
 // lane walks its ray in lattice units (one FMA per axis per sample), keeps
 // the control points of its current span block in registers and reloads
-// them (ceil((p+1)/2)^2 x (p+1) vector loads from the quad array) only when
-// a sample leaves the span.  The contraction runs on packed FP32 FMAs.
+// them (ceil((p+1)/2) x ceil((p+1)/4) x (p+1) vector loads from the row
+// array) only when a sample leaves the span.  The contraction runs on packed
+// FP32 FMAs.
 //
 // The batched kernel runs the same per-ray code over the concatenated tiles
 // of many render jobs (one image of one model each).  A warp keeps its
@@ -37,7 +38,7 @@ constexpr unsigned kFull = 0xffffffffu;
 __device__ __forceinline__ float clamp01f(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }
 
 // The span block is cached in registers up to degree 4; degree 5 (216
-// values) reads it from the quad array at every sample.
+// values) reads it from the row array at every sample.
 template <int P>
 struct CacheCP {
     static constexpr bool value = P <= 4;
@@ -58,7 +59,7 @@ struct LaneRay {
     float X0[3], dX[3], dir[3];  // sample s sits at lattice coordinates X0 + s dX
     float kf[3];                 // current span (local index) per axis, as float
     int kk[3];                   // the same as int
-    int base;                    // quad index of the span block's first control point
+    int base;                    // row-entry index of the span block's first control point
     bool interior;               // all three spans unclamped: uniform pieces apply
     float sf, nsf;               // samples contracted / samples on the ray
     float Cr, Cg, Cb, A;         // premultiplied colour and opacity so far
@@ -215,14 +216,14 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
         ray.interior = span_interior<P>(ray.kk[0], mv.m[0]) && span_interior<P>(ray.kk[1], mv.m[1]) &&
                        span_interior<P>(ray.kk[2], mv.m[2]);
         if constexpr (kCache) {
-            float4 q[P + 1][JP][Block<P>::IQ];
-            load_block<P, T>(mv.quads, ray.base, mv.n[0], mv.n01, q);
+            Row q[P + 1][JP][Block<P>::IR];
+            load_block<P, T>(mv.rows, ray.base, mv.n[0], mv.n01, q);
 #pragma unroll
             for (int k = 0; k <= P; ++k)
 #pragma unroll
                 for (int jp = 0; jp < JP; ++jp)
 #pragma unroll
-                    for (int i = 0; i <= P; ++i) cache.v[k][jp][i] = quad_pair<P>(q, k, jp, i);
+                    for (int i = 0; i <= P; ++i) cache.v[k][jp][i] = block_pair<P>(q, k, jp, i);
         }
     }
     // uniform pieces, replaced from the piece table on clamped spans
@@ -281,11 +282,7 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
     } else {
         const int n0 = mv.n[0], n01 = mv.n01, base = ray.base;
         contract_pairs<P>(Nu, dNu, Nv, dNv, Nw, dNw,
-                          [&](int k, int jp, int i) {
-                              const float4 qv = QuadLoad<T>::at(mv.quads, base + (i & ~1) + 2 * jp * n0 + k * n01);
-                              return (i & 1) ? make_float2(qv.z, qv.w) : make_float2(qv.x, qv.y);
-                          },
-                          ray.r);
+                          [&](int k, int jp, int i) { return row_pair<T>(mv.rows, base, n0, n01, k, jp, i); }, ray.r);
     }
     ray.sf = s + 1.0f;
 

@@ -12,7 +12,7 @@
 // in library-owned memory, and mfadvr_render allocates its ray-tile counter
 // ring on first use.  This entry point allocates nothing.  The caller passes
 // its own FP32 lattice, transfer function and outputs in device memory.  The
-// quad layout the render kernel reads and the ray-tile counter live in one
+// row layout the render kernel reads and the ray-tile counter live in one
 // file-scope device array of fixed size, which every GPU that loads the
 // library holds until the process exits.
 #include <cmath>
@@ -24,10 +24,10 @@
 
 namespace {
 
-// [0, 256): the ray-tile counter; [256, 256 + 16 * MFADVR_NOALLOC_MAX_POINTS):
-// the FP32 quad array of the lattice.
+// [0, 256): the ray-tile counter; [256, 256 + 32 * MFADVR_NOALLOC_MAX_POINTS):
+// the FP32 row array of the lattice.
 constexpr size_t kCounterBytes = 256;
-constexpr size_t kScratchBytes = kCounterBytes + 16ull * MFADVR_NOALLOC_MAX_POINTS;
+constexpr size_t kScratchBytes = kCounterBytes + mfadvr::row_entry_bytes(MFADVR_F32) * MFADVR_NOALLOC_MAX_POINTS;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -107,10 +107,10 @@ extern "C" MFADVR_API mfadvr_status mfadvr_render_lattice_noalloc(
         scratch = g_scratch_ptr[dev];
     }
     int *counter = static_cast<int *>(scratch);
-    void *quads = static_cast<unsigned char *>(scratch) + kCounterBytes;
+    void *rows = static_cast<unsigned char *>(scratch) + kCounterBytes;
 
     mfadvr::ModelView mv;
-    mv.quads = quads;
+    mv.rows = rows;
     mv.p = degree[0];
     mv.dtype = MFADVR_F32;
     mv.scale = 1.0f;
@@ -124,9 +124,9 @@ extern "C" MFADVR_API mfadvr_status mfadvr_render_lattice_noalloc(
     rs.nsamples = nsamples_dev;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // The quads are rebuilt and the counter zeroed (by the render launcher)
+    // The rows are rebuilt and the counter zeroed (by the render launcher)
     // on every call, so nothing a previous call left in the array is read.
-    e = mfadvr::launch_build_quads(ctrl_dev, quads, n[0], n[1], n[2], MFADVR_F32, 1.0f, s);
+    e = mfadvr::launch_build_rows(ctrl_dev, rows, n[0], n[1], n[2], MFADVR_F32, 1.0f, s);
     if (e == cudaSuccess) e = mfadvr::launch_render(mv, rs, counter, s);
     if (e != cudaSuccess) {
         char msg[160];

@@ -79,7 +79,7 @@ def test_eval_parity_16bit_storage(ctx, torch_cuda, orc, storage, p):
     mid = ctx.load_model(ctrl, p, storage=storage)
     info = ctx.model_info(mid)
     assert info["scale"] == pytest.approx(float(np.abs(ctrl).max()))
-    assert info["bytes"] == ctrl.size * 8  # quad layout: 4 values per lattice point
+    assert info["bytes"] == ctrl.size * 16  # row layout: 8 16-bit values per lattice point
     got, sp = _run(ctx, torch_cuda, mid, pts)
     deq = dequantize(ctrl, storage)
     ref, ref_sp = orc.eval_points(deq, p, pts)
@@ -157,8 +157,8 @@ def test_invalid_arguments(ctx, torch_cuda):
 
 def test_hbm_budget(torch_cuda):
     from paper_2204_11762_gb300 import mfadvr
-    with mfadvr.Context(0, hbm_budget_bytes=200_000) as c:
-        a = c.load_model(np.zeros((20, 20, 20), dtype=np.float32), 3)  # 8000 quads x 16 B
+    with mfadvr.Context(0, hbm_budget_bytes=400_000) as c:
+        a = c.load_model(np.zeros((20, 20, 20), dtype=np.float32), 3)  # 8000 row entries x 32 B
         with pytest.raises(mfadvr.MfadvrError) as e:
             c.load_model(np.zeros((20, 20, 20), dtype=np.float32), 3)
         assert e.value.status == mfadvr.ENOMEM
