@@ -47,11 +47,13 @@ def _args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
-    ap.add_argument("--workload", default="gauss128", choices=["gauss128", "noise512", "multi16", "serve48"],
+    ap.add_argument("--workload", default="gauss128",
+                    choices=["gauss128", "noise512", "multi16", "serve48", "sweep"],
                     help="gauss128: 128^3 degree-3 render + 2^24 points (default); "
                          "noise512: 512^3 degree-4 render at 3840x2160; "
                          "multi16: one batched render of 16 models of degree 2-5; "
-                         "serve48: 2000 Poisson requests over 48 resident models through the serving loop")
+                         "serve48: 2000 Poisson requests over 48 resident models through the serving loop; "
+                         "sweep: value / gradient / combined query time vs lattice size and degree")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 16-bit storage comparison")
@@ -558,6 +560,88 @@ def run_multi16(args, jobs):
         print(json.dumps(line), flush=True)
 
 
+SWEEP_DEGREES = (1, 2, 3, 4, 5)
+SWEEP_SIZES = (32, 64, 128, 256, 512)
+SWEEP_MODES = (("value", 1), ("gradient", 2), ("both", 3))
+
+
+def _query_fma(p, mode):
+    a = p + 1
+    return {1: a ** 3 + a * a + a, 2: 2 * a ** 3 + 3 * a * a + 3 * a, 3: 2 * a ** 3 + 3 * a * a + 4 * a}[mode]
+
+
+def run_sweep(args):
+    """Query-time sweep of the MFA parameter study (Sec. 4.3.3, Fig. 12): the
+    time of one value query, one gradient query and one combined query, per
+    point, for the Gaussian beam (Eq. 1) on n^3 control points, n in
+    {32..512}, degrees 1-5, over 2^24 U[0,1]^3 points (inputs larger than L2).
+    The headline value is the combined query at degree 3 on 256^3, the
+    paper's beam size."""
+    import numpy as np
+    import torch
+
+    from paper_2204_11762_gb300 import mfadvr, workloads
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    npts = 1 << 24
+    steps = max(3, min(args.steps, 20))
+    rng = np.random.default_rng(workloads.seed_for(6))
+    pts = workloads.uniform_points(rng, npts)
+    d_pts = torch.from_numpy(pts).to(dev)
+    d_out = torch.empty((npts, 4), device=dev)
+    table, launches = {}, 0
+    clocks = ClockSampler(local)
+    clocks.start()
+    with mfadvr.Context(local) as ctx:
+        for n in SWEEP_SIZES:
+            for p in SWEEP_DEGREES:
+                # control points at the degree's Greville abscissae
+                mid = ctx.load_model(workloads.gaussian_beam_lattice((n, n, n), p), p)
+                row = {}
+                for name, q in SWEEP_MODES:
+                    for _ in range(3):
+                        ctx.query_points(mid, d_pts, npts, d_out, q, stream=stream)
+                    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                          for _ in range(steps)]
+                    for e0, e1 in ev:
+                        e0.record(stream)
+                        ctx.query_points(mid, d_pts, npts, d_out, q, stream=stream)
+                        e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    launches += steps
+                    ms = statistics.median(e0.elapsed_time(e1) for e0, e1 in ev)
+                    row[name] = {"ns_per_query": ms * 1e6 / npts, "queries_per_s": npts / (ms / 1000.0),
+                                 "tflops": npts * _query_fma(p, q) * 2 / (ms / 1000.0) / 1e12}
+                table[f"p{p}_n{n}"] = row
+                ctx.unload_model(mid)
+    clk = clocks.stop()
+    head = table["p3_n256"]["both"]
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = (clk or {}).get("sm_max_mhz") or _measured_peaks().get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    peak_src = f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 FLOP x {sm_max:.0f} MHz"
+    line = {"metric": METRIC, "value": head["queries_per_s"], "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": 3, "ms_per_step": npts / head["queries_per_s"] * 1000.0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sweep: query time of mfadvr_query_points (value / gradient / both) on the "
+                                   "Gaussian beam (Eq. 1) at the Greville abscissae, n^3 control points for n in "
+                                   f"{list(SWEEP_SIZES)}, degrees {list(SWEEP_DEGREES)}, 2^24 U[0,1]^3 points; "
+                                   "headline: both, degree 3, 256^3",
+                       "l2": "inputs larger than L2 (2^24 points: 201 MB in, 268 MB out)"},
+            "gpu_launches": launches,
+            "roofline": {"kernel": "eval_points_kernel", "bound": "alu", "achieved": head["tflops"], "peak": peak,
+                         "unit": "TFLOP/s", "frac": head["tflops"] / peak, "traffic": None,
+                         "peak_source": peak_src,
+                         "per_unit": "192 FMA per combined query (degree 3); the kernel is bound by the L1/L2 "
+                                     "sector rate of the control-point gathers"},
+            "clocks": clk, "sweep": table}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def _pct(xs, q):
     xs = sorted(xs)
     return xs[min(len(xs) - 1, int(q * len(xs)))]
@@ -729,6 +813,13 @@ def main():
                                                                    "default workload only"}))
             return
         run_multi16(args, workloads.multi_model_workload())
+        return
+    if args.workload == "sweep":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm is timed on the "
+                                                                   "default workload only"}))
+            return
+        run_sweep(args)
         return
     wl = workloads.gaussian_sum_workload()
     if args.impl == "reference":

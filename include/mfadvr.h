@@ -150,6 +150,31 @@ MFADVR_API mfadvr_status mfadvr_eval_points(mfadvr_ctx *ctx, int32_t model_id, c
 MFADVR_API mfadvr_status mfadvr_eval_points_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_host,
                                       int64_t n, float *out_host, int32_t *spans_host, void *stream);
 
+/* What a point query returns: the value alone (queryValueMFA), the gradient
+ * alone (queryGradientMFA), or both (Algorithm 1; the parameter study of
+ * Sec. 4.3.3 times each of the three).  Only the sums a query needs are
+ * formed: per point (p+1)^3 + (p+1)^2 + (p+1) multiply-adds for the value,
+ * 2(p+1)^3 + 3(p+1)^2 + 3(p+1) for the gradient, 2(p+1)^3 + 3(p+1)^2 + 4(p+1)
+ * for both. */
+typedef enum {
+    MFADVR_QUERY_VALUE = 1,    /* out: n FP32 f, 4-byte aligned */
+    MFADVR_QUERY_GRADIENT = 2, /* out: n x 3 FP32 (df/du, df/dv, df/dw), 4-byte aligned */
+    MFADVR_QUERY_BOTH = 3      /* out: n x 4 FP32 (f, df/du, df/dv, df/dw), 16-byte aligned */
+} mfadvr_query;
+
+/* mfadvr_eval_points for one mfadvr_query (an int32 here); with
+ * MFADVR_QUERY_BOTH it is mfadvr_eval_points.  params_dev and spans_dev as
+ * there; out_dev laid out as the query says.  Each output equals the same
+ * component of MFADVR_QUERY_BOTH bit for bit.  EINVAL: an unknown query,
+ * plus mfadvr_eval_points' cases. */
+MFADVR_API mfadvr_status mfadvr_query_points(mfadvr_ctx *ctx, int32_t model_id, const float *params_dev, int64_t n,
+                                  int32_t query, float *out_dev, int32_t *spans_dev, void *stream);
+
+/* mfadvr_query_points with HOST buffers, as mfadvr_eval_points_host. */
+MFADVR_API mfadvr_status mfadvr_query_points_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_host,
+                                       int64_t n, int32_t query, float *out_host, int32_t *spans_host,
+                                       void *stream);
+
 /* Ray-cast one image (Algorithm 1): per pixel, march the ray through the
  * model's world box, query value (+ gradient when shading), map through the
  * transfer function, shade, composite front to back and stop early once the

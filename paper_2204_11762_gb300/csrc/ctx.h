@@ -118,10 +118,11 @@ mfadvr_status make_job(mfadvr_ctx *ctx, const mfadvr_render_job &job, int index,
 // One launch of a batched render: jobs dst[first, first+count) of one degree
 // and storage type, `tiles` tiles in all.
 struct BatchGroup {
-    int p, dtype, first, count, tiles;
+    int p, dtype, grad, first, count, tiles;
 };
-// Orders n jobs by (degree, storage type) into dst, fills their tile fields
-// and returns the launch groups.
+// Orders n jobs by (degree, storage type, shading) into dst, fills their tile
+// fields and returns the launch groups (grad = shading: the gradient is
+// queried).
 std::vector<BatchGroup> pack_jobs(const RenderJob *jobs, int n, RenderJob *dst);
 // Tears down a context's serving loop, if one runs (serve.cu).
 void stop_server(mfadvr_ctx *ctx);

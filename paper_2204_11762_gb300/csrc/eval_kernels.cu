@@ -17,9 +17,9 @@
 namespace mfadvr {
 namespace {
 
-template <int P, typename T>
+template <int P, typename T, int Q>
 __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const float *__restrict__ params,
-                                                          int64_t n, float4 *__restrict__ out,
+                                                          int64_t n, float *__restrict__ out,
                                                           int32_t *__restrict__ spans)
 {
     const float mf0 = static_cast<float>(mv.m[0]);
@@ -51,17 +51,24 @@ __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const fl
             basis<P>(fmaf(u, mf0, -static_cast<float>(k0)), k0, mv.m[0], Nu, dNu);
             basis<P>(fmaf(v, mf1, -static_cast<float>(k1)), k1, mv.m[1], Nv, dNv);
             basis<P>(fmaf(w, mf2, -static_cast<float>(k2)), k2, mv.m[2], Nw, dNw);
-            contract_pairs<P>(Nu, dNu, Nv, dNv, Nw, dNw,
-                              [&](int k, int jp, int i) { return block_pair<P>(q, k, jp, i); }, r);
+            contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return block_pair<P>(q, k, jp, i); },
+                           r);
         } else {
             basis<P>(fmaf(u, mf0, -static_cast<float>(k0)), k0, mv.m[0], Nu, dNu);
             basis<P>(fmaf(v, mf1, -static_cast<float>(k1)), k1, mv.m[1], Nv, dNv);
             basis<P>(fmaf(w, mf2, -static_cast<float>(k2)), k2, mv.m[2], Nw, dNw);
-            contract_pairs<P>(Nu, dNu, Nv, dNv, Nw, dNw,
-                              [&](int k, int jp, int i) { return row_pair<T>(mv.rows, base, n0, n01, k, jp, i); },
-                              r);
+            contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw,
+                           [&](int k, int jp, int i) { return row_pair<T>(mv.rows, base, n0, n01, k, jp, i); }, r);
         }
-        __stcs(out + idx, make_float4(r[0] * sv, r[1] * s0, r[2] * s1, r[3] * s2));
+        if constexpr (Q == kQueryBoth) {
+            __stcs(reinterpret_cast<float4 *>(out) + idx, make_float4(r[0] * sv, r[1] * s0, r[2] * s1, r[3] * s2));
+        } else if constexpr (Q == kQueryValue) {
+            __stcs(out + idx, r[0] * sv);
+        } else {
+            __stcs(out + 3 * idx + 0, r[1] * s0);
+            __stcs(out + 3 * idx + 1, r[2] * s1);
+            __stcs(out + 3 * idx + 2, r[3] * s2);
+        }
         if (spans) {
             __stcs(spans + 3 * idx + 0, k0 + P);
             __stcs(spans + 3 * idx + 1, k1 + P);
@@ -70,32 +77,44 @@ __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const fl
     }
 }
 
-template <int P, typename T>
-cudaError_t launch_eval_t(const ModelView &mv, const float *params, int64_t n, float4 *out, int32_t *spans,
+template <int P, typename T, int Q>
+cudaError_t launch_eval_q(const ModelView &mv, const float *params, int64_t n, float *out, int32_t *spans,
                           cudaStream_t stream)
 {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval_points_kernel<P, T>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval_points_kernel<P, T, Q>, 256, 0);
     if (per_sm < 1) per_sm = 1;
     const int64_t need = (n + 255) / 256;
     const int64_t cap = static_cast<int64_t>(sms) * per_sm;
     const int blocks = static_cast<int>(need < cap ? need : cap);
-    eval_points_kernel<P, T><<<blocks, 256, 0, stream>>>(mv, params, n, out, spans);
+    eval_points_kernel<P, T, Q><<<blocks, 256, 0, stream>>>(mv, params, n, out, spans);
     return cudaGetLastError();
 }
 
+template <int P, typename T>
+cudaError_t launch_eval_t(const ModelView &mv, const float *params, int64_t n, float *out, int query,
+                          int32_t *spans, cudaStream_t stream)
+{
+    switch (query) {
+    case kQueryValue: return launch_eval_q<P, T, kQueryValue>(mv, params, n, out, spans, stream);
+    case kQueryGradient: return launch_eval_q<P, T, kQueryGradient>(mv, params, n, out, spans, stream);
+    case kQueryBoth: return launch_eval_q<P, T, kQueryBoth>(mv, params, n, out, spans, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename T>
-cudaError_t launch_eval_dtype(const ModelView &mv, const float *params, int64_t n, float4 *out, int32_t *spans,
-                              cudaStream_t stream)
+cudaError_t launch_eval_dtype(const ModelView &mv, const float *params, int64_t n, float *out, int query,
+                              int32_t *spans, cudaStream_t stream)
 {
     switch (mv.p) {
-    case 1: return launch_eval_t<1, T>(mv, params, n, out, spans, stream);
-    case 2: return launch_eval_t<2, T>(mv, params, n, out, spans, stream);
-    case 3: return launch_eval_t<3, T>(mv, params, n, out, spans, stream);
-    case 4: return launch_eval_t<4, T>(mv, params, n, out, spans, stream);
-    case 5: return launch_eval_t<5, T>(mv, params, n, out, spans, stream);
+    case 1: return launch_eval_t<1, T>(mv, params, n, out, query, spans, stream);
+    case 2: return launch_eval_t<2, T>(mv, params, n, out, query, spans, stream);
+    case 3: return launch_eval_t<3, T>(mv, params, n, out, query, spans, stream);
+    case 4: return launch_eval_t<4, T>(mv, params, n, out, query, spans, stream);
+    case 5: return launch_eval_t<5, T>(mv, params, n, out, query, spans, stream);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -144,14 +163,14 @@ __global__ void build_rows_kernel(const float *__restrict__ src, void *__restric
 
 }  // namespace
 
-cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t n, float4 *out, int32_t *spans,
-                               cudaStream_t stream)
+cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t n, float *out, int query,
+                               int32_t *spans, cudaStream_t stream)
 {
     if (n <= 0) return cudaSuccess;
     switch (mv.dtype) {
-    case MFADVR_F32: return launch_eval_dtype<float>(mv, params, n, out, spans, stream);
-    case MFADVR_F16: return launch_eval_dtype<__half>(mv, params, n, out, spans, stream);
-    case MFADVR_BF16: return launch_eval_dtype<__nv_bfloat16>(mv, params, n, out, spans, stream);
+    case MFADVR_F32: return launch_eval_dtype<float>(mv, params, n, out, query, spans, stream);
+    case MFADVR_F16: return launch_eval_dtype<__half>(mv, params, n, out, query, spans, stream);
+    case MFADVR_BF16: return launch_eval_dtype<__nv_bfloat16>(mv, params, n, out, query, spans, stream);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -335,20 +335,35 @@ struct Block {
     static constexpr int IR = (P + 4) / 4;  // row entries along i
 };
 
+// What a query computes: bit 0 the value f, bit 1 the gradient (mfadvr_query).
+constexpr int kQueryValue = 1, kQueryGradient = 2, kQueryBoth = 3;
+
+// Multiply-adds of contract<P, Q>: value only (p+1)^3 + (p+1)^2 + (p+1);
+// gradient only 2(p+1)^3 + 3(p+1)^2 + 3(p+1); both 2(p+1)^3 + 3(p+1)^2 + 4(p+1).
+constexpr int contract_fma(int p, int q)
+{
+    const int a = p + 1;
+    return q == kQueryValue ? a * a * a + a * a + a
+                            : (q == kQueryGradient ? 2 * a * a * a + 3 * a * a + 3 * a : 2 * a * a * a + 3 * a * a + 4 * a);
+}
+
 // Sum-factorised contraction of the (P+1)^3 control points under a span
 // with the tensor-product basis:
 //   f = sum N_i N_j N_k P_ijk,  f_u = sum N'_i N_j N_k P_ijk, f_v, f_w alike.
 // pair(k, jp, i) yields (P(i, 2jp, k), P(i, 2jp+1, k)).  The u sums run on
 // packed FP32 FMAs over j pairs (two rows per instruction), the v and w sums
-// on scalar FMAs: 2(P+1)^3 + 3(P+1)^2 + 4(P+1) multiply-adds (the u sums
-// carry a padded row when P is even).  r = {f, df/dx_u, df/dx_v, df/dx_w} in
-// span-local units, times the product of the three basis scales.
-template <int P, typename PairAt>
-__device__ __forceinline__ void contract_pairs(const float Nu[P + 1], const float dNu[P + 1], const float Nv[P + 1],
-                                               const float dNv[P + 1], const float Nw[P + 1], const float dNw[P + 1],
-                                               PairAt pair, float r[4])
+// on scalar FMAs; Q selects the value, the gradient or both, and only the
+// sums those need are formed (contract_fma counts them; the u sums carry a
+// padded row when P is even).  r = {f, df/dx_u, df/dx_v, df/dx_w} in
+// span-local units, times the product of the three basis scales; entries Q
+// does not ask for are left unset.
+template <int P, int Q, typename PairAt>
+__device__ __forceinline__ void contract(const float Nu[P + 1], const float dNu[P + 1], const float Nv[P + 1],
+                                         const float dNv[P + 1], const float Nw[P + 1], const float dNw[P + 1],
+                                         PairAt pair, float r[4])
 {
     constexpr int JP = Block<P>::JP;
+    constexpr bool kV = (Q & kQueryValue) != 0, kG = (Q & kQueryGradient) != 0;
     float f = 0.f, fu = 0.f, fv = 0.f, fw = 0.f;
 #pragma unroll
     for (int k = 0; k <= P; ++k) {
@@ -360,27 +375,35 @@ __device__ __forceinline__ void contract_pairs(const float Nu[P + 1], const floa
             for (int i = 0; i <= P; ++i) {
                 const float2 pv = pair(k, jp, i);
                 a = __ffma2_rn(make_float2(Nu[i], Nu[i]), pv, a);
-                b = __ffma2_rn(make_float2(dNu[i], dNu[i]), pv, b);
+                if constexpr (kG) b = __ffma2_rn(make_float2(dNu[i], dNu[i]), pv, b);
             }
             // v sums on scalar FMAs: no pair halves to add afterwards
             c = fmaf(Nv[2 * jp], a.x, c);
-            dv = fmaf(dNv[2 * jp], a.x, dv);
-            e = fmaf(Nv[2 * jp], b.x, e);
+            if constexpr (kG) {
+                dv = fmaf(dNv[2 * jp], a.x, dv);
+                e = fmaf(Nv[2 * jp], b.x, e);
+            }
             if (2 * jp + 1 <= P) {
                 c = fmaf(Nv[2 * jp + 1], a.y, c);
-                dv = fmaf(dNv[2 * jp + 1], a.y, dv);
-                e = fmaf(Nv[2 * jp + 1], b.y, e);
+                if constexpr (kG) {
+                    dv = fmaf(dNv[2 * jp + 1], a.y, dv);
+                    e = fmaf(Nv[2 * jp + 1], b.y, e);
+                }
             }
         }
-        f = fmaf(Nw[k], c, f);
-        fw = fmaf(dNw[k], c, fw);
-        fv = fmaf(Nw[k], dv, fv);
-        fu = fmaf(Nw[k], e, fu);
+        if constexpr (kV) f = fmaf(Nw[k], c, f);
+        if constexpr (kG) {
+            fw = fmaf(dNw[k], c, fw);
+            fv = fmaf(Nw[k], dv, fv);
+            fu = fmaf(Nw[k], e, fu);
+        }
     }
-    r[0] = f;
-    r[1] = fu;
-    r[2] = fv;
-    r[3] = fw;
+    if constexpr (kV) r[0] = f;
+    if constexpr (kG) {
+        r[1] = fu;
+        r[2] = fv;
+        r[3] = fw;
+    }
 }
 
 // Loads the row entries of the span block whose first control point is

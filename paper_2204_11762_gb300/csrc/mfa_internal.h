@@ -64,15 +64,19 @@ struct RenderJob {
 static_assert(sizeof(RenderJob) % 8 == 0, "RenderJob is copied in 8-byte words");
 
 // Kernel launchers (asynchronous on `stream`).
-cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t n, float4 *out,
+// query is an mfadvr_query: out holds n floats (value), 3n (gradient) or n
+// float4 (both).
+cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t n, float *out, int query,
                                int32_t *spans, cudaStream_t stream);
 // `counter` is one device int the render kernel's warps take ray tiles from;
-// the launcher zeroes it on `stream` first.
+// the launcher zeroes it on `stream` first.  The value-only kernel runs when
+// rs.shading is 0 (no gradient is needed).
 cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream);
-// Batched render of njobs jobs of degree p and storage dtype (jobs_dev in
-// device memory, sorted by tile_begin, total_tiles tiles in all); `counter`
-// is zeroed on `stream` first.
-cudaError_t launch_render_batch(int p, int dtype, const RenderJob *jobs_dev, int njobs, int total_tiles,
+// Batched render of njobs jobs of degree p and storage dtype, all with
+// shading on (grad = 1) or all off (grad = 0) (jobs_dev in device memory,
+// sorted by tile_begin, total_tiles tiles in all); `counter` is zeroed on
+// `stream` first.
+cudaError_t launch_render_batch(int p, int dtype, int grad, const RenderJob *jobs_dev, int njobs, int total_tiles,
                                 int ctas_per_sm, int *counter, cudaStream_t stream);
 // Bytes of one row-layout entry (8 control points) in a storage type.
 constexpr size_t row_entry_bytes(int dtype) { return dtype == MFADVR_F32 ? 32 : 16; }

@@ -278,14 +278,15 @@ std::vector<BatchGroup> pack_jobs(const RenderJob *jobs, int n, RenderJob *dst)
 {
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        return std::make_pair(jobs[a].mv.p, jobs[a].mv.dtype) < std::make_pair(jobs[b].mv.p, jobs[b].mv.dtype);
-    });
+    auto key = [&](int a) { return std::make_tuple(jobs[a].mv.p, jobs[a].mv.dtype, jobs[a].rs.shading != 0); };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
     std::vector<BatchGroup> groups;
     for (int k = 0; k < n; ++k) {
         RenderJob jb = jobs[order[k]];
-        if (groups.empty() || groups.back().p != jb.mv.p || groups.back().dtype != jb.mv.dtype)
-            groups.push_back({jb.mv.p, jb.mv.dtype, k, 0, 0});
+        const int grad = jb.rs.shading != 0 ? 1 : 0;
+        if (groups.empty() || groups.back().p != jb.mv.p || groups.back().dtype != jb.mv.dtype ||
+            groups.back().grad != grad)
+            groups.push_back({jb.mv.p, jb.mv.dtype, grad, k, 0, 0});
         BatchGroup &gr = groups.back();
         const int tw = 1 << jb.rs.tile_w_log2, th = 32 / tw;
         jb.tiles_x = (jb.rs.width + tw - 1) / tw;
@@ -330,6 +331,79 @@ mfadvr_status mfadvr::setup_for_lattice(int p, const int n[3], const float box_m
 }
 
 mfadvr_status mfadvr::fail_noctx(mfadvr_status st, const char *msg) { return fail(nullptr, st, "%s", msg); }
+
+namespace {
+
+// Output bytes per point of a query, 0 for an unknown query.
+size_t query_out_bytes(int32_t query)
+{
+    switch (query) {
+    case MFADVR_QUERY_VALUE: return 4;
+    case MFADVR_QUERY_GRADIENT: return 12;
+    case MFADVR_QUERY_BOTH: return 16;
+    default: return 0;
+    }
+}
+
+mfadvr_status query_device(mfadvr_ctx *ctx, int32_t model_id, const float *params_dev, int64_t n, int32_t query,
+                           float *out_dev, int32_t *spans_dev, void *stream)
+{
+    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
+    Model *m = nullptr;
+    if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
+    if (query_out_bytes(query) == 0) return fail(ctx, MFADVR_EINVAL, "query must be 1 (value), 2 (gradient) or 3");
+    if (n < 0) return fail(ctx, MFADVR_EINVAL, "n must be >= 0");
+    if (n == 0) return MFADVR_OK;
+    if (!params_dev || !out_dev) return fail(ctx, MFADVR_EINVAL, "params and out must not be NULL");
+    const uintptr_t out_align = query == MFADVR_QUERY_BOTH ? 16 : 4;
+    if (reinterpret_cast<uintptr_t>(out_dev) % out_align != 0 || reinterpret_cast<uintptr_t>(params_dev) % 4 != 0 ||
+        reinterpret_cast<uintptr_t>(spans_dev) % 4 != 0)
+        return fail(ctx, MFADVR_EINVAL, "out must be %u-byte aligned, params and spans 4-byte aligned",
+                    static_cast<unsigned>(out_align));
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
+    if (!is_device_ptr(params_dev) || !is_device_ptr(out_dev) || (spans_dev && !is_device_ptr(spans_dev)))
+        return fail(ctx, MFADVR_EINVAL, "params, out and spans must be device pointers");
+    cudaError_t e = launch_eval_points(view_of(*m), params_dev, n, out_dev, query, spans_dev,
+                                       static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "eval_points launch");
+    return MFADVR_OK;
+}
+
+mfadvr_status query_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_host, int64_t n, int32_t query,
+                         float *out_host, int32_t *spans_host, void *stream)
+{
+    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
+    Model *m = nullptr;
+    if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
+    const size_t per = query_out_bytes(query);
+    if (per == 0) return fail(ctx, MFADVR_EINVAL, "query must be 1 (value), 2 (gradient) or 3");
+    if (n < 0) return fail(ctx, MFADVR_EINVAL, "n must be >= 0");
+    if (n == 0) return MFADVR_OK;
+    if (!params_host || !out_host) return fail(ctx, MFADVR_EINVAL, "params and out must not be NULL");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t in_b = static_cast<size_t>(n) * 12;
+    const size_t out_b = (static_cast<size_t>(n) * per + 15) / 16 * 16;
+    const size_t sp_b = spans_host ? static_cast<size_t>(n) * 12 : 0;
+    cudaError_t e = ctx->st_in.reserve(in_b);
+    if (e == cudaSuccess) e = ctx->st_out.reserve(out_b + sp_b);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "staging allocation");
+    float *d_in = static_cast<float *>(ctx->st_in.ptr);
+    float *d_out = static_cast<float *>(ctx->st_out.ptr);
+    int32_t *d_sp = spans_host ? reinterpret_cast<int32_t *>(static_cast<char *>(ctx->st_out.ptr) + out_b) : nullptr;
+    e = cudaMemcpyAsync(d_in, params_host, in_b, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_eval_points(view_of(*m), d_in, n, d_out, query, d_sp, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out_host, d_out, static_cast<size_t>(n) * per, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && d_sp) e = cudaMemcpyAsync(spans_host, d_sp, sp_b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "eval_points_host");
+    return MFADVR_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -482,52 +556,25 @@ mfadvr_status mfadvr_model_info(mfadvr_ctx *ctx, int32_t model_id, float *pmin, 
 mfadvr_status mfadvr_eval_points(mfadvr_ctx *ctx, int32_t model_id, const float *params_dev, int64_t n,
                                  float *out_dev, int32_t *spans_dev, void *stream)
 {
-    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
-    Model *m = nullptr;
-    if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
-    if (n < 0) return fail(ctx, MFADVR_EINVAL, "n must be >= 0");
-    if (n == 0) return MFADVR_OK;
-    if (!params_dev || !out_dev) return fail(ctx, MFADVR_EINVAL, "params and out must not be NULL");
-    if (reinterpret_cast<uintptr_t>(out_dev) % 16 != 0 || reinterpret_cast<uintptr_t>(params_dev) % 4 != 0 ||
-        reinterpret_cast<uintptr_t>(spans_dev) % 4 != 0)
-        return fail(ctx, MFADVR_EINVAL, "out must be 16-byte aligned, params and spans 4-byte aligned");
-    DeviceGuard g(ctx->device);
-    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
-    if (!is_device_ptr(params_dev) || !is_device_ptr(out_dev) || (spans_dev && !is_device_ptr(spans_dev)))
-        return fail(ctx, MFADVR_EINVAL, "params, out and spans must be device pointers");
-    cudaError_t e = launch_eval_points(view_of(*m), params_dev, n, reinterpret_cast<float4 *>(out_dev), spans_dev,
-                                       static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "eval_points launch");
-    return MFADVR_OK;
+    return query_device(ctx, model_id, params_dev, n, MFADVR_QUERY_BOTH, out_dev, spans_dev, stream);
 }
 
 mfadvr_status mfadvr_eval_points_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_host, int64_t n,
                                       float *out_host, int32_t *spans_host, void *stream)
 {
-    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
-    Model *m = nullptr;
-    if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
-    if (n < 0) return fail(ctx, MFADVR_EINVAL, "n must be >= 0");
-    if (n == 0) return MFADVR_OK;
-    if (!params_host || !out_host) return fail(ctx, MFADVR_EINVAL, "params and out must not be NULL");
-    DeviceGuard g(ctx->device);
-    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const size_t in_b = static_cast<size_t>(n) * 12, out_b = static_cast<size_t>(n) * 16;
-    const size_t sp_b = spans_host ? static_cast<size_t>(n) * 12 : 0;
-    cudaError_t e = ctx->st_in.reserve(in_b);
-    if (e == cudaSuccess) e = ctx->st_out.reserve(out_b + sp_b);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "staging allocation");
-    float *d_in = static_cast<float *>(ctx->st_in.ptr);
-    float4 *d_out = static_cast<float4 *>(ctx->st_out.ptr);
-    int32_t *d_sp = spans_host ? reinterpret_cast<int32_t *>(static_cast<char *>(ctx->st_out.ptr) + out_b) : nullptr;
-    e = cudaMemcpyAsync(d_in, params_host, in_b, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_eval_points(view_of(*m), d_in, n, d_out, d_sp, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, d_out, out_b, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && d_sp) e = cudaMemcpyAsync(spans_host, d_sp, sp_b, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "eval_points_host");
-    return MFADVR_OK;
+    return query_host(ctx, model_id, params_host, n, MFADVR_QUERY_BOTH, out_host, spans_host, stream);
+}
+
+mfadvr_status mfadvr_query_points(mfadvr_ctx *ctx, int32_t model_id, const float *params_dev, int64_t n,
+                                  int32_t query, float *out_dev, int32_t *spans_dev, void *stream)
+{
+    return query_device(ctx, model_id, params_dev, n, query, out_dev, spans_dev, stream);
+}
+
+mfadvr_status mfadvr_query_points_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_host, int64_t n,
+                                       int32_t query, float *out_host, int32_t *spans_host, void *stream)
+{
+    return query_host(ctx, model_id, params_host, n, query, out_host, spans_host, stream);
 }
 
 mfadvr_status mfadvr_render(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_camera *camera,
@@ -621,7 +668,7 @@ mfadvr_status mfadvr_render_batch(mfadvr_ctx *ctx, int32_t njobs, const mfadvr_r
     for (const BatchGroup &gr : groups) {
         int *counter = nullptr;
         if (mfadvr_status st = next_counter(ctx, &counter)) return st;
-        e = launch_render_batch(gr.p, gr.dtype, dj + gr.first, gr.count, gr.tiles, 0, counter, s);
+        e = launch_render_batch(gr.p, gr.dtype, gr.grad, dj + gr.first, gr.count, gr.tiles, 0, counter, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "batched render launch");
     }
     e = cudaEventRecord(ctx->job_done[slot], s);

@@ -184,9 +184,10 @@ __device__ __forceinline__ float lg2_approx(float x)
 // two halves are independent, so the compiler interleaves the contraction's
 // FMAs with the serial TF / shading / compositing chain.  Early termination
 // is decided on the composited sample; the query of sample sf is then
-// dropped, as is the one past the last sample.  Returns true when the ray
-// is finished (pixel written).
-template <int P, typename T, typename Tf>
+// dropped, as is the one past the last sample.  G: the gradient is queried
+// (shading on); without it the value-only contraction runs.  Returns true
+// when the ray is finished (pixel written).
+template <int P, typename T, bool G, typename Tf>
 __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSetup &rs, const Tf &tf, LaneRay &ray,
                                             SpanCache<P> &cache)
 {
@@ -263,7 +264,7 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
         const float spec = rs.ks * __powf(ndl, rs.shininess);
         const float diff = fmaf(rs.kd, ndl, rs.ka);
         const bool flat = g2 <= rs.gthresh2;
-        const bool lit = rs.shading != 0;
+        const bool lit = G && rs.shading != 0;
         cr = lit ? (flat ? cr * rs.ka : clamp01f(fmaf(cr, diff, spec))) : cr;
         cg = lit ? (flat ? cg * rs.ka : clamp01f(fmaf(cg, diff, spec))) : cg;
         cb = lit ? (flat ? cb * rs.ka : clamp01f(fmaf(cb, diff, spec))) : cb;
@@ -277,12 +278,13 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
     ray.A += wgt;
 
     // ---- query of sample s (composited by the next iteration) -------------
+    constexpr int Q = G ? kQueryBoth : kQueryValue;
     if constexpr (kCache) {
-        contract_pairs<P>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return cache.v[k][jp][i]; }, ray.r);
+        contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return cache.v[k][jp][i]; }, ray.r);
     } else {
         const int n0 = mv.n[0], n01 = mv.n01, base = ray.base;
-        contract_pairs<P>(Nu, dNu, Nv, dNv, Nw, dNw,
-                          [&](int k, int jp, int i) { return row_pair<T>(mv.rows, base, n0, n01, k, jp, i); }, ray.r);
+        contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw,
+                       [&](int k, int jp, int i) { return row_pair<T>(mv.rows, base, n0, n01, k, jp, i); }, ray.r);
     }
     ray.sf = s + 1.0f;
 
@@ -298,7 +300,7 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
 // ---------------------------------------------------------------------------
 // One image
 // ---------------------------------------------------------------------------
-template <int P, typename T>
+template <int P, typename T, bool G>
 __global__ void __launch_bounds__(kThreads, MinBlocks<P>::value)
     render_kernel(ModelView mv, RenderSetup rs, int *__restrict__ counter)
 {
@@ -349,14 +351,14 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P>::value)
             if (exhausted && __all_sync(kFull, idle)) break;
         }
         if (idle) continue;
-        if (sample_step<P, T>(mv, rs, tf, ray, cache)) idle = true;
+        if (sample_step<P, T, G>(mv, rs, tf, ray, cache)) idle = true;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Many images (render jobs) of one degree and storage type
 // ---------------------------------------------------------------------------
-template <int P, typename T>
+template <int P, typename T, bool G>
 __global__ void __launch_bounds__(kThreads, MinBlocks<P>::value)
     render_batch_kernel(const RenderJob *__restrict__ jobs, int njobs, int total_tiles, int *__restrict__ counter)
 {
@@ -413,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P>::value)
         }
         if (idle) continue;
         const TfGlobal tf{J.rs.tf};
-        if (sample_step<P, T>(J.mv, J.rs, tf, ray, cache)) idle = true;
+        if (sample_step<P, T, G>(J.mv, J.rs, tf, ray, cache)) idle = true;
     }
 }
 
@@ -425,17 +427,17 @@ int sm_count()
     return sms;
 }
 
-template <int P, typename T>
+template <int P, typename T, bool G>
 cudaError_t launch_render_t(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream)
 {
     const size_t smem = 2 * sizeof(float4) * static_cast<size_t>(rs.tf_size);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(render_kernel<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(render_kernel<P, T, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem));
         if (e != cudaSuccess) return e;
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<P, T>, kThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<P, T, G>, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (rs.ctas_per_sm > 0 && rs.ctas_per_sm < per_sm) per_sm = rs.ctas_per_sm;
@@ -447,16 +449,16 @@ cudaError_t launch_render_t(const ModelView &mv, const RenderSetup &rs, int *cou
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
     if (e != cudaSuccess) return e;
-    render_kernel<P, T><<<static_cast<int>(blocks), kThreads, smem, stream>>>(mv, rs, counter);
+    render_kernel<P, T, G><<<static_cast<int>(blocks), kThreads, smem, stream>>>(mv, rs, counter);
     return cudaGetLastError();
 }
 
-template <int P, typename T>
+template <int P, typename T, bool G>
 cudaError_t launch_batch_t(const RenderJob *jobs, int njobs, int total_tiles, int ctas_per_sm, int *counter,
                            cudaStream_t stream)
 {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_batch_kernel<P, T>, kThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_batch_kernel<P, T, G>, kThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
@@ -466,35 +468,38 @@ cudaError_t launch_batch_t(const RenderJob *jobs, int njobs, int total_tiles, in
     if (blocks < 1) return cudaSuccess;
     e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
     if (e != cudaSuccess) return e;
-    render_batch_kernel<P, T><<<static_cast<int>(blocks), kThreads, 0, stream>>>(jobs, njobs, total_tiles, counter);
+    render_batch_kernel<P, T, G><<<static_cast<int>(blocks), kThreads, 0, stream>>>(jobs, njobs, total_tiles, counter);
     return cudaGetLastError();
 }
 
-template <int P, typename T>
+template <int P, typename T, bool G>
 struct RenderOne {
     static cudaError_t run(const ModelView *mv, const RenderSetup *rs, int *counter, cudaStream_t s)
     {
-        return launch_render_t<P, T>(*mv, *rs, counter, s);
+        return launch_render_t<P, T, G>(*mv, *rs, counter, s);
     }
 };
-template <int P, typename T>
+template <int P, typename T, bool G>
 struct RenderBatch {
     static cudaError_t run(const RenderJob *jobs, int njobs, int total_tiles, int ctas_per_sm, int *counter,
                            cudaStream_t s)
     {
-        return launch_batch_t<P, T>(jobs, njobs, total_tiles, ctas_per_sm, counter, s);
+        return launch_batch_t<P, T, G>(jobs, njobs, total_tiles, ctas_per_sm, counter, s);
     }
 };
 
-// Instantiates F<P, T>::run for the model's degree and storage type.
-template <template <int, typename> class F, typename... A>
-cudaError_t dispatch(int p, int dtype, A... args)
+// Instantiates F<P, T, G>::run for the model's degree, storage type and
+// whether the gradient is queried.
+template <template <int, typename, bool> class F, typename... A>
+cudaError_t dispatch(int p, int dtype, bool grad, A... args)
 {
+#define MFADVR_GRAD_CASES(PP, TT) \
+    return grad ? F<PP, TT, true>::run(args...) : F<PP, TT, false>::run(args...);
 #define MFADVR_DTYPE_CASES(PP)                                   \
     switch (dtype) {                                             \
-    case MFADVR_F32: return F<PP, float>::run(args...);          \
-    case MFADVR_F16: return F<PP, __half>::run(args...);         \
-    case MFADVR_BF16: return F<PP, __nv_bfloat16>::run(args...); \
+    case MFADVR_F32: MFADVR_GRAD_CASES(PP, float)                \
+    case MFADVR_F16: MFADVR_GRAD_CASES(PP, __half)               \
+    case MFADVR_BF16: MFADVR_GRAD_CASES(PP, __nv_bfloat16)       \
     default: return cudaErrorInvalidValue;                       \
     }
     switch (p) {
@@ -506,19 +511,20 @@ cudaError_t dispatch(int p, int dtype, A... args)
     default: return cudaErrorInvalidValue;
     }
 #undef MFADVR_DTYPE_CASES
+#undef MFADVR_GRAD_CASES
 }
 
 }  // namespace
 
 cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream)
 {
-    return dispatch<RenderOne>(mv.p, mv.dtype, &mv, &rs, counter, stream);
+    return dispatch<RenderOne>(mv.p, mv.dtype, rs.shading != 0, &mv, &rs, counter, stream);
 }
 
-cudaError_t launch_render_batch(int p, int dtype, const RenderJob *jobs_dev, int njobs, int total_tiles,
+cudaError_t launch_render_batch(int p, int dtype, int grad, const RenderJob *jobs_dev, int njobs, int total_tiles,
                                 int ctas_per_sm, int *counter, cudaStream_t stream)
 {
-    return dispatch<RenderBatch>(p, dtype, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, stream);
+    return dispatch<RenderBatch>(p, dtype, grad != 0, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, stream);
 }
 
 }  // namespace mfadvr

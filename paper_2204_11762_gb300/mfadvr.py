@@ -19,6 +19,7 @@ import numpy as np
 from . import build as _build
 
 F32, F16, BF16 = 0, 1, 2
+QUERY_VALUE, QUERY_GRADIENT, QUERY_BOTH = 1, 2, 3
 _DTYPES = {"f32": F32, "float32": F32, "f16": F16, "float16": F16, "bf16": BF16, "bfloat16": BF16}
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTFOUND, ETIMEOUT, EBUSY, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
@@ -30,7 +31,8 @@ EXPORTS = ("mfadvr_create", "mfadvr_destroy", "mfadvr_load_model", "mfadvr_unloa
            "mfadvr_eval_points", "mfadvr_eval_points_host", "mfadvr_render", "mfadvr_render_host",
            "mfadvr_status_string", "mfadvr_last_error", "mfadvr_render_lattice_noalloc", "mfadvr_render_batch",
            "mfadvr_autotune", "mfadvr_tuning_save", "mfadvr_tuning_load", "mfadvr_serve_start", "mfadvr_serve_stop",
-           "mfadvr_submit", "mfadvr_wait", "mfadvr_serve_stats", "mfadvr_serve_trace")
+           "mfadvr_submit", "mfadvr_wait", "mfadvr_serve_stats", "mfadvr_serve_trace", "mfadvr_query_points",
+           "mfadvr_query_points_host")
 MAX_BATCH = 256
 NOALLOC_MAX_POINTS = 1 << 19
 
@@ -104,6 +106,8 @@ def load_library(build_if_missing: bool = True):
         "mfadvr_model_info": [vp, i32, P(ctypes.c_float), P(ctypes.c_float), P(ctypes.c_float), P(u64)],
         "mfadvr_eval_points": [vp, i32, vp, i64, vp, vp, vp],
         "mfadvr_eval_points_host": [vp, i32, vp, i64, vp, vp, vp],
+        "mfadvr_query_points": [vp, i32, vp, i64, i32, vp, vp, vp],
+        "mfadvr_query_points_host": [vp, i32, vp, i64, i32, vp, vp, vp],
         "mfadvr_render": [vp, i32, P(Camera), P(RenderParams), vp, vp, vp],
         "mfadvr_render_host": [vp, i32, P(Camera), P(RenderParams), vp, vp, vp],
     }
@@ -291,6 +295,22 @@ class Context:
             out = np.empty((n, 4), dtype=np.float32)
         self._check(self._L.mfadvr_eval_points_host(self._h, int(model_id), _ptr(params), n, _ptr(out),
                                                     _ptr(spans), _stream(stream)))
+        return out
+
+    def query_points(self, model_id, params_dev, n, out_dev, query=QUERY_BOTH, spans_dev=None, stream=None):
+        """eval_points for one query: out_dev holds n values (QUERY_VALUE), n x 3
+        gradients (QUERY_GRADIENT) or n x 4 (QUERY_BOTH)."""
+        self._check(self._L.mfadvr_query_points(self._h, int(model_id), _ptr(params_dev), int(n), int(query),
+                                                _ptr(out_dev), _ptr(spans_dev), _stream(stream)))
+
+    def query_points_host(self, model_id, params, query=QUERY_BOTH, out=None, spans=None, stream=None):
+        params = np.ascontiguousarray(params, dtype=np.float32).reshape(-1, 3)
+        n = params.shape[0]
+        if out is None:
+            shape = {QUERY_VALUE: (n,), QUERY_GRADIENT: (n, 3)}.get(int(query), (n, 4))
+            out = np.empty(shape, dtype=np.float32)
+        self._check(self._L.mfadvr_query_points_host(self._h, int(model_id), _ptr(params), n, int(query),
+                                                     _ptr(out), _ptr(spans), _stream(stream)))
         return out
 
     def render(self, model_id, camera: dict, params: dict, tf_dev, tf_size, rgba_dev, nsamples_dev=None,

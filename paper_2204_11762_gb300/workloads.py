@@ -94,6 +94,19 @@ def field_lattice(field, n, p, lo=-1.0, hi=1.0):
     return field(X, Y, Z).astype(np.float64)
 
 
+def gaussian_beam_lattice(n, p):
+    """Eq. 1 (the Gaussian beam) on [-1, 1]^3 sampled at the Greville
+    abscissae; float32 (n_w, n_v, n_u), built one w-slice at a time so that a
+    512^3 lattice needs no 512^3 float64 temporaries."""
+    n = tuple(int(v) for v in n)
+    xs = _grid(n, p, -1.0, 1.0)
+    Y, X = np.meshgrid(xs[1], xs[0], indexing="ij")
+    out = np.empty((n[2], n[1], n[0]), dtype=np.float32)
+    for k, z in enumerate(xs[2]):
+        out[k] = gaussian_beam(X, Y, np.full_like(X, z))
+    return out
+
+
 def value_noise_lattice(n, p, rng, octaves=5, persistence=0.5, lacunarity=2.0, base_cells=4):
     """Multi-octave value noise on [0,1]^3 at the Greville abscissae:
     octave o has base_cells * lacunarity^o cells per axis, hashed lattice

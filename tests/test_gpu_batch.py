@@ -59,6 +59,27 @@ def test_batch_equals_single_renders(torch_cuda):
             np.testing.assert_array_equal(ns, j["nsamples_dev"].cpu().numpy())
 
 
+def test_batch_mixed_shading_equals_single_renders(torch_cuda):
+    """Shaded and unshaded jobs of the same degree and storage run in separate
+    groups (gradient and value-only kernels); each image equals its single
+    render."""
+    from paper_2204_11762_gb300 import mfadvr
+    torch = torch_cuda
+    with mfadvr.Context(0) as ctx:
+        jobs = _jobs(ctx, torch, SPECS[:4] + SPECS[:3], seed=11)
+        for j in jobs[::2]:
+            j["params"] = dict(j["params"], shading=0)
+        ctx.render_batch(jobs)
+        torch.cuda.synchronize()
+        batch = [(j["rgba_dev"].cpu().numpy(), j["nsamples_dev"].cpu().numpy()) for j in jobs]
+        for j, (img, ns) in zip(jobs, batch):
+            ctx.render(j["model_id"], j["camera"], j["params"], j["tf_dev"], j["tf_size"], j["rgba_dev"],
+                       j["nsamples_dev"])
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(img, j["rgba_dev"].cpu().numpy())
+            np.testing.assert_array_equal(ns, j["nsamples_dev"].cpu().numpy())
+
+
 def test_batch_against_oracle(torch_cuda, orc):
     from _parity import dequantize
     from paper_2204_11762_gb300 import mfadvr

@@ -164,3 +164,58 @@ def test_hbm_budget(torch_cuda):
         assert e.value.status == mfadvr.ENOMEM
         c.unload_model(a)
         c.load_model(np.zeros((20, 20, 20), dtype=np.float32), 3)
+
+
+@pytest.mark.parametrize("p,storage", [(1, "f32"), (2, "f16"), (3, "f32"), (3, "bf16"), (4, "f32"), (5, "f32"),
+                                       (5, "f16")])
+def test_query_modes_equal_both_bitwise(ctx, torch_cuda, orc, p, storage):
+    """Value-only and gradient-only queries (Sec. 4.3.3) form only the sums
+    they need; each output must equal the matching component of the combined
+    query bit for bit, and the value and gradient must match the oracle."""
+    from paper_2204_11762_gb300 import mfadvr
+    torch = torch_cuda
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(900 + p)
+    n = (p + 12, p + 7, p + 15)
+    ctrl = rng.normal(size=(n[2], n[1], n[0])).astype(np.float32)
+    pts = np.concatenate([rng.uniform(0, 1, size=(2049, 3)).astype(np.float32), _edge_points(n, p)])
+    mid = ctx.load_model(ctrl, p, storage=storage)
+    both, sp = _run(ctx, torch, mid, pts)
+    d_pts = torch.from_numpy(pts).to(dev)
+    k = pts.shape[0]
+    d_val = torch.full((k,), float("nan"), device=dev)
+    d_grad = torch.full((k, 3), float("nan"), device=dev)
+    d_sp = torch.full((k, 3), -1, dtype=torch.int32, device=dev)
+    ctx.query_points(mid, d_pts, k, d_val, mfadvr.QUERY_VALUE, d_sp)
+    ctx.query_points(mid, d_pts, k, d_grad, mfadvr.QUERY_GRADIENT)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(d_val.cpu().numpy(), both[:, 0])
+    np.testing.assert_array_equal(d_grad.cpu().numpy(), both[:, 1:])
+    np.testing.assert_array_equal(d_sp.cpu().numpy(), sp)
+    # host-buffer variants give the same bits
+    np.testing.assert_array_equal(ctx.query_points_host(mid, pts, mfadvr.QUERY_VALUE), both[:, 0])
+    np.testing.assert_array_equal(ctx.query_points_host(mid, pts, mfadvr.QUERY_GRADIENT), both[:, 1:])
+    deq = dequantize(ctrl, storage)
+    ref, ref_sp = orc.eval_points(deq, p, pts)
+    assert_eval_parity(both, ref, deq, n, p, sp, ref_sp)
+    ctx.unload_model(mid)
+
+
+def test_query_rejects_bad_query(ctx, torch_cuda):
+    from paper_2204_11762_gb300 import mfadvr
+    torch = torch_cuda
+    dev = torch.device("cuda:0")
+    mid = ctx.load_model(np.ones((6, 6, 6), dtype=np.float32), 2)
+    d_pts = torch.zeros((4, 3), device=dev)
+    d_out = torch.zeros((4, 4), device=dev)
+    for q in (0, 4, -1):
+        with pytest.raises(mfadvr.MfadvrError) as e:
+            ctx.query_points(mid, d_pts, 4, d_out, q)
+        assert e.value.status == mfadvr.EINVAL
+    with pytest.raises(mfadvr.MfadvrError) as e:  # QUERY_BOTH needs 16-byte alignment
+        ctx.query_points(mid, d_pts, 3, d_out.view(-1)[1:], mfadvr.QUERY_BOTH)
+    assert e.value.status == mfadvr.EINVAL
+    ctx.query_points(mid, d_pts, 3, d_out.view(-1)[1:], mfadvr.QUERY_VALUE)  # 4-byte aligned is enough
+    torch.cuda.synchronize()
+    assert np.allclose(d_out.view(-1)[1:4].cpu().numpy(), 1.0)
+    ctx.unload_model(mid)

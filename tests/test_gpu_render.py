@@ -71,7 +71,8 @@ def test_tiny_images(ctx, torch_cuda, orc, p, n, W, H, shading):
 
 
 @pytest.mark.parametrize("case", ["ortho_oblique", "inside_box", "opacity_correction", "tf_size_1",
-                                  "no_ert", "ragged", "world_box", "high_opacity", "explicit_tf_range"])
+                                  "no_ert", "ragged", "world_box", "high_opacity", "explicit_tf_range",
+                                  "shading_off"])
 def test_render_variants(ctx, torch_cuda, orc, case):
     from paper_2204_11762_gb300 import workloads
     import zlib
@@ -103,11 +104,33 @@ def test_render_variants(ctx, torch_cuda, orc, case):
         tf[:, 3] = np.minimum(1.0, tf[:, 3] * 4)
     elif case == "explicit_tf_range":
         prm["tf_lo"], prm["tf_hi"] = -1.0, 1.5
+    elif case == "shading_off":
+        prm["shading"] = 0
     mid = ctx.load_model(ctrl, p, box_min=box[0], box_max=box[1])
     img, ns = _render(ctx, torch_cuda, mid, cam, prm, tf)
     ref = orc.render(ctrl, p, cam, dict(prm, tf=tf), box_min=box[0], box_max=box[1])
     assert_render_parity(img, ns, ref)
     ctx.unload_model(mid)
+
+@pytest.mark.parametrize("p,storage", [(1, "f32"), (2, "bf16"), (3, "f32"), (3, "f16"), (4, "f32"), (5, "bf16")])
+def test_render_shading_off_value_only(ctx, torch_cuda, orc, p, storage):
+    """Shading off: the value-only kernel (no gradient sums) against the
+    oracle, which composites the unshaded TF colours (Algorithm 1 without its
+    shading step)."""
+    from paper_2204_11762_gb300 import workloads
+    rng = np.random.default_rng(700 + p)
+    n = (p + 9, p + 11, p + 8)
+    ctrl = workloads.gaussian_sum_lattice(n, p, rng)
+    tf = workloads.transfer_function(rng, 64)
+    cam = _persp((1.8, -1.1, 1.5))
+    prm = {"width": 48, "height": 40, "step": 1 / 200, "max_opacity": 0.99, "ref_step": 1 / 16, "shading": 0}
+    mid = ctx.load_model(ctrl, p, storage=storage)
+    img, ns = _render(ctx, torch_cuda, mid, cam, prm, tf)
+    ref = orc.render(dequantize(ctrl, storage), p, cam, dict(prm, tf=tf, tf_lo=float(ctrl.min()),
+                                                                 tf_hi=float(ctrl.max())))
+    assert_render_parity(img, ns, ref)
+    ctx.unload_model(mid)
+
 
 
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
