@@ -43,7 +43,8 @@ def build(force: bool = False) -> str:
 class Model(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32 * 3), ("n", ctypes.c_int32 * 3),
                 ("ctrl", ctypes.c_void_p),
-                ("box_min", ctypes.c_double * 3), ("box_max", ctypes.c_double * 3)]
+                ("box_min", ctypes.c_double * 3), ("box_max", ctypes.c_double * 3),
+                ("knots", ctypes.c_void_p * 3)]
 
 
 class Camera(ctypes.Structure):
@@ -97,14 +98,24 @@ def knots(n: int, p: int) -> np.ndarray:
     return t
 
 
-def find_span(n: int, p: int, u: float) -> int:
-    t = knots(n, p)
+def _knot_vector(n, p, t):
+    if t is None:
+        return knots(n, p)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    if t.shape != (n + p + 1,):
+        raise ValueError("a knot vector has n + p + 1 entries")
+    return t
+
+
+def find_span(n: int, p: int, u: float, t=None) -> int:
+    t = _knot_vector(n, p, t)
     return lib().orc_find_span(n, p, _dptr(t), float(u))
 
 
-def basis_ders(n: int, p: int, u: float):
-    """(span, N[0..p], dN[0..p]) at u for the clamped uniform knots."""
-    t = knots(n, p)
+def basis_ders(n: int, p: int, u: float, t=None):
+    """(span, N[0..p], dN[0..p]) at u for the knot vector t (default: the
+    clamped uniform knots)."""
+    t = _knot_vector(n, p, t)
     s = lib().orc_find_span(n, p, _dptr(t), float(u))
     N = np.zeros(p + 1)
     dN = np.zeros(p + 1)
@@ -112,17 +123,19 @@ def basis_ders(n: int, p: int, u: float):
     return s, N, dN
 
 
-def basis_brute(n: int, p: int, u: float):
+def basis_brute(n: int, p: int, u: float, t=None):
     """All n basis functions and derivatives at u by the raw recursion."""
-    t = knots(n, p)
+    t = _knot_vector(n, p, t)
     N = np.array([lib().orc_basis_brute(i, p, float(u), _dptr(t), n) for i in range(n)])
     dN = np.array([lib().orc_basis_brute_der(i, p, float(u), _dptr(t), n) for i in range(n)])
     return N, dN
 
 
-def _model(ctrl: np.ndarray, degree, box_min=(0.0, 0.0, 0.0), box_max=(1.0, 1.0, 1.0)):
+def _model(ctrl: np.ndarray, degree, box_min=(0.0, 0.0, 0.0), box_max=(1.0, 1.0, 1.0), knot_vectors=None):
     """ctrl: array of shape (n2, n1, n0) (u fastest in memory); FP32
-    lattices convert to FP64 exactly."""
+    lattices convert to FP64 exactly.  knot_vectors: None or three entries,
+    each None (uniform) or the axis' n + p + 1 knots.  Returns the ctypes
+    model and the arrays it points into (keep them alive)."""
     ctrl = np.ascontiguousarray(ctrl, dtype=np.float64)
     if ctrl.ndim != 3:
         raise ValueError("ctrl must be 3-D (n_w, n_v, n_u)")
@@ -134,12 +147,18 @@ def _model(ctrl: np.ndarray, degree, box_min=(0.0, 0.0, 0.0), box_max=(1.0, 1.0,
     m.ctrl = ctrl.ctypes.data
     m.box_min[:] = [float(x) for x in box_min]
     m.box_max[:] = [float(x) for x in box_max]
-    return m, ctrl
+    keep = [ctrl]
+    for a, t in enumerate(knot_vectors or (None, None, None)):
+        if t is not None:
+            t = _knot_vector(m.n[a], m.p[a], t)
+            keep.append(t)
+            m.knots[a] = t.ctypes.data
+    return m, keep
 
 
-def eval_points(ctrl, degree, uvw, *, brute=False, threads=None, with_spans=True):
+def eval_points(ctrl, degree, uvw, *, brute=False, threads=None, with_spans=True, knot_vectors=None):
     """Value and gradient (f, df/du, df/dv, df/dw) in FP64 at FP32 points."""
-    m, keep = _model(ctrl, degree)
+    m, keep = _model(ctrl, degree, knot_vectors=knot_vectors)
     uvw = np.ascontiguousarray(uvw, dtype=np.float32).reshape(-1, 3)
     npts = uvw.shape[0]
     out = np.zeros((npts, 4), dtype=np.float64)
@@ -155,10 +174,10 @@ def eval_points(ctrl, degree, uvw, *, brute=False, threads=None, with_spans=True
 
 
 def render(ctrl, degree, camera: dict, params: dict, *, box_min=(0, 0, 0), box_max=(1, 1, 1),
-           row_step=1, threads=None, brute=False):
+           row_step=1, threads=None, brute=False, knot_vectors=None):
     """Algorithm 1 in FP64.  Returns dict with rgba (H, W, 4), nsamples,
     nambig, rgba_alt, ns_lo and ns_hi (see orc_render in mfa_oracle.c)."""
-    m, keep = _model(ctrl, degree, box_min, box_max)
+    m, keep = _model(ctrl, degree, box_min, box_max, knot_vectors)
     cam = Camera()
     cam.kind = int(camera.get("kind", 1))
     cam.eye[:] = [float(x) for x in camera["eye"]]

@@ -11,7 +11,10 @@
  *  - The MFA model (Sec. 2.3, Sec. 3): a tensor product of B-splines of degree
  *    p_d on each axis d, with weights 1, over an n0 x n1 x n2 control-point
  *    lattice and clamped knot vectors on the parameter box [0,1]^3.  Knots:
- *    t_0..t_p = 0, t_{p+j} = j/m for j = 1..m-1, t_n..t_{n+p} = 1, m = n - p.
+ *    t_0..t_p = 0, t_{p+j} = j/m for j = 1..m-1, t_n..t_{n+p} = 1, m = n - p,
+ *    unless the model gives its own clamped knot vector for an axis (the
+ *    non-uniform knots an adaptive MFA fit places, Sec. 2.3); the span
+ *    search and the basis below take any clamped, non-decreasing vector.
  *  - Value and first partial derivatives at a parameter point, computed
  *    together (queryValueMFA / queryGradientMFA of Algorithm 1; Sec. 3.1 asks
  *    for all three derivatives at once).  Two modes:
@@ -144,6 +147,8 @@ typedef struct {
     const double *ctrl;  /* n0*n1*n2, index i + n0*(j + n1*k) (u fastest) */
     double box_min[3];   /* world box that maps onto the parameter box */
     double box_max[3];
+    const double *knots[3]; /* NULL: clamped uniform knots; else the n+p+1
+                               clamped, non-decreasing knots of the axis */
 } orc_model;
 
 typedef struct {
@@ -157,9 +162,20 @@ static int ctx_init(orc_ctx *c, const orc_model *m)
     for (int d = 0; d < 3; ++d) c->t[d] = NULL;
     for (int d = 0; d < 3; ++d) {
         if (m->p[d] < 1 || m->p[d] > ORC_MAX_DEGREE || m->n[d] < m->p[d] + 1) return -1;
-        c->t[d] = (double *)malloc(sizeof(double) * (size_t)(m->n[d] + m->p[d] + 1));
+        const int n = m->n[d], p = m->p[d];
+        c->t[d] = (double *)malloc(sizeof(double) * (size_t)(n + p + 1));
         if (!c->t[d]) return -1;
-        orc_make_knots(m->n[d], m->p[d], c->t[d]);
+        if (!m->knots[d]) {
+            orc_make_knots(n, p, c->t[d]);
+            continue;
+        }
+        /* a given vector must be clamped to [0, 1] and non-decreasing */
+        const double *t = m->knots[d];
+        for (int i = 0; i <= p; ++i)
+            if (t[i] != 0.0 || t[n + i] != 1.0) return -1;
+        for (int i = 1; i < n + p + 1; ++i)
+            if (!(t[i] >= t[i - 1])) return -1;
+        memcpy(c->t[d], t, sizeof(double) * (size_t)(n + p + 1));
     }
     return 0;
 }

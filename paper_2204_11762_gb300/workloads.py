@@ -33,6 +33,21 @@ def seed_for(config_index: int) -> int:
 # Lattice placement
 # --------------------------------------------------------------------------
 
+def graded_knots(rng, n: int, p: int, spread=0.8) -> np.ndarray:
+    """A clamped knot vector of n + p + 1 FP32 values with non-uniform interior
+    knots (the kind an adaptive MFA fit places, Sec. 2.3): span widths drawn
+    from U[1 - spread, 1 + spread] and normalised to [0, 1], so neighbouring
+    spans differ by up to a factor (1 + spread) / (1 - spread).  float32."""
+    m = n - p
+    for _ in range(100):
+        w = rng.uniform(1.0 - spread, 1.0 + spread, size=m)
+        inner = np.cumsum(w)[:-1] / w.sum()
+        t = np.concatenate([np.zeros(p + 1), inner, np.ones(p + 1)]).astype(np.float32)
+        if m == 1 or np.all(np.diff(t[p:n + 1]) > 0):
+            return t
+    raise ValueError("could not draw strictly increasing FP32 knots")
+
+
 def greville(n: int, p: int) -> np.ndarray:
     """Greville abscissae of the clamped uniform knot vector of n control
     points and degree p (mean of p consecutive interior knots)."""
