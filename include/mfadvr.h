@@ -6,8 +6,10 @@
  * every sample of every ray queries a tensor-product B-spline model for its
  * value and gradient (Sec. 3.1, Algorithm 1).  The model (Sec. 2.3) is a
  * lattice of control points with a clamped knot vector and a degree p_d per
- * axis over the parameter box [0,1]^3; knots are uniform:
- *   t_0..t_p = 0,  t_{p+j} = j/m (j = 1..m-1),  t_n..t_{n+p} = 1,  m = n - p.
+ * axis over the parameter box [0,1]^3.  Knots are uniform by default:
+ *   t_0..t_p = 0,  t_{p+j} = j/m (j = 1..m-1),  t_n..t_{n+p} = 1,  m = n - p;
+ * a model may instead give its own clamped knots per axis (the adaptive,
+ * non-uniform knots an MFA fit places, Sec. 2.3).
  *
  * Conventions shared by every call:
  *  - Status: every entry point returns an mfadvr_status, 0 on success.  No
@@ -27,7 +29,8 @@
  *    external lock).
  *  - Degrees: 1..MFADVR_MAX_DEGREE and equal on the three axes (the kernels
  *    are compiled per degree); other degrees return MFADVR_EUNSUPPORTED.
- *  - Knots: clamped uniform only (mfadvr_model_desc.knots must be NULL).
+ *  - Knots: clamped, uniform unless mfadvr_model_desc.knots gives them (see
+ *    there).
  */
 #ifndef MFADVR_H
 #define MFADVR_H
@@ -72,7 +75,12 @@ typedef struct {
     float box_min[3];      /* world box; box_max > box_min on every axis       */
     float box_max[3];
     const float *ctrl;     /* HOST, n0*n1*n2 finite FP32 values (u fastest)    */
-    const float *knots[3]; /* must be NULL: clamped uniform knots             */
+    const float *knots[3]; /* per axis: NULL (uniform knots) or HOST, n_d+p+1
+                              FP32 knots: p+1 zeros, interior knots strictly
+                              increasing inside (0,1), p+1 ones.  With any
+                              axis given, queries find spans by binary search
+                              and take the basis from per-span tables built
+                              at load (NULL axes then use j/m rounded to FP32) */
     mfadvr_dtype storage;  /* storage type in HBM                              */
 } mfadvr_model_desc;
 
@@ -119,7 +127,8 @@ MFADVR_API mfadvr_status mfadvr_destroy(mfadvr_ctx *ctx);
 /* Copy a model into library-owned HBM (Sec. 3: the encoded model is the
  * renderer's input).  Synchronous: the caller may free desc->ctrl on return.
  * *model_id receives a handle >= 0.  EINVAL: bad sizes, box, non-finite
- * control points, knots != NULL.  EUNSUPPORTED: degree outside
+ * control points, a knot vector that is not clamped and strictly increasing
+ * inside.  EUNSUPPORTED: degree outside
  * 1..MFADVR_MAX_DEGREE or unequal per axis.  ENOMEM: over budget. */
 MFADVR_API mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, int32_t *model_id);
 

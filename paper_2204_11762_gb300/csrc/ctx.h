@@ -24,6 +24,12 @@ struct Model {
     float scale = 1.0f;
     float pmin = 0.0f, pmax = 0.0f, pabs = 0.0f;
     float box_min[3] = {0, 0, 0}, box_max[3] = {1, 1, 1};
+    // General knots (nu = 1): one device buffer holding, per axis, the
+    // breakpoints, inverse widths and per-span pieces at these float offsets.
+    int nu = 0;
+    void *d_knots = nullptr;
+    uint64_t knot_bytes = 0;
+    size_t brk_off[3] = {0, 0, 0}, ih_off[3] = {0, 0, 0}, pc_off[3] = {0, 0, 0};
 };
 
 // Device buffer owned by the context, grown on demand (host-buffer calls).
@@ -118,11 +124,11 @@ mfadvr_status make_job(mfadvr_ctx *ctx, const mfadvr_render_job &job, int index,
 // One launch of a batched render: jobs dst[first, first+count) of one degree
 // and storage type, `tiles` tiles in all.
 struct BatchGroup {
-    int p, dtype, grad, first, count, tiles;
+    int p, dtype, grad, nu, first, count, tiles;
 };
-// Orders n jobs by (degree, storage type, shading) into dst, fills their tile
-// fields and returns the launch groups (grad = shading: the gradient is
-// queried).
+// Orders n jobs by (degree, storage type, shading, general knots) into dst,
+// fills their tile fields and returns the launch groups (grad = shading: the
+// gradient is queried; nu: general knots).
 std::vector<BatchGroup> pack_jobs(const RenderJob *jobs, int n, RenderJob *dst);
 // Tears down a context's serving loop, if one runs (serve.cu).
 void stop_server(mfadvr_ctx *ctx);

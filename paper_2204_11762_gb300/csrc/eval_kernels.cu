@@ -17,7 +17,9 @@
 namespace mfadvr {
 namespace {
 
-template <int P, typename T, int Q>
+// NU: general knots (span search, per-span pieces); otherwise uniform knots
+// (exact floor, uniform pieces or the clamped-pattern table).
+template <int P, typename T, int Q, bool NU>
 __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const float *__restrict__ params,
                                                           int64_t n, float *__restrict__ out,
                                                           int32_t *__restrict__ spans)
@@ -38,36 +40,61 @@ __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const fl
         const float u = fminf(fmaxf(__ldcs(params + 3 * idx + 0), 0.0f), 1.0f);
         const float v = fminf(fmaxf(__ldcs(params + 3 * idx + 1), 0.0f), 1.0f);
         const float w = fminf(fmaxf(__ldcs(params + 3 * idx + 2), 0.0f), 1.0f);
-        const int k0 = span_exact(u, mv.m[0], mf0);
-        const int k1 = span_exact(v, mv.m[1], mf1);
-        const int k2 = span_exact(w, mv.m[2], mf2);
+        int k0, k1, k2;
+        float x0, x1, x2, g0 = s0, g1 = s1, g2 = s2;
+        if constexpr (NU) {
+            k0 = span_search(mv.brk[0], mv.m[0], u);
+            k1 = span_search(mv.brk[1], mv.m[1], v);
+            k2 = span_search(mv.brk[2], mv.m[2], w);
+            const float ih0 = __ldg(mv.ih[0] + k0), ih1 = __ldg(mv.ih[1] + k1), ih2 = __ldg(mv.ih[2] + k2);
+            x0 = (u - __ldg(mv.brk[0] + k0)) * ih0;
+            x1 = (v - __ldg(mv.brk[1] + k1)) * ih1;
+            x2 = (w - __ldg(mv.brk[2] + k2)) * ih2;
+            g0 = sv * ih0;  // d/du = (1 / span width) d/dx
+            g1 = sv * ih1;
+            g2 = sv * ih2;
+        } else {
+            k0 = span_exact(u, mv.m[0], mf0);
+            k1 = span_exact(v, mv.m[1], mf1);
+            k2 = span_exact(w, mv.m[2], mf2);
+            x0 = fmaf(u, mf0, -static_cast<float>(k0));
+            x1 = fmaf(v, mf1, -static_cast<float>(k1));
+            x2 = fmaf(w, mf2, -static_cast<float>(k2));
+        }
         const int base = k0 + n0 * k1 + n01 * k2;
+        auto basis3 = [&](float *Nu, float *dNu, float *Nv, float *dNv, float *Nw, float *dNw) {
+            if constexpr (NU) {
+                basis_pieces<P>(x0, mv.pieces[0], k0, Nu, dNu);
+                basis_pieces<P>(x1, mv.pieces[1], k1, Nv, dNv);
+                basis_pieces<P>(x2, mv.pieces[2], k2, Nw, dNw);
+            } else {
+                basis<P>(x0, k0, mv.m[0], Nu, dNu);
+                basis<P>(x1, k1, mv.m[1], Nv, dNv);
+                basis<P>(x2, k2, mv.m[2], Nw, dNw);
+            }
+        };
         float r[4];
         float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
         if constexpr (P <= 3) {
             // the whole block in flight before the basis is evaluated
             Row q[P + 1][Block<P>::JP][Block<P>::IR];
             load_block<P, T>(mv.rows, base, n0, n01, q);
-            basis<P>(fmaf(u, mf0, -static_cast<float>(k0)), k0, mv.m[0], Nu, dNu);
-            basis<P>(fmaf(v, mf1, -static_cast<float>(k1)), k1, mv.m[1], Nv, dNv);
-            basis<P>(fmaf(w, mf2, -static_cast<float>(k2)), k2, mv.m[2], Nw, dNw);
+            basis3(Nu, dNu, Nv, dNv, Nw, dNw);
             contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return block_pair<P>(q, k, jp, i); },
                            r);
         } else {
-            basis<P>(fmaf(u, mf0, -static_cast<float>(k0)), k0, mv.m[0], Nu, dNu);
-            basis<P>(fmaf(v, mf1, -static_cast<float>(k1)), k1, mv.m[1], Nv, dNv);
-            basis<P>(fmaf(w, mf2, -static_cast<float>(k2)), k2, mv.m[2], Nw, dNw);
+            basis3(Nu, dNu, Nv, dNv, Nw, dNw);
             contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw,
                            [&](int k, int jp, int i) { return row_pair<T>(mv.rows, base, n0, n01, k, jp, i); }, r);
         }
         if constexpr (Q == kQueryBoth) {
-            __stcs(reinterpret_cast<float4 *>(out) + idx, make_float4(r[0] * sv, r[1] * s0, r[2] * s1, r[3] * s2));
+            __stcs(reinterpret_cast<float4 *>(out) + idx, make_float4(r[0] * sv, r[1] * g0, r[2] * g1, r[3] * g2));
         } else if constexpr (Q == kQueryValue) {
             __stcs(out + idx, r[0] * sv);
         } else {
-            __stcs(out + 3 * idx + 0, r[1] * s0);
-            __stcs(out + 3 * idx + 1, r[2] * s1);
-            __stcs(out + 3 * idx + 2, r[3] * s2);
+            __stcs(out + 3 * idx + 0, r[1] * g0);
+            __stcs(out + 3 * idx + 1, r[2] * g1);
+            __stcs(out + 3 * idx + 2, r[3] * g2);
         }
         if (spans) {
             __stcs(spans + 3 * idx + 0, k0 + P);
@@ -77,20 +104,28 @@ __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const fl
     }
 }
 
-template <int P, typename T, int Q>
-cudaError_t launch_eval_q(const ModelView &mv, const float *params, int64_t n, float *out, int32_t *spans,
+template <int P, typename T, int Q, bool NU>
+cudaError_t launch_eval_k(const ModelView &mv, const float *params, int64_t n, float *out, int32_t *spans,
                           cudaStream_t stream)
 {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval_points_kernel<P, T, Q>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval_points_kernel<P, T, Q, NU>, 256, 0);
     if (per_sm < 1) per_sm = 1;
     const int64_t need = (n + 255) / 256;
     const int64_t cap = static_cast<int64_t>(sms) * per_sm;
     const int blocks = static_cast<int>(need < cap ? need : cap);
-    eval_points_kernel<P, T, Q><<<blocks, 256, 0, stream>>>(mv, params, n, out, spans);
+    eval_points_kernel<P, T, Q, NU><<<blocks, 256, 0, stream>>>(mv, params, n, out, spans);
     return cudaGetLastError();
+}
+
+template <int P, typename T, int Q>
+cudaError_t launch_eval_q(const ModelView &mv, const float *params, int64_t n, float *out, int32_t *spans,
+                          cudaStream_t stream)
+{
+    return mv.nu ? launch_eval_k<P, T, Q, true>(mv, params, n, out, spans, stream)
+                 : launch_eval_k<P, T, Q, false>(mv, params, n, out, spans, stream);
 }
 
 template <int P, typename T>

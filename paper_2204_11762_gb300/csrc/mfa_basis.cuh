@@ -133,6 +133,43 @@ struct SpanPieces {
     float c[P * P][P + 1][P + 1];  // pattern a*P + b: BasisScale<P> N_r(x) = sum_e c[.][r][e] x^e
 };
 
+// Monomial coefficients of the P+1 basis functions on one span, from the
+// Cox-de Boor recurrence run on polynomials of the local coordinate x in
+// [0, 1].  kap[j + P - 1] is the span-local position of knot t_{s+j},
+// j = 1-P..P, in units of the span width (so kap(0) = 0, kap(1) = 1); the
+// convention 0/0 = 0 covers repeated end knots.  out[r][e] = scale * coefficient
+// of x^e in N_{s-P+r}.  Runs at compile time (the pattern tables below) and
+// on the host at model load (per-span tables of general knots).
+template <int P>
+constexpr void pieces_from_knots(const double (&kap)[2 * P], double scale, double (&out)[P + 1][P + 1])
+{
+    double B[P + 1][P + 1][P + 1] = {};  // [q][r][e]: N_{s-q+r, q}
+    B[0][0][0] = 1.0;
+    for (int q = 1; q <= P; ++q) {
+        for (int r = 0; r <= q; ++r) {
+            const int i = r - q;
+            if (r > 0) {  // (x - kappa(i)) / (kappa(i+q) - kappa(i)) N_{s+i, q-1}
+                const double k0 = kap[i + P - 1], den = kap[i + q + P - 1] - k0;
+                if (den != 0.0)
+                    for (int e = 0; e < q; ++e) {
+                        B[q][r][e + 1] += B[q - 1][r - 1][e] / den;
+                        B[q][r][e] -= k0 * B[q - 1][r - 1][e] / den;
+                    }
+            }
+            if (r < q) {  // (kappa(i+q+1) - x) / (kappa(i+q+1) - kappa(i+1)) N_{s+i+1, q-1}
+                const double k1 = kap[i + q + P], den = k1 - kap[i + P];
+                if (den != 0.0)
+                    for (int e = 0; e < q; ++e) {
+                        B[q][r][e] += k1 * B[q - 1][r][e] / den;
+                        B[q][r][e + 1] -= B[q - 1][r][e] / den;
+                    }
+            }
+        }
+    }
+    for (int r = 0; r <= P; ++r)
+        for (int e = 0; e <= P; ++e) out[r][e] = scale * B[P][r][e];
+}
+
 template <int P>
 constexpr SpanPieces<P> make_span_pieces(double scale)
 {
@@ -144,31 +181,10 @@ constexpr SpanPieces<P> make_span_pieces(double scale)
                 int v = j < -(P - 1 - a) ? -(P - 1 - a) : j;
                 kap[j + P - 1] = v > P - b ? P - b : v;
             }
-            double B[P + 1][P + 1][P + 1] = {};  // [q][r][e]: N_{s-q+r, q}
-            B[0][0][0] = 1.0;
-            for (int q = 1; q <= P; ++q) {
-                for (int r = 0; r <= q; ++r) {
-                    const int i = r - q;
-                    if (r > 0) {  // (x - kappa(i)) / (kappa(i+q) - kappa(i)) N_{s+i, q-1}
-                        const double k0 = kap[i + P - 1], den = kap[i + q + P - 1] - k0;
-                        if (den != 0.0)
-                            for (int e = 0; e < q; ++e) {
-                                B[q][r][e + 1] += B[q - 1][r - 1][e] / den;
-                                B[q][r][e] -= k0 * B[q - 1][r - 1][e] / den;
-                            }
-                    }
-                    if (r < q) {  // (kappa(i+q+1) - x) / (kappa(i+q+1) - kappa(i+1)) N_{s+i+1, q-1}
-                        const double k1 = kap[i + q + P], den = k1 - kap[i + P];
-                        if (den != 0.0)
-                            for (int e = 0; e < q; ++e) {
-                                B[q][r][e] += k1 * B[q - 1][r][e] / den;
-                                B[q][r][e + 1] -= B[q - 1][r][e] / den;
-                            }
-                    }
-                }
-            }
+            double c[P + 1][P + 1] = {};
+            pieces_from_knots<P>(kap, scale, c);
             for (int r = 0; r <= P; ++r)
-                for (int e = 0; e <= P; ++e) out.c[a * P + b][r][e] = static_cast<float>(scale * B[P][r][e]);
+                for (int e = 0; e <= P; ++e) out.c[a * P + b][r][e] = static_cast<float>(c[r][e]);
         }
     }
     return out;
@@ -259,6 +275,63 @@ __device__ __forceinline__ void basis(float x, int k, int m, float N[P + 1], flo
 {
     if (span_interior<P>(k, m)) basis_uniform_scaled<P>(x, N, dN);
     else basis_table<P>(x, k, m, N, dN);
+}
+
+// ---------------------------------------------------------------------------
+// General (non-uniform) clamped knots.  Per axis the model holds the m+1
+// span breakpoints b_k = t_{p+k}, the inverse widths 1/(b_{k+1} - b_k) and,
+// per span, the monomial coefficients of its P+1 basis functions in the local
+// coordinate x = (u - b_k) / (b_{k+1} - b_k), times BasisScale<P>, each span's
+// block padded to a multiple of 4 floats (16-byte aligned).
+// ---------------------------------------------------------------------------
+template <int P>
+struct GeneralPieces {
+    static constexpr int kStride = ((P + 1) * (P + 1) + 3) / 4 * 4;  // floats per span
+};
+
+// Span k in [0, m-1] with b_k <= u < b_{k+1} (u = 1 in the last span) for
+// FP32 u in [0, 1]: binary search over the breakpoints, exact FP32 compares,
+// at most ceil(log2 m) steps.
+__device__ __forceinline__ int span_search(const float *__restrict__ brk, int m, float u)
+{
+    int lo = 0, hi = m - 1;  // brk[lo] <= u, answer in [lo, hi]
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(brk + mid) <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Basis (times BasisScale<P>) and derivative with respect to the local
+// coordinate on span k, from the span's pieces: Horner's rule for the value
+// and its derivative together.
+template <int P>
+__device__ __forceinline__ void basis_pieces(float x, const float *__restrict__ pieces, int k, float N[P + 1],
+                                             float dN[P + 1])
+{
+    constexpr int S = GeneralPieces<P>::kStride;
+    float c[S];
+    const float4 *src = reinterpret_cast<const float4 *>(pieces + static_cast<int64_t>(k) * S);
+#pragma unroll
+    for (int q = 0; q < S / 4; ++q) {
+        const float4 v = __ldg(src + q);
+        c[4 * q] = v.x;
+        c[4 * q + 1] = v.y;
+        c[4 * q + 2] = v.z;
+        c[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int r = 0; r <= P; ++r) {
+        float v = c[r * (P + 1) + P], d = 0.0f;
+#pragma unroll
+        for (int e = P - 1; e >= 0; --e) {
+            d = fmaf(d, x, v);
+            v = fmaf(v, x, c[r * (P + 1) + e]);
+        }
+        N[r] = v;
+        dN[r] = d;
+    }
 }
 
 // Exact k = floor(u*m) for FP32 u in [0, 1], clamped to [0, m-1].  The FP32

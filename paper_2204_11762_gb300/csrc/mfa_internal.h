@@ -23,6 +23,13 @@ struct ModelView {
     int p;          // degree (equal on all axes)
     int dtype;      // mfadvr_dtype
     float scale;    // storage scale s (1 for FP32)
+    // General (non-uniform) clamped knots when nu != 0; per axis: m+1 span
+    // breakpoints, m inverse span widths and per-span basis pieces (layout in
+    // mfa_basis.cuh, GeneralPieces).  Null with uniform knots (nu = 0).
+    int nu;
+    const float *brk[3];
+    const float *ih[3];
+    const float *pieces[3];
 };
 
 // Everything the render kernel needs besides the model, in FP32, derived on
@@ -33,7 +40,7 @@ struct RenderSetup {
     float eye[3], fwd[3], right[3], up[3];
     float sx_scale, sx_off, sy_scale, sy_off;  // sx = sx_scale*(x+1/2) + sx_off
     float box_min[3], box_max[3], inv_ext[3];
-    float lat_scale[3];                 // world -> lattice units: m / extent
+    float lat_scale[3];                 // world -> lattice units: m / extent (general knots: 1 / extent)
     float grad_scale[3];                // contraction derivative -> world gradient
     float step, max_opacity, opacity_ratio;
     int correct_opacity;                // 1 when step != ref_step
@@ -73,11 +80,11 @@ cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t
 // rs.shading is 0 (no gradient is needed).
 cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream);
 // Batched render of njobs jobs of degree p and storage dtype, all with
-// shading on (grad = 1) or all off (grad = 0) (jobs_dev in device memory,
-// sorted by tile_begin, total_tiles tiles in all); `counter` is zeroed on
-// `stream` first.
-cudaError_t launch_render_batch(int p, int dtype, int grad, const RenderJob *jobs_dev, int njobs, int total_tiles,
-                                int ctas_per_sm, int *counter, cudaStream_t stream);
+// shading on (grad = 1) or all off (grad = 0), all on general knots (nu = 1)
+// or all on uniform ones (jobs_dev in device memory, sorted by tile_begin,
+// total_tiles tiles in all); `counter` is zeroed on `stream` first.
+cudaError_t launch_render_batch(int p, int dtype, int grad, int nu, const RenderJob *jobs_dev, int njobs,
+                                int total_tiles, int ctas_per_sm, int *counter, cudaStream_t stream);
 // Bytes of one row-layout entry (8 control points) in a storage type.
 constexpr size_t row_entry_bytes(int dtype) { return dtype == MFADVR_F32 ? 32 : 16; }
 // Builds the row array of an n0 x n1 x n2 FP32 lattice (device memory),

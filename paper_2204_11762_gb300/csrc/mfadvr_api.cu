@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "mfa_basis.cuh"
 #include "mfa_internal.h"
 #include "mfadvr.h"
 
@@ -75,6 +76,13 @@ ModelView view_of(const Model &m)
     for (int a = 0; a < 3; ++a) {
         v.n[a] = m.n[a];
         v.m[a] = m.n[a] - m.p;
+    }
+    v.nu = m.nu;
+    const float *k = static_cast<const float *>(m.d_knots);
+    for (int a = 0; a < 3; ++a) {
+        v.brk[a] = m.nu ? k + m.brk_off[a] : nullptr;
+        v.ih[a] = m.nu ? k + m.ih_off[a] : nullptr;
+        v.pieces[a] = m.nu ? k + m.pc_off[a] : nullptr;
     }
     return v;
 }
@@ -181,8 +189,11 @@ mfadvr_status make_setup(mfadvr_ctx *ctx, const Model &m, const mfadvr_camera *c
         rs->box_max[i] = m.box_max[i];
         const double ext = static_cast<double>(m.box_max[i]) - m.box_min[i];
         rs->inv_ext[i] = static_cast<float>(1.0 / ext);
-        rs->lat_scale[i] = static_cast<float>(static_cast<double>(m.n[i] - m.p) / ext);
-        rs->grad_scale[i] = static_cast<float>(static_cast<double>(m.n[i] - m.p) * m.scale / ext / bs3);
+        // uniform knots: lattice units (span k covers [k, k+1)); general
+        // knots: parameter units, the span's inverse width applied per sample
+        const double units = m.nu ? 1.0 : static_cast<double>(m.n[i] - m.p);
+        rs->lat_scale[i] = static_cast<float>(units / ext);
+        rs->grad_scale[i] = static_cast<float>(units * m.scale / ext / bs3);
     }
     rs->sx_scale = static_cast<float>(2.0 * a / W);
     rs->sx_off = static_cast<float>(-a);
@@ -278,15 +289,17 @@ std::vector<BatchGroup> pack_jobs(const RenderJob *jobs, int n, RenderJob *dst)
 {
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
-    auto key = [&](int a) { return std::make_tuple(jobs[a].mv.p, jobs[a].mv.dtype, jobs[a].rs.shading != 0); };
+    auto key = [&](int a) {
+        return std::make_tuple(jobs[a].mv.p, jobs[a].mv.dtype, jobs[a].rs.shading != 0, jobs[a].mv.nu != 0);
+    };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
     std::vector<BatchGroup> groups;
     for (int k = 0; k < n; ++k) {
         RenderJob jb = jobs[order[k]];
-        const int grad = jb.rs.shading != 0 ? 1 : 0;
+        const int grad = jb.rs.shading != 0 ? 1 : 0, nu = jb.mv.nu != 0 ? 1 : 0;
         if (groups.empty() || groups.back().p != jb.mv.p || groups.back().dtype != jb.mv.dtype ||
-            groups.back().grad != grad)
-            groups.push_back({jb.mv.p, jb.mv.dtype, grad, k, 0, 0});
+            groups.back().grad != grad || groups.back().nu != nu)
+            groups.push_back({jb.mv.p, jb.mv.dtype, grad, nu, k, 0, 0});
         BatchGroup &gr = groups.back();
         const int tw = 1 << jb.rs.tile_w_log2, th = 32 / tw;
         jb.tiles_x = (jb.rs.width + tw - 1) / tw;
@@ -306,6 +319,100 @@ void apply_tuning(const mfadvr_ctx *ctx, const Model &m, RenderSetup *rs)
     if (it == ctx->tuning.end()) return;
     rs->tile_w_log2 = ilog2_u64(static_cast<uint64_t>(it->second.tile_w));
     rs->ctas_per_sm = it->second.ctas_per_sm;
+}
+
+// ---- general (non-uniform) clamped knots --------------------------------
+
+// A clamped knot vector of n+p+1 finite FP32 values: p+1 zeros, strictly
+// increasing interior knots in (0, 1), p+1 ones.  Returns an empty string or
+// the reason it is not one.
+std::string knot_problem(const float *t, int n, int p)
+{
+    for (int i = 0; i < n + p + 1; ++i)
+        if (!std::isfinite(t[i])) return "knots must be finite";
+    for (int i = 0; i <= p; ++i)
+        if (t[i] != 0.0f || t[n + i] != 1.0f) return "knots must start with p+1 zeros and end with p+1 ones";
+    for (int i = p + 1; i <= n; ++i)
+        if (!(t[i] > t[i - 1])) return "interior knots must increase strictly inside (0, 1)";
+    return std::string();
+}
+
+// Per-span pieces of one axis with knot vector t (n+p+1 values, as FP64):
+// the span-local positions of the 2P knots around each span, then the
+// recurrence of pieces_from_knots, scaled by the device basis scale.
+template <int P>
+void axis_pieces(const std::vector<double> &t, int n, float *pieces)
+{
+    constexpr int S = GeneralPieces<P>::kStride;
+    const double scale = basis_scale_host(P);
+    for (int k = 0; k < n - P; ++k) {
+        const int s = P + k;
+        const double h = t[s + 1] - t[s];
+        double kap[2 * P] = {};
+        for (int j = 1 - P; j <= P; ++j) kap[j + P - 1] = (t[s + j] - t[s]) / h;
+        double c[P + 1][P + 1] = {};
+        pieces_from_knots<P>(kap, scale, c);
+        float *dst = pieces + static_cast<size_t>(k) * S;
+        for (int q = 0; q < S; ++q) dst[q] = 0.0f;
+        for (int r = 0; r <= P; ++r)
+            for (int e = 0; e <= P; ++e) dst[r * (P + 1) + e] = static_cast<float>(c[r][e]);
+    }
+}
+
+void axis_pieces_p(int p, const std::vector<double> &t, int n, float *pieces)
+{
+    switch (p) {
+    case 1: axis_pieces<1>(t, n, pieces); break;
+    case 2: axis_pieces<2>(t, n, pieces); break;
+    case 3: axis_pieces<3>(t, n, pieces); break;
+    case 4: axis_pieces<4>(t, n, pieces); break;
+    default: axis_pieces<5>(t, n, pieces); break;
+    }
+}
+
+int pieces_stride(int p)
+{
+    switch (p) {
+    case 1: return GeneralPieces<1>::kStride;
+    case 2: return GeneralPieces<2>::kStride;
+    case 3: return GeneralPieces<3>::kStride;
+    case 4: return GeneralPieces<4>::kStride;
+    default: return GeneralPieces<5>::kStride;
+    }
+}
+
+// Host image of a general-knot model's knot buffer: per axis the m+1
+// breakpoints t_p..t_n, the m inverse widths and the m x stride pieces, each
+// section starting on a 4-float (16-byte) boundary.  Axes without knots get
+// the uniform knots j/m rounded to FP32.
+std::vector<float> build_knot_buffer(const mfadvr_model_desc *desc, Model *m)
+{
+    auto up4 = [](size_t v) { return (v + 3) / 4 * 4; };
+    const int p = m->p;
+    std::vector<float> buf;
+    for (int a = 0; a < 3; ++a) {
+        const int n = m->n[a], mm = n - p;
+        std::vector<double> t(static_cast<size_t>(n + p + 1));
+        for (int i = 0; i < n + p + 1; ++i) {
+            if (desc->knots[a]) {
+                t[i] = desc->knots[a][i];
+            } else {
+                const int j = i < p ? 0 : (i > n ? mm : i - p);
+                t[i] = static_cast<float>(static_cast<double>(j) / mm);
+            }
+        }
+        m->brk_off[a] = buf.size();
+        buf.resize(up4(buf.size() + mm + 1), 0.0f);
+        for (int k = 0; k <= mm; ++k) buf[m->brk_off[a] + k] = static_cast<float>(t[p + k]);
+        m->ih_off[a] = buf.size();
+        buf.resize(up4(buf.size() + mm), 0.0f);
+        for (int k = 0; k < mm; ++k)
+            buf[m->ih_off[a] + k] = static_cast<float>(1.0 / (t[p + k + 1] - t[p + k]));
+        m->pc_off[a] = buf.size();
+        buf.resize(buf.size() + static_cast<size_t>(mm) * pieces_stride(p), 0.0f);
+        axis_pieces_p(p, t, n, buf.data() + m->pc_off[a]);
+    }
+    return buf;
 }
 
 }  // namespace api
@@ -431,8 +538,10 @@ mfadvr_status mfadvr_destroy(mfadvr_ctx *ctx)
     {
         DeviceGuard g(ctx->device);
         cudaDeviceSynchronize();
-        for (auto &kv : ctx->models)
+        for (auto &kv : ctx->models) {
             if (kv.second.d_rows) cudaFree(kv.second.d_rows);
+            if (kv.second.d_knots) cudaFree(kv.second.d_knots);
+        }
         if (ctx->counters) cudaFree(ctx->counters);
         if (ctx->d_jobs) cudaFree(ctx->d_jobs);
         if (ctx->h_jobs) cudaFreeHost(ctx->h_jobs);
@@ -451,8 +560,6 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
     if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
     if (!desc || !model_id) return fail(ctx, MFADVR_EINVAL, "desc and model_id must not be NULL");
     if (!desc->ctrl) return fail(ctx, MFADVR_EINVAL, "desc->ctrl must not be NULL");
-    for (int a = 0; a < 3; ++a)
-        if (desc->knots[a]) return fail(ctx, MFADVR_EUNSUPPORTED, "only clamped uniform knots (knots = NULL)");
     if (desc->storage != MFADVR_F32 && desc->storage != MFADVR_F16 && desc->storage != MFADVR_BF16)
         return fail(ctx, MFADVR_EINVAL, "unknown storage type %d", static_cast<int>(desc->storage));
     for (int a = 0; a < 3; ++a) {
@@ -468,6 +575,11 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
         return fail(ctx, MFADVR_EUNSUPPORTED, "degree above %d", MFADVR_MAX_DEGREE);
     if (desc->degree[0] != desc->degree[1] || desc->degree[0] != desc->degree[2])
         return fail(ctx, MFADVR_EUNSUPPORTED, "degrees must be equal on the three axes");
+    for (int a = 0; a < 3; ++a) {
+        if (!desc->knots[a]) continue;
+        const std::string why = knot_problem(desc->knots[a], desc->ncp[a], desc->degree[a]);
+        if (!why.empty()) return fail(ctx, MFADVR_EINVAL, "knots[%d]: %s", a, why.c_str());
+    }
 
     const uint64_t count = static_cast<uint64_t>(desc->ncp[0]) * desc->ncp[1] * desc->ncp[2];
     if (count >= (uint64_t(1) << 31))
@@ -494,6 +606,13 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
     m.pabs = pabs;
     m.scale = (desc->storage == MFADVR_F32 || pabs == 0.0f) ? 1.0f : pabs;
     m.bytes = count * row_entry_bytes(m.dtype);
+    std::vector<float> knot_buf;
+    if (desc->knots[0] || desc->knots[1] || desc->knots[2]) {
+        m.nu = 1;
+        knot_buf = build_knot_buffer(desc, &m);
+        m.knot_bytes = knot_buf.size() * sizeof(float);
+        m.bytes += m.knot_bytes;
+    }
     if (ctx->budget && ctx->used + m.bytes > ctx->budget)
         return fail(ctx, MFADVR_ENOMEM, "model of %llu bytes exceeds the HBM budget (%llu of %llu used)",
                     static_cast<unsigned long long>(m.bytes), static_cast<unsigned long long>(ctx->used),
@@ -508,6 +627,17 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
         return fail(ctx, MFADVR_ENOMEM, "cudaMalloc(%llu): %s", static_cast<unsigned long long>(m.bytes),
                     cudaGetErrorString(e));
     }
+    if (m.nu) {
+        e = cudaMalloc(&m.d_knots, m.knot_bytes);
+        if (e == cudaSuccess) e = cudaMemcpy(m.d_knots, knot_buf.data(), m.knot_bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(m.d_rows);
+            if (m.d_knots) cudaFree(m.d_knots);
+            return fail(ctx, MFADVR_ENOMEM, "knot tables of %llu bytes: %s",
+                        static_cast<unsigned long long>(m.knot_bytes), cudaGetErrorString(e));
+        }
+    }
     void *tmp = nullptr;
     e = cudaMalloc(&tmp, count * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(tmp, desc->ctrl, count * sizeof(float), cudaMemcpyHostToDevice);
@@ -518,6 +648,7 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
     if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) {
         cudaFree(m.d_rows);
+        if (m.d_knots) cudaFree(m.d_knots);
         return cuda_fail(ctx, e, "model upload");
     }
     const int32_t id = ctx->next_id++;
@@ -535,6 +666,7 @@ mfadvr_status mfadvr_unload_model(mfadvr_ctx *ctx, int32_t model_id)
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
     cudaFree(m->d_rows);
+    if (m->d_knots) cudaFree(m->d_knots);
     ctx->used -= m->bytes;
     ctx->models.erase(model_id);
     return MFADVR_OK;
@@ -668,7 +800,7 @@ mfadvr_status mfadvr_render_batch(mfadvr_ctx *ctx, int32_t njobs, const mfadvr_r
     for (const BatchGroup &gr : groups) {
         int *counter = nullptr;
         if (mfadvr_status st = next_counter(ctx, &counter)) return st;
-        e = launch_render_batch(gr.p, gr.dtype, gr.grad, dj + gr.first, gr.count, gr.tiles, 0, counter, s);
+        e = launch_render_batch(gr.p, gr.dtype, gr.grad, gr.nu, dj + gr.first, gr.count, gr.tiles, 0, counter, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "batched render launch");
     }
     e = cudaEventRecord(ctx->job_done[slot], s);

@@ -46,11 +46,12 @@ struct CacheCP {
 
 // Resident CTAs per SM the compiler is asked to fit: four (16 warps, at
 // most 128 registers a thread) up to degree 3, where the 64-value cache
-// fits beside the ray state; the degree-4 cache needs the whole register
-// file of a thread.
-template <int P>
+// fits beside the ray state; three on general knots, whose span bounds and
+// widths take nine more registers; the degree-4 cache needs the whole
+// register file of a thread.
+template <int P, bool NU>
 struct MinBlocks {
-    static constexpr int value = P <= 3 ? 4 : 1;
+    static constexpr int value = P <= 3 ? (NU ? 3 : 4) : 1;
 };
 
 // State of the ray a lane is marching.
@@ -59,6 +60,7 @@ struct LaneRay {
     float X0[3], dX[3], dir[3];  // sample s sits at lattice coordinates X0 + s dX
     float kf[3];                 // current span (local index) per axis, as float
     int kk[3];                   // the same as int
+    float lo[3], hi[3], ih[3];   // general knots: span bounds and inverse width per axis
     int base;                    // row-entry index of the span block's first control point
     bool interior;               // all three spans unclamped: uniform pieces apply
     float sf, nsf;               // samples contracted / samples on the ray
@@ -135,6 +137,8 @@ __device__ __forceinline__ bool start_ray(const RenderSetup &rs, int px, int py,
         ray.X0[a] = (fmaf(tm, ray.dir[a], o[a]) - rs.box_min[a]) * rs.lat_scale[a];
         ray.dX[a] = rs.step * ray.dir[a] * rs.lat_scale[a];
         ray.kf[a] = -2.0f;  // forces a span lookup at the first sample
+        ray.lo[a] = 2.0f;   // (general knots: an empty span)
+        ray.hi[a] = -1.0f;
     }
     ray.sf = 0.f;
     ray.Cr = ray.Cg = ray.Cb = ray.A = 0.f;
@@ -185,9 +189,11 @@ __device__ __forceinline__ float lg2_approx(float x)
 // FMAs with the serial TF / shading / compositing chain.  Early termination
 // is decided on the composited sample; the query of sample sf is then
 // dropped, as is the one past the last sample.  G: the gradient is queried
-// (shading on); without it the value-only contraction runs.  Returns true
+// (shading on); without it the value-only contraction runs.  NU: general
+// knots, the ray walked in parameter units, the span found by binary search
+// on a span change and the basis taken from the span's pieces.  Returns true
 // when the ray is finished (pixel written).
-template <int P, typename T, bool G, typename Tf>
+template <int P, typename T, bool G, bool NU, typename Tf>
 __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSetup &rs, const Tf &tf, LaneRay &ray,
                                             SpanCache<P> &cache)
 {
@@ -199,19 +205,39 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
     // the span changes (a sample outside [0, m] always leaves its span) ------
     float x[3];
     bool moved = false;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        x[a] = fmaf(s, ray.dX[a], ray.X0[a]) - ray.kf[a];
-        moved |= (x[a] < 0.0f) | (x[a] >= 1.0f);
-    }
-    if (moved) {
+    if constexpr (NU) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const float mfa = static_cast<float>(mv.m[a]);
-            const float X = fminf(fmaxf(fmaf(s, ray.dX[a], ray.X0[a]), 0.0f), mfa);
-            ray.kf[a] = fminf(floorf(X), mfa - 1.0f);
-            x[a] = X - ray.kf[a];
-            ray.kk[a] = static_cast<int>(ray.kf[a]);
+            x[a] = fmaf(s, ray.dX[a], ray.X0[a]);  // parameter u, turned local below
+            moved |= (x[a] < ray.lo[a]) | (x[a] >= ray.hi[a]);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            x[a] = fmaf(s, ray.dX[a], ray.X0[a]) - ray.kf[a];
+            moved |= (x[a] < 0.0f) | (x[a] >= 1.0f);
+        }
+    }
+    if (moved) {
+        if constexpr (NU) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                x[a] = clamp01f(x[a]);
+                const int k = span_search(mv.brk[a], mv.m[a], x[a]);
+                ray.kk[a] = k;
+                ray.lo[a] = __ldg(mv.brk[a] + k);
+                ray.hi[a] = __ldg(mv.brk[a] + k + 1);
+                ray.ih[a] = __ldg(mv.ih[a] + k);
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float mfa = static_cast<float>(mv.m[a]);
+                const float X = fminf(fmaxf(fmaf(s, ray.dX[a], ray.X0[a]), 0.0f), mfa);
+                ray.kf[a] = fminf(floorf(X), mfa - 1.0f);
+                x[a] = X - ray.kf[a];
+                ray.kk[a] = static_cast<int>(ray.kf[a]);
+            }
         }
         ray.base = ray.kk[0] + mv.n[0] * ray.kk[1] + mv.n01 * ray.kk[2];
         ray.interior = span_interior<P>(ray.kk[0], mv.m[0]) && span_interior<P>(ray.kk[1], mv.m[1]) &&
@@ -227,15 +253,24 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
                     for (int i = 0; i <= P; ++i) cache.v[k][jp][i] = block_pair<P>(q, k, jp, i);
         }
     }
-    // uniform pieces, replaced from the piece table on clamped spans
     float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
-    basis_uniform_scaled<P>(x[0], Nu, dNu);
-    basis_uniform_scaled<P>(x[1], Nv, dNv);
-    basis_uniform_scaled<P>(x[2], Nw, dNw);
-    if (!ray.interior) {
-        if (!span_interior<P>(ray.kk[0], mv.m[0])) basis_table<P>(x[0], ray.kk[0], mv.m[0], Nu, dNu);
-        if (!span_interior<P>(ray.kk[1], mv.m[1])) basis_table<P>(x[1], ray.kk[1], mv.m[1], Nv, dNv);
-        if (!span_interior<P>(ray.kk[2], mv.m[2])) basis_table<P>(x[2], ray.kk[2], mv.m[2], Nw, dNw);
+    if constexpr (NU) {
+        // local coordinate on the span, basis from the span's pieces
+#pragma unroll
+        for (int a = 0; a < 3; ++a) x[a] = (x[a] - ray.lo[a]) * ray.ih[a];
+        basis_pieces<P>(x[0], mv.pieces[0], ray.kk[0], Nu, dNu);
+        basis_pieces<P>(x[1], mv.pieces[1], ray.kk[1], Nv, dNv);
+        basis_pieces<P>(x[2], mv.pieces[2], ray.kk[2], Nw, dNw);
+    } else {
+        // uniform pieces, replaced from the piece table on clamped spans
+        basis_uniform_scaled<P>(x[0], Nu, dNu);
+        basis_uniform_scaled<P>(x[1], Nv, dNv);
+        basis_uniform_scaled<P>(x[2], Nw, dNw);
+        if (!ray.interior) {
+            if (!span_interior<P>(ray.kk[0], mv.m[0])) basis_table<P>(x[0], ray.kk[0], mv.m[0], Nu, dNu);
+            if (!span_interior<P>(ray.kk[1], mv.m[1])) basis_table<P>(x[1], ray.kk[1], mv.m[1], Nv, dNv);
+            if (!span_interior<P>(ray.kk[2], mv.m[2])) basis_table<P>(x[2], ray.kk[2], mv.m[2], Nw, dNw);
+        }
     }
 
     // ---- applyTFs on sample s - 1: linear interpolation in the table -------
@@ -286,6 +321,12 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
         contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw,
                        [&](int k, int jp, int i) { return row_pair<T>(mv.rows, base, n0, n01, k, jp, i); }, ray.r);
     }
+    if constexpr (NU && G) {
+        // d/du = (1 / span width) d/dx, applied now: the next iteration may
+        // change span before it shades this query
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ray.r[a + 1] *= ray.ih[a];
+    }
     ray.sf = s + 1.0f;
 
     // ---- early ray termination / end of the ray: s samples composited ------
@@ -300,8 +341,8 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
 // ---------------------------------------------------------------------------
 // One image
 // ---------------------------------------------------------------------------
-template <int P, typename T, bool G>
-__global__ void __launch_bounds__(kThreads, MinBlocks<P>::value)
+template <int P, typename T, bool G, bool NU>
+__global__ void __launch_bounds__(kThreads, MinBlocks<P, NU>::value)
     render_kernel(ModelView mv, RenderSetup rs, int *__restrict__ counter)
 {
     // transfer function as (entry, next entry - entry) pairs: one FMA per
@@ -351,15 +392,15 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P>::value)
             if (exhausted && __all_sync(kFull, idle)) break;
         }
         if (idle) continue;
-        if (sample_step<P, T, G>(mv, rs, tf, ray, cache)) idle = true;
+        if (sample_step<P, T, G, NU>(mv, rs, tf, ray, cache)) idle = true;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Many images (render jobs) of one degree and storage type
 // ---------------------------------------------------------------------------
-template <int P, typename T, bool G>
-__global__ void __launch_bounds__(kThreads, MinBlocks<P>::value)
+template <int P, typename T, bool G, bool NU>
+__global__ void __launch_bounds__(kThreads, MinBlocks<P, NU>::value)
     render_batch_kernel(const RenderJob *__restrict__ jobs, int njobs, int total_tiles, int *__restrict__ counter)
 {
     __shared__ RenderJob s_job[kWarps];  // the current job of each warp
@@ -415,7 +456,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P>::value)
         }
         if (idle) continue;
         const TfGlobal tf{J.rs.tf};
-        if (sample_step<P, T, G>(J.mv, J.rs, tf, ray, cache)) idle = true;
+        if (sample_step<P, T, G, NU>(J.mv, J.rs, tf, ray, cache)) idle = true;
     }
 }
 
@@ -427,17 +468,17 @@ int sm_count()
     return sms;
 }
 
-template <int P, typename T, bool G>
+template <int P, typename T, bool G, bool NU>
 cudaError_t launch_render_t(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream)
 {
     const size_t smem = 2 * sizeof(float4) * static_cast<size_t>(rs.tf_size);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(render_kernel<P, T, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(render_kernel<P, T, G, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem));
         if (e != cudaSuccess) return e;
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<P, T, G>, kThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<P, T, G, NU>, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (rs.ctas_per_sm > 0 && rs.ctas_per_sm < per_sm) per_sm = rs.ctas_per_sm;
@@ -449,16 +490,16 @@ cudaError_t launch_render_t(const ModelView &mv, const RenderSetup &rs, int *cou
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
     if (e != cudaSuccess) return e;
-    render_kernel<P, T, G><<<static_cast<int>(blocks), kThreads, smem, stream>>>(mv, rs, counter);
+    render_kernel<P, T, G, NU><<<static_cast<int>(blocks), kThreads, smem, stream>>>(mv, rs, counter);
     return cudaGetLastError();
 }
 
-template <int P, typename T, bool G>
+template <int P, typename T, bool G, bool NU>
 cudaError_t launch_batch_t(const RenderJob *jobs, int njobs, int total_tiles, int ctas_per_sm, int *counter,
                            cudaStream_t stream)
 {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_batch_kernel<P, T, G>, kThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_batch_kernel<P, T, G, NU>, kThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
@@ -468,38 +509,39 @@ cudaError_t launch_batch_t(const RenderJob *jobs, int njobs, int total_tiles, in
     if (blocks < 1) return cudaSuccess;
     e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
     if (e != cudaSuccess) return e;
-    render_batch_kernel<P, T, G><<<static_cast<int>(blocks), kThreads, 0, stream>>>(jobs, njobs, total_tiles, counter);
+    render_batch_kernel<P, T, G, NU><<<static_cast<int>(blocks), kThreads, 0, stream>>>(jobs, njobs, total_tiles, counter);
     return cudaGetLastError();
 }
 
-template <int P, typename T, bool G>
+template <int P, typename T, bool G, bool NU>
 struct RenderOne {
     static cudaError_t run(const ModelView *mv, const RenderSetup *rs, int *counter, cudaStream_t s)
     {
-        return launch_render_t<P, T, G>(*mv, *rs, counter, s);
+        return launch_render_t<P, T, G, NU>(*mv, *rs, counter, s);
     }
 };
-template <int P, typename T, bool G>
+template <int P, typename T, bool G, bool NU>
 struct RenderBatch {
     static cudaError_t run(const RenderJob *jobs, int njobs, int total_tiles, int ctas_per_sm, int *counter,
                            cudaStream_t s)
     {
-        return launch_batch_t<P, T, G>(jobs, njobs, total_tiles, ctas_per_sm, counter, s);
+        return launch_batch_t<P, T, G, NU>(jobs, njobs, total_tiles, ctas_per_sm, counter, s);
     }
 };
 
-// Instantiates F<P, T, G>::run for the model's degree, storage type and
-// whether the gradient is queried.
-template <template <int, typename, bool> class F, typename... A>
-cudaError_t dispatch(int p, int dtype, bool grad, A... args)
+// Instantiates F<P, T, G, NU>::run for the model's degree, storage type,
+// whether the gradient is queried and whether the knots are general.
+template <template <int, typename, bool, bool> class F, typename... A>
+cudaError_t dispatch(int p, int dtype, bool grad, bool nu, A... args)
 {
-#define MFADVR_GRAD_CASES(PP, TT) \
-    return grad ? F<PP, TT, true>::run(args...) : F<PP, TT, false>::run(args...);
+#define MFADVR_FLAG_CASES(PP, TT)                                                   \
+    if (nu) return grad ? F<PP, TT, true, true>::run(args...) : F<PP, TT, false, true>::run(args...); \
+    return grad ? F<PP, TT, true, false>::run(args...) : F<PP, TT, false, false>::run(args...);
 #define MFADVR_DTYPE_CASES(PP)                                   \
     switch (dtype) {                                             \
-    case MFADVR_F32: MFADVR_GRAD_CASES(PP, float)                \
-    case MFADVR_F16: MFADVR_GRAD_CASES(PP, __half)               \
-    case MFADVR_BF16: MFADVR_GRAD_CASES(PP, __nv_bfloat16)       \
+    case MFADVR_F32: MFADVR_FLAG_CASES(PP, float)                \
+    case MFADVR_F16: MFADVR_FLAG_CASES(PP, __half)               \
+    case MFADVR_BF16: MFADVR_FLAG_CASES(PP, __nv_bfloat16)       \
     default: return cudaErrorInvalidValue;                       \
     }
     switch (p) {
@@ -511,20 +553,21 @@ cudaError_t dispatch(int p, int dtype, bool grad, A... args)
     default: return cudaErrorInvalidValue;
     }
 #undef MFADVR_DTYPE_CASES
-#undef MFADVR_GRAD_CASES
+#undef MFADVR_FLAG_CASES
 }
 
 }  // namespace
 
 cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream)
 {
-    return dispatch<RenderOne>(mv.p, mv.dtype, rs.shading != 0, &mv, &rs, counter, stream);
+    return dispatch<RenderOne>(mv.p, mv.dtype, rs.shading != 0, mv.nu != 0, &mv, &rs, counter, stream);
 }
 
-cudaError_t launch_render_batch(int p, int dtype, int grad, const RenderJob *jobs_dev, int njobs, int total_tiles,
-                                int ctas_per_sm, int *counter, cudaStream_t stream)
+cudaError_t launch_render_batch(int p, int dtype, int grad, int nu, const RenderJob *jobs_dev, int njobs,
+                                int total_tiles, int ctas_per_sm, int *counter, cudaStream_t stream)
 {
-    return dispatch<RenderBatch>(p, dtype, grad != 0, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, stream);
+    return dispatch<RenderBatch>(p, dtype, grad != 0, nu != 0, jobs_dev, njobs, total_tiles, ctas_per_sm, counter,
+                                 stream);
 }
 
 }  // namespace mfadvr

@@ -115,9 +115,11 @@ extern "C" MFADVR_API mfadvr_status mfadvr_render_lattice_noalloc(
     mv.dtype = MFADVR_F32;
     mv.scale = 1.0f;
     mv.n01 = n[0] * n[1];
+    mv.nu = 0;  // clamped uniform knots
     for (int a = 0; a < 3; ++a) {
         mv.n[a] = n[a];
         mv.m[a] = n[a] - degree[0];
+        mv.brk[a] = mv.ih[a] = mv.pieces[a] = nullptr;
     }
     rs.tf = reinterpret_cast<const float4 *>(params->tf_rgba);
     rs.out = reinterpret_cast<float4 *>(rgba_dev);

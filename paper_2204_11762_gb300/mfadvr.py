@@ -256,8 +256,11 @@ class Context:
         return self._h.value
 
     # -- model store ------------------------------------------------------
-    def load_model(self, ctrl, degree, storage="f32", box_min=(0.0, 0.0, 0.0), box_max=(1.0, 1.0, 1.0)) -> int:
-        """ctrl: float32 array (n_w, n_v, n_u), u fastest in memory."""
+    def load_model(self, ctrl, degree, storage="f32", box_min=(0.0, 0.0, 0.0), box_max=(1.0, 1.0, 1.0),
+                   knots=None) -> int:
+        """ctrl: float32 array (n_w, n_v, n_u), u fastest in memory.  knots:
+        None (uniform) or three entries, each None or n_d + p + 1 clamped knots
+        (u, v, w order)."""
         ctrl = np.ascontiguousarray(ctrl, dtype=np.float32)
         if ctrl.ndim != 3:
             raise ValueError("ctrl must be a 3-D array (n_w, n_v, n_u)")
@@ -269,6 +272,12 @@ class Context:
         d.box_max[:] = [float(v) for v in box_max]
         d.ctrl = ctrl.ctypes.data
         d.storage = _DTYPES[storage] if isinstance(storage, str) else int(storage)
+        keep = []
+        for a, t in enumerate(knots or (None, None, None)):
+            if t is not None:
+                t = np.ascontiguousarray(t, dtype=np.float32).ravel()
+                keep.append(t)
+                d.knots[a] = t.ctypes.data
         mid = ctypes.c_int32(-1)
         self._check(self._L.mfadvr_load_model(self._h, ctypes.byref(d), ctypes.byref(mid)))
         return mid.value
