@@ -29,7 +29,7 @@ struct Model {
     int nu = 0;
     void *d_knots = nullptr;
     uint64_t knot_bytes = 0;
-    size_t brk_off[3] = {0, 0, 0}, ih_off[3] = {0, 0, 0}, pc_off[3] = {0, 0, 0};
+    size_t brk_off[3] = {0, 0, 0}, ih_off[3] = {0, 0, 0}, cell_off[3] = {0, 0, 0}, pc_off[3] = {0, 0, 0};
 };
 
 // Device buffer owned by the context, grown on demand (host-buffer calls).

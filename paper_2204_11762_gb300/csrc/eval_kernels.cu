@@ -43,9 +43,9 @@ __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const fl
         int k0, k1, k2;
         float x0, x1, x2, g0 = s0, g1 = s1, g2 = s2;
         if constexpr (NU) {
-            k0 = span_search(mv.brk[0], mv.m[0], u);
-            k1 = span_search(mv.brk[1], mv.m[1], v);
-            k2 = span_search(mv.brk[2], mv.m[2], w);
+            k0 = span_search(mv.brk[0], mv.cell[0], mv.grid[0], u);
+            k1 = span_search(mv.brk[1], mv.cell[1], mv.grid[1], v);
+            k2 = span_search(mv.brk[2], mv.cell[2], mv.grid[2], w);
             const float ih0 = __ldg(mv.ih[0] + k0), ih1 = __ldg(mv.ih[1] + k1), ih2 = __ldg(mv.ih[2] + k2);
             x0 = (u - __ldg(mv.brk[0] + k0)) * ih0;
             x1 = (v - __ldg(mv.brk[1] + k1)) * ih1;

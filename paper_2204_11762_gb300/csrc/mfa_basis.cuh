@@ -279,28 +279,40 @@ __device__ __forceinline__ void basis(float x, int k, int m, float N[P + 1], flo
 
 // ---------------------------------------------------------------------------
 // General (non-uniform) clamped knots.  Per axis the model holds the m+1
-// span breakpoints b_k = t_{p+k}, the inverse widths 1/(b_{k+1} - b_k) and,
-// per span, the monomial coefficients of its P+1 basis functions in the local
-// coordinate x = (u - b_k) / (b_{k+1} - b_k), times BasisScale<P>, each span's
-// block padded to a multiple of 4 floats (16-byte aligned).
+// span breakpoints b_k = t_{p+k}, the inverse widths 1/(b_{k+1} - b_k), a
+// lookup grid of G+1 cells (G = 2m; cell c holds the span containing c/G)
+// and, per span, the monomial coefficients of its P+1 basis functions in the
+// local coordinate x = (u - b_k) / (b_{k+1} - b_k), times BasisScale<P>,
+// each span's block padded to a multiple of 8 floats (one 32-byte sector per
+// 8 coefficients).
 // ---------------------------------------------------------------------------
 template <int P>
 struct GeneralPieces {
-    static constexpr int kStride = ((P + 1) * (P + 1) + 3) / 4 * 4;  // floats per span
+    static constexpr int kStride = ((P + 1) * (P + 1) + 7) / 8 * 8;  // floats per span
 };
 
-// Span k in [0, m-1] with b_k <= u < b_{k+1} (u = 1 in the last span) for
-// FP32 u in [0, 1]: binary search over the breakpoints, exact FP32 compares,
-// at most ceil(log2 m) steps.
-__device__ __forceinline__ int span_search(const float *__restrict__ brk, int m, float u)
+// Span k in [lo, hi] with b_k <= u < b_{k+1}, given b_lo <= u: binary search,
+// exact FP32 compares, at most ceil(log2(hi - lo + 1)) steps.
+__device__ __forceinline__ int span_bisect(const float *__restrict__ brk, int lo, int hi, float u)
 {
-    int lo = 0, hi = m - 1;  // brk[lo] <= u, answer in [lo, hi]
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (__ldg(brk + mid) <= u) lo = mid;
         else hi = mid - 1;
     }
     return lo;
+}
+
+// Span of FP32 u in [0, 1] (u = 1 in the last span) through the lookup grid.
+// With c* = floor(u G) the span lies in [cell[c*], cell[c*+1]]; the FP32
+// product u G can round across one integer, so [cell[c-1], cell[c+2]] is
+// searched, which holds that range whichever way it rounded.
+__device__ __forceinline__ int span_search(const float *__restrict__ brk, const int *__restrict__ cell, int G,
+                                           float u)
+{
+    const int c = min(static_cast<int>(u * static_cast<float>(G)), G);
+    const int lo = __ldg(cell + max(c - 1, 0)), hi = __ldg(cell + min(c + 2, G));
+    return span_bisect(brk, lo, hi, u);
 }
 
 // Basis (times BasisScale<P>) and derivative with respect to the local
@@ -312,15 +324,13 @@ __device__ __forceinline__ void basis_pieces(float x, const float *__restrict__ 
 {
     constexpr int S = GeneralPieces<P>::kStride;
     float c[S];
-    const float4 *src = reinterpret_cast<const float4 *>(pieces + static_cast<int64_t>(k) * S);
+    const float *src = pieces + static_cast<int64_t>(k) * S;
 #pragma unroll
-    for (int q = 0; q < S / 4; ++q) {
-        const float4 v = __ldg(src + q);
-        c[4 * q] = v.x;
-        c[4 * q + 1] = v.y;
-        c[4 * q + 2] = v.z;
-        c[4 * q + 3] = v.w;
-    }
+    for (int q = 0; q < S / 8; ++q)
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(c[8 * q]), "=f"(c[8 * q + 1]), "=f"(c[8 * q + 2]), "=f"(c[8 * q + 3]), "=f"(c[8 * q + 4]),
+              "=f"(c[8 * q + 5]), "=f"(c[8 * q + 6]), "=f"(c[8 * q + 7])
+            : "l"(src + 8 * q));
 #pragma unroll
     for (int r = 0; r <= P; ++r) {
         float v = c[r * (P + 1) + P], d = 0.0f;

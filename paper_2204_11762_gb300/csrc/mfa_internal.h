@@ -27,8 +27,10 @@ struct ModelView {
     // breakpoints, m inverse span widths and per-span basis pieces (layout in
     // mfa_basis.cuh, GeneralPieces).  Null with uniform knots (nu = 0).
     int nu;
+    int grid[3];  // lookup cells per axis (G = 2m)
     const float *brk[3];
     const float *ih[3];
+    const int *cell[3];
     const float *pieces[3];
 };
 

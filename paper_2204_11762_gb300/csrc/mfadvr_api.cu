@@ -80,8 +80,10 @@ ModelView view_of(const Model &m)
     v.nu = m.nu;
     const float *k = static_cast<const float *>(m.d_knots);
     for (int a = 0; a < 3; ++a) {
+        v.grid[a] = 2 * (m.n[a] - m.p);
         v.brk[a] = m.nu ? k + m.brk_off[a] : nullptr;
         v.ih[a] = m.nu ? k + m.ih_off[a] : nullptr;
+        v.cell[a] = m.nu ? reinterpret_cast<const int *>(k + m.cell_off[a]) : nullptr;
         v.pieces[a] = m.nu ? k + m.pc_off[a] : nullptr;
     }
     return v;
@@ -382,12 +384,13 @@ int pieces_stride(int p)
 }
 
 // Host image of a general-knot model's knot buffer: per axis the m+1
-// breakpoints t_p..t_n, the m inverse widths and the m x stride pieces, each
-// section starting on a 4-float (16-byte) boundary.  Axes without knots get
-// the uniform knots j/m rounded to FP32.
+// breakpoints t_p..t_n, the m inverse widths, the 2m+1 lookup cells (int32:
+// cell c holds the largest k with t_{p+k} <= c / 2m) and the m x stride
+// pieces, each section starting on an 8-float (32-byte) boundary.  Axes
+// without knots get the uniform knots j/m rounded to FP32.
 std::vector<float> build_knot_buffer(const mfadvr_model_desc *desc, Model *m)
 {
-    auto up4 = [](size_t v) { return (v + 3) / 4 * 4; };
+    auto up4 = [](size_t v) { return (v + 7) / 8 * 8; };
     const int p = m->p;
     std::vector<float> buf;
     for (int a = 0; a < 3; ++a) {
@@ -408,6 +411,15 @@ std::vector<float> build_knot_buffer(const mfadvr_model_desc *desc, Model *m)
         buf.resize(up4(buf.size() + mm), 0.0f);
         for (int k = 0; k < mm; ++k)
             buf[m->ih_off[a] + k] = static_cast<float>(1.0 / (t[p + k + 1] - t[p + k]));
+        const int G = 2 * mm;
+        m->cell_off[a] = buf.size();
+        buf.resize(up4(buf.size() + G + 1), 0.0f);
+        for (int c = 0, k = 0; c <= G; ++c) {
+            const double x = static_cast<double>(c) / G;
+            while (k + 1 < mm && t[p + k + 1] <= x) ++k;
+            const int32_t kc = k;
+            std::memcpy(&buf[m->cell_off[a] + c], &kc, sizeof kc);
+        }
         m->pc_off[a] = buf.size();
         buf.resize(buf.size() + static_cast<size_t>(mm) * pieces_stride(p), 0.0f);
         axis_pieces_p(p, t, n, buf.data() + m->pc_off[a]);

@@ -223,7 +223,7 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 x[a] = clamp01f(x[a]);
-                const int k = span_search(mv.brk[a], mv.m[a], x[a]);
+                const int k = span_search(mv.brk[a], mv.cell[a], mv.grid[a], x[a]);
                 ray.kk[a] = k;
                 ray.lo[a] = __ldg(mv.brk[a] + k);
                 ray.hi[a] = __ldg(mv.brk[a] + k + 1);

@@ -120,6 +120,8 @@ extern "C" MFADVR_API mfadvr_status mfadvr_render_lattice_noalloc(
         mv.n[a] = n[a];
         mv.m[a] = n[a] - degree[0];
         mv.brk[a] = mv.ih[a] = mv.pieces[a] = nullptr;
+        mv.cell[a] = nullptr;
+        mv.grid[a] = 0;
     }
     rs.tf = reinterpret_cast<const float4 *>(params->tf_rgba);
     rs.out = reinterpret_cast<float4 *>(rgba_dev);
