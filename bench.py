@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 # 128^3 workload from one ncu capture (profiles/render_kernel_gauss128_p3_persp1024.md),
 # valid only for the kernel sources it was taken on.
 RENDER_TRAFFIC = {"sources_sha256_16": "0c819b989c416b95", "bytes": 78245376}
-RENDER_SOURCES = ("paper_2204_11762_gb300/csrc/render_kernels.cu", "paper_2204_11762_gb300/csrc/mfa_basis.cuh",
+RENDER_SOURCES = ("paper_2204_11762_gb300/csrc/render_kernels.cuh", "paper_2204_11762_gb300/csrc/mfa_basis.cuh",
                   "paper_2204_11762_gb300/csrc/mfa_internal.h")
 
 METRIC = "MFA value+grad samples/s"

@@ -1,573 +1,33 @@
-// mfadvr_render: the ray caster of Algorithm 1 as one fused kernel, and its
-// batched form over many images and models.
-//
-// Per pixel: ray definition (Sec. 3.1), slab test against the world box
-// (Sample_First..Sample_Last), constant-distance samples, value and gradient
-// query of the MFA model, transfer-function lookup (applyTFs), optional
-// gradient shading (getLightingCoefficient / addShading), front-to-back
-// compositing (doColorCompositing) and early ray termination once the
-// cumulative opacity exceeds O_max.
-//
-// GPU mapping.  A persistent grid of warps takes 32-ray tiles (tile_w x
-// 32/tile_w pixels) from a global counter; every lane owns one ray and, when
-// its ray ends (exit or early termination), takes the next ray of the warp's
-// tile pool, so lanes stay busy however unequal the ray lengths are.  Each
-// lane walks its ray in lattice units (one FMA per axis per sample), keeps
-// the control points of its current span block in registers and reloads
-// them (ceil((p+1)/2) x ceil((p+1)/4) x (p+1) vector loads from the row
-// array) only when a sample leaves the span.  The contraction runs on packed
-// FP32 FMAs.
-//
-// The batched kernel runs the same per-ray code over the concatenated tiles
-// of many render jobs (one image of one model each).  A warp keeps its
-// current job's model and settings in a shared-memory slot and moves to the
-// next job's tiles only when all its lanes are idle.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-
-#include "mfa_basis.cuh"
+// mfadvr_render's launchers: pick the per-degree instantiation (the kernels
+// are in render_kernels.cuh, one degree per render_pN.cu).
 #include "mfa_internal.h"
+#include "render_kernels.cuh"
 
 namespace mfadvr {
-namespace {
-
-constexpr int kThreads = 128;
-constexpr int kWarps = kThreads / 32;
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ float clamp01f(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }
-
-// The span block is cached in registers up to degree 4; degree 5 (216
-// values) reads it from the row array at every sample.
-template <int P>
-struct CacheCP {
-    static constexpr bool value = P <= 4;
-};
-
-// Resident CTAs per SM the compiler is asked to fit: four (16 warps, at
-// most 128 registers a thread) up to degree 3, where the 64-value cache
-// fits beside the ray state; three on general knots, whose span bounds and
-// widths take nine more registers; the degree-4 cache needs the whole
-// register file of a thread.
-template <int P, bool NU>
-struct MinBlocks {
-    static constexpr int value = P <= 3 ? (NU ? 3 : 4) : 1;
-};
-
-// State of the ray a lane is marching.
-struct LaneRay {
-    int pix;
-    float X0[3], dX[3], dir[3];  // sample s sits at lattice coordinates X0 + s dX
-    float kf[3];                 // current span (local index) per axis, as float
-    int kk[3];                   // the same as int
-    float lo[3], hi[3], ih[3];   // general knots: span bounds and inverse width per axis
-    int base;                    // row-entry index of the span block's first control point
-    bool interior;               // all three spans unclamped: uniform pieces apply
-    float sf, nsf;               // samples contracted / samples on the ray
-    float Cr, Cg, Cb, A;         // premultiplied colour and opacity so far
-    float r[4];                  // query of sample sf - 1, not yet composited
-};
-
-template <int P>
-struct SpanCache {
-    static constexpr bool kOn = CacheCP<P>::value;
-    float2 v[kOn ? (P + 1) : 1][kOn ? Block<P>::JP : 1][kOn ? (P + 1) : 1];
-};
-
-// Pixel of ray slot `slot` (tile = slot / 32, lane-in-tile = slot % 32) for
-// tiles of 2^tw_log2 x 32/2^tw_log2 pixels, tiles_x tiles per image row.
-__device__ __forceinline__ void slot_pixel(int slot, int tiles_x, int tw_log2, int &px, int &py)
-{
-    const int tile = slot >> 5, l = slot & 31;
-    const int th_log2 = 5 - tw_log2;
-    px = ((tile % tiles_x) << tw_log2) + (l & ((1 << tw_log2) - 1));
-    py = ((tile / tiles_x) << th_log2) + (l >> tw_log2);
-}
-
-// Ray definition and slab test for pixel (px, py).  Returns true when the
-// ray has samples; otherwise writes the empty pixel and returns false.
-__device__ __forceinline__ bool start_ray(const RenderSetup &rs, int px, int py, LaneRay &ray)
-{
-    ray.pix = py * rs.width + px;
-    const float sx = fmaf(rs.sx_scale, static_cast<float>(px) + 0.5f, rs.sx_off);
-    const float sy = fmaf(rs.sy_scale, static_cast<float>(py) + 0.5f, rs.sy_off);
-    float o[3];
-    if (rs.kind == 0) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            o[a] = fmaf(sy, rs.up[a], fmaf(sx, rs.right[a], rs.eye[a]));
-            ray.dir[a] = rs.fwd[a];
-        }
-    } else {
-        float dd = 0.f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            o[a] = rs.eye[a];
-            ray.dir[a] = fmaf(sy, rs.up[a], fmaf(sx, rs.right[a], rs.fwd[a]));
-            dd = fmaf(ray.dir[a], ray.dir[a], dd);
-        }
-        const float inv = 1.0f / sqrtf(dd);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) ray.dir[a] *= inv;
-    }
-    // slab test: [t0, t1] inside the box, t0 >= 0
-    float t0 = 0.0f, t1 = INFINITY;
-    bool hit = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (ray.dir[a] == 0.0f) {
-            if (o[a] < rs.box_min[a] || o[a] > rs.box_max[a]) hit = false;
-        } else {
-            float ta = (rs.box_min[a] - o[a]) / ray.dir[a];
-            float tb = (rs.box_max[a] - o[a]) / ray.dir[a];
-            if (ta > tb) { const float s = ta; ta = tb; tb = s; }
-            t0 = fmaxf(t0, ta);
-            t1 = fminf(t1, tb);
-        }
-    }
-    ray.nsf = (hit && t1 > t0) ? floorf((t1 - t0) / rs.step) : 0.0f;
-    if (ray.nsf < 1.0f) {
-        rs.out[ray.pix] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (rs.nsamples) rs.nsamples[ray.pix] = 0;
-        return false;
-    }
-    const float tm = fmaf(0.5f, rs.step, t0);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        ray.X0[a] = (fmaf(tm, ray.dir[a], o[a]) - rs.box_min[a]) * rs.lat_scale[a];
-        ray.dX[a] = rs.step * ray.dir[a] * rs.lat_scale[a];
-        ray.kf[a] = -2.0f;  // forces a span lookup at the first sample
-        ray.lo[a] = 2.0f;   // (general knots: an empty span)
-        ray.hi[a] = -1.0f;
-    }
-    ray.sf = 0.f;
-    ray.Cr = ray.Cg = ray.Cb = ray.A = 0.f;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) ray.r[c] = 0.f;
-    return true;
-}
-
-// Transfer-function lookups: `TfShared` reads (entry, next - entry) pairs the
-// kernel staged in shared memory; `TfGlobal` reads two entries of the
-// caller's table through the read-only cache.
-struct TfShared {
-    const float4 *t;
-    __device__ __forceinline__ void at(int i, float4 &a, float4 &d) const
-    {
-        a = t[2 * i];
-        d = t[2 * i + 1];
-    }
-};
-struct TfGlobal {
-    const float4 *t;
-    __device__ __forceinline__ void at(int i, float4 &a, float4 &d) const
-    {
-        a = __ldg(t + i);
-        const float4 b = __ldg(t + i + 1);
-        d = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
-    }
-};
-
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float lg2_approx(float x)
-{
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// One iteration of the lane's ray, software-pipelined over two samples:
-// the span bookkeeping (with a cache reload when the span changed), basis
-// and contraction of sample sf, and the applyTFs, shading and compositing
-// of sample sf - 1, whose query the previous iteration left in ray.r.  The
-// two halves are independent, so the compiler interleaves the contraction's
-// FMAs with the serial TF / shading / compositing chain.  Early termination
-// is decided on the composited sample; the query of sample sf is then
-// dropped, as is the one past the last sample.  G: the gradient is queried
-// (shading on); without it the value-only contraction runs.  NU: general
-// knots, the ray walked in parameter units, the span found by binary search
-// on a span change and the basis taken from the span's pieces.  Returns true
-// when the ray is finished (pixel written).
-template <int P, typename T, bool G, bool NU, typename Tf>
-__device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSetup &rs, const Tf &tf, LaneRay &ray,
-                                            SpanCache<P> &cache)
-{
-    constexpr int JP = Block<P>::JP;
-    constexpr bool kCache = SpanCache<P>::kOn;
-    const float s = ray.sf;
-
-    // ---- span of sample s; positions are clamped to the lattice only when
-    // the span changes (a sample outside [0, m] always leaves its span) ------
-    float x[3];
-    bool moved = false;
-    if constexpr (NU) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            x[a] = fmaf(s, ray.dX[a], ray.X0[a]);  // parameter u, turned local below
-            moved |= (x[a] < ray.lo[a]) | (x[a] >= ray.hi[a]);
-        }
-    } else {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            x[a] = fmaf(s, ray.dX[a], ray.X0[a]) - ray.kf[a];
-            moved |= (x[a] < 0.0f) | (x[a] >= 1.0f);
-        }
-    }
-    if (moved) {
-        if constexpr (NU) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                x[a] = clamp01f(x[a]);
-                const int k = span_search(mv.brk[a], mv.cell[a], mv.grid[a], x[a]);
-                ray.kk[a] = k;
-                ray.lo[a] = __ldg(mv.brk[a] + k);
-                ray.hi[a] = __ldg(mv.brk[a] + k + 1);
-                ray.ih[a] = __ldg(mv.ih[a] + k);
-            }
-        } else {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float mfa = static_cast<float>(mv.m[a]);
-                const float X = fminf(fmaxf(fmaf(s, ray.dX[a], ray.X0[a]), 0.0f), mfa);
-                ray.kf[a] = fminf(floorf(X), mfa - 1.0f);
-                x[a] = X - ray.kf[a];
-                ray.kk[a] = static_cast<int>(ray.kf[a]);
-            }
-        }
-        ray.base = ray.kk[0] + mv.n[0] * ray.kk[1] + mv.n01 * ray.kk[2];
-        ray.interior = span_interior<P>(ray.kk[0], mv.m[0]) && span_interior<P>(ray.kk[1], mv.m[1]) &&
-                       span_interior<P>(ray.kk[2], mv.m[2]);
-        if constexpr (kCache) {
-            Row q[P + 1][JP][Block<P>::IR];
-            load_block<P, T>(mv.rows, ray.base, mv.n[0], mv.n01, q);
-#pragma unroll
-            for (int k = 0; k <= P; ++k)
-#pragma unroll
-                for (int jp = 0; jp < JP; ++jp)
-#pragma unroll
-                    for (int i = 0; i <= P; ++i) cache.v[k][jp][i] = block_pair<P>(q, k, jp, i);
-        }
-    }
-    float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
-    if constexpr (NU) {
-        // local coordinate on the span, basis from the span's pieces
-#pragma unroll
-        for (int a = 0; a < 3; ++a) x[a] = (x[a] - ray.lo[a]) * ray.ih[a];
-        basis_pieces<P>(x[0], mv.pieces[0], ray.kk[0], Nu, dNu);
-        basis_pieces<P>(x[1], mv.pieces[1], ray.kk[1], Nv, dNv);
-        basis_pieces<P>(x[2], mv.pieces[2], ray.kk[2], Nw, dNw);
-    } else {
-        // uniform pieces, replaced from the piece table on clamped spans
-        basis_uniform_scaled<P>(x[0], Nu, dNu);
-        basis_uniform_scaled<P>(x[1], Nv, dNv);
-        basis_uniform_scaled<P>(x[2], Nw, dNw);
-        if (!ray.interior) {
-            if (!span_interior<P>(ray.kk[0], mv.m[0])) basis_table<P>(x[0], ray.kk[0], mv.m[0], Nu, dNu);
-            if (!span_interior<P>(ray.kk[1], mv.m[1])) basis_table<P>(x[1], ray.kk[1], mv.m[1], Nv, dNv);
-            if (!span_interior<P>(ray.kk[2], mv.m[2])) basis_table<P>(x[2], ray.kk[2], mv.m[2], Nw, dNw);
-        }
-    }
-
-    // ---- applyTFs on sample s - 1: linear interpolation in the table -------
-    const float r[4] = {ray.r[0], ray.r[1], ray.r[2], ray.r[3]};
-    const float xt = fminf(fmaxf(fmaf(r[0], rs.tf_a, rs.tf_b), 0.0f), static_cast<float>(rs.tf_size - 1));
-    const int it = min(static_cast<int>(xt), rs.tf_size - 2);
-    const float fr = xt - static_cast<float>(it);
-    float4 ta, td;
-    tf.at(it, ta, td);
-    float cr = fmaf(fr, td.x, ta.x);
-    float cg = fmaf(fr, td.y, ta.y);
-    float cb = fmaf(fr, td.z, ta.z);
-    float alpha = clamp01f(fmaf(fr, td.w, ta.w));
-    const float corrected = 1.0f - ex2_approx(lg2_approx(1.0f - alpha) * rs.opacity_ratio);
-    alpha = rs.correct_opacity ? corrected : alpha;
-    alpha = s > 0.0f ? alpha : 0.0f;  // no sample before the first
-
-    // ---- shading: Blinn-Phong, headlight L = V = -d, two-sided -------------
-    {
-        const float gx = r[1] * rs.grad_scale[0];
-        const float gy = r[2] * rs.grad_scale[1];
-        const float gz = r[3] * rs.grad_scale[2];
-        const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-        const float ndl =
-            fminf(fabsf(fmaf(gx, ray.dir[0], fmaf(gy, ray.dir[1], gz * ray.dir[2]))) * rsqrtf(g2), 1.0f);
-        const float spec = rs.ks * __powf(ndl, rs.shininess);
-        const float diff = fmaf(rs.kd, ndl, rs.ka);
-        const bool flat = g2 <= rs.gthresh2;
-        const bool lit = G && rs.shading != 0;
-        cr = lit ? (flat ? cr * rs.ka : clamp01f(fmaf(cr, diff, spec))) : cr;
-        cg = lit ? (flat ? cg * rs.ka : clamp01f(fmaf(cg, diff, spec))) : cg;
-        cb = lit ? (flat ? cb * rs.ka : clamp01f(fmaf(cb, diff, spec))) : cb;
-    }
-
-    // ---- front-to-back compositing of sample s - 1 -------------------------
-    const float wgt = (1.0f - ray.A) * alpha;
-    ray.Cr = fmaf(wgt, cr, ray.Cr);
-    ray.Cg = fmaf(wgt, cg, ray.Cg);
-    ray.Cb = fmaf(wgt, cb, ray.Cb);
-    ray.A += wgt;
-
-    // ---- query of sample s (composited by the next iteration) -------------
-    constexpr int Q = G ? kQueryBoth : kQueryValue;
-    if constexpr (kCache) {
-        contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return cache.v[k][jp][i]; }, ray.r);
-    } else {
-        const int n0 = mv.n[0], n01 = mv.n01, base = ray.base;
-        contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw,
-                       [&](int k, int jp, int i) { return row_pair<T>(mv.rows, base, n0, n01, k, jp, i); }, ray.r);
-    }
-    if constexpr (NU && G) {
-        // d/du = (1 / span width) d/dx, applied now: the next iteration may
-        // change span before it shades this query
-#pragma unroll
-        for (int a = 0; a < 3; ++a) ray.r[a + 1] *= ray.ih[a];
-    }
-    ray.sf = s + 1.0f;
-
-    // ---- early ray termination / end of the ray: s samples composited ------
-    if (s > 0.0f && (ray.A > rs.max_opacity || s >= ray.nsf)) {
-        rs.out[ray.pix] = make_float4(ray.Cr, ray.Cg, ray.Cb, ray.A);
-        if (rs.nsamples) rs.nsamples[ray.pix] = static_cast<int>(s);
-        return true;
-    }
-    return false;
-}
-
-// ---------------------------------------------------------------------------
-// One image
-// ---------------------------------------------------------------------------
-template <int P, typename T, bool G, bool NU>
-__global__ void __launch_bounds__(kThreads, MinBlocks<P, NU>::value)
-    render_kernel(ModelView mv, RenderSetup rs, int *__restrict__ counter)
-{
-    // transfer function as (entry, next entry - entry) pairs: one FMA per
-    // channel interpolates
-    extern __shared__ float4 s_tf[];
-    for (int i = threadIdx.x; i < rs.tf_size; i += blockDim.x) {
-        const float4 a = rs.tf[i];
-        const float4 b = (i + 1 < rs.tf_size) ? rs.tf[i + 1] : a;
-        s_tf[2 * i] = a;
-        s_tf[2 * i + 1] = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
-    }
-    __syncthreads();
-    const TfShared tf{s_tf};
-
-    const int lane = threadIdx.x & 31;
-    const unsigned lane_lt = (1u << lane) - 1u;
-    const int tw_log2 = rs.tile_w_log2;
-    const int tiles_x = (rs.width + (1 << tw_log2) - 1) >> tw_log2;
-    const int tiles_y = (rs.height + (32 >> tw_log2) - 1) >> (5 - tw_log2);
-    const int total = tiles_x * tiles_y * 32;  // ray slots, some outside the image
-
-    int pool_next = 0, pool_end = 0;
-    bool exhausted = false;
-    bool idle = true;
-    LaneRay ray;
-    SpanCache<P> cache;
-
-    for (;;) {
-        // ---- hand rays to idle lanes ----------------------------------------
-        const unsigned need = __ballot_sync(kFull, idle);
-        if (need) {
-            if (pool_next >= pool_end && !exhausted) {
-                int b = 0;
-                if (lane == 0) b = atomicAdd(counter, 32);
-                b = __shfl_sync(kFull, b, 0);
-                if (b >= total) exhausted = true;
-                else { pool_next = b; pool_end = b + 32; }
-            }
-            const int avail = pool_end - pool_next;
-            const int rank = __popc(need & lane_lt);
-            if (idle && rank < avail) {
-                int px, py;
-                slot_pixel(pool_next + rank, tiles_x, tw_log2, px, py);
-                if (px < rs.width && py < rs.height) idle = !start_ray(rs, px, py, ray);
-            }
-            pool_next += min(avail, __popc(need));
-            if (exhausted && __all_sync(kFull, idle)) break;
-        }
-        if (idle) continue;
-        if (sample_step<P, T, G, NU>(mv, rs, tf, ray, cache)) idle = true;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Many images (render jobs) of one degree and storage type
-// ---------------------------------------------------------------------------
-template <int P, typename T, bool G, bool NU>
-__global__ void __launch_bounds__(kThreads, MinBlocks<P, NU>::value)
-    render_batch_kernel(const RenderJob *__restrict__ jobs, int njobs, int total_tiles, int *__restrict__ counter)
-{
-    __shared__ RenderJob s_job[kWarps];  // the current job of each warp
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned lane_lt = (1u << lane) - 1u;
-    RenderJob &J = s_job[warp];
-
-    int cur = -1;   // current job
-    int held = -1;  // a fetched tile not yet handed out
-    int pool_next = 0, pool_end = 0;
-    bool exhausted = false;
-    bool idle = true;
-    LaneRay ray;
-    SpanCache<P> cache;
-
-    for (;;) {
-        const unsigned need = __ballot_sync(kFull, idle);
-        if (need) {
-            if (pool_next >= pool_end && held < 0 && !exhausted) {
-                int t = 0;
-                if (lane == 0) t = atomicAdd(counter, 1);
-                t = __shfl_sync(kFull, t, 0);
-                if (t >= total_tiles) exhausted = true;
-                else held = t;
-            }
-            if (held >= 0 && pool_next >= pool_end) {
-                // the job owning the tile: jobs are sorted by tile_begin
-                int j = 0;
-                while (j + 1 < njobs && __ldg(&jobs[j + 1].tile_begin) <= held) ++j;
-                if (j != cur && need == kFull) {
-                    // all lanes idle: take the new job's model and settings
-                    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(jobs + j);
-                    unsigned long long *dst = reinterpret_cast<unsigned long long *>(&J);
-                    for (int w = lane; w < static_cast<int>(sizeof(RenderJob) / 8); w += 32) dst[w] = src[w];
-                    __syncwarp();
-                    cur = j;
-                }
-                if (j == cur) {
-                    pool_next = (held - J.tile_begin) * 32;
-                    pool_end = pool_next + 32;
-                    held = -1;
-                }
-            }
-            const int avail = pool_end - pool_next;
-            const int rank = __popc(need & lane_lt);
-            if (idle && rank < avail) {
-                int px, py;
-                slot_pixel(pool_next + rank, J.tiles_x, J.rs.tile_w_log2, px, py);
-                if (px < J.rs.width && py < J.rs.height) idle = !start_ray(J.rs, px, py, ray);
-            }
-            pool_next += min(avail, __popc(need));
-            if (exhausted && held < 0 && __all_sync(kFull, idle)) break;
-        }
-        if (idle) continue;
-        const TfGlobal tf{J.rs.tf};
-        if (sample_step<P, T, G, NU>(J.mv, J.rs, tf, ray, cache)) idle = true;
-    }
-}
-
-int sm_count()
-{
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms;
-}
-
-template <int P, typename T, bool G, bool NU>
-cudaError_t launch_render_t(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream)
-{
-    const size_t smem = 2 * sizeof(float4) * static_cast<size_t>(rs.tf_size);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(render_kernel<P, T, G, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-    }
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<P, T, G, NU>, kThreads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    if (rs.ctas_per_sm > 0 && rs.ctas_per_sm < per_sm) per_sm = rs.ctas_per_sm;
-    // no more warps than ray tiles
-    const int tw = 1 << rs.tile_w_log2, th = 32 / tw;
-    const int64_t tiles = static_cast<int64_t>((rs.width + tw - 1) / tw) * ((rs.height + th - 1) / th);
-    int64_t blocks = static_cast<int64_t>(sm_count()) * per_sm;
-    const int64_t need = (tiles + kWarps - 1) / kWarps;
-    if (blocks > need) blocks = need;
-    e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
-    if (e != cudaSuccess) return e;
-    render_kernel<P, T, G, NU><<<static_cast<int>(blocks), kThreads, smem, stream>>>(mv, rs, counter);
-    return cudaGetLastError();
-}
-
-template <int P, typename T, bool G, bool NU>
-cudaError_t launch_batch_t(const RenderJob *jobs, int njobs, int total_tiles, int ctas_per_sm, int *counter,
-                           cudaStream_t stream)
-{
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_batch_kernel<P, T, G, NU>, kThreads, 0);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
-    int64_t blocks = static_cast<int64_t>(sm_count()) * per_sm;
-    const int64_t need = (static_cast<int64_t>(total_tiles) + kWarps - 1) / kWarps;
-    if (blocks > need) blocks = need;
-    if (blocks < 1) return cudaSuccess;
-    e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
-    if (e != cudaSuccess) return e;
-    render_batch_kernel<P, T, G, NU><<<static_cast<int>(blocks), kThreads, 0, stream>>>(jobs, njobs, total_tiles, counter);
-    return cudaGetLastError();
-}
-
-template <int P, typename T, bool G, bool NU>
-struct RenderOne {
-    static cudaError_t run(const ModelView *mv, const RenderSetup *rs, int *counter, cudaStream_t s)
-    {
-        return launch_render_t<P, T, G, NU>(*mv, *rs, counter, s);
-    }
-};
-template <int P, typename T, bool G, bool NU>
-struct RenderBatch {
-    static cudaError_t run(const RenderJob *jobs, int njobs, int total_tiles, int ctas_per_sm, int *counter,
-                           cudaStream_t s)
-    {
-        return launch_batch_t<P, T, G, NU>(jobs, njobs, total_tiles, ctas_per_sm, counter, s);
-    }
-};
-
-// Instantiates F<P, T, G, NU>::run for the model's degree, storage type,
-// whether the gradient is queried and whether the knots are general.
-template <template <int, typename, bool, bool> class F, typename... A>
-cudaError_t dispatch(int p, int dtype, bool grad, bool nu, A... args)
-{
-#define MFADVR_FLAG_CASES(PP, TT)                                                   \
-    if (nu) return grad ? F<PP, TT, true, true>::run(args...) : F<PP, TT, false, true>::run(args...); \
-    return grad ? F<PP, TT, true, false>::run(args...) : F<PP, TT, false, false>::run(args...);
-#define MFADVR_DTYPE_CASES(PP)                                   \
-    switch (dtype) {                                             \
-    case MFADVR_F32: MFADVR_FLAG_CASES(PP, float)                \
-    case MFADVR_F16: MFADVR_FLAG_CASES(PP, __half)               \
-    case MFADVR_BF16: MFADVR_FLAG_CASES(PP, __nv_bfloat16)       \
-    default: return cudaErrorInvalidValue;                       \
-    }
-    switch (p) {
-    case 1: MFADVR_DTYPE_CASES(1)
-    case 2: MFADVR_DTYPE_CASES(2)
-    case 3: MFADVR_DTYPE_CASES(3)
-    case 4: MFADVR_DTYPE_CASES(4)
-    case 5: MFADVR_DTYPE_CASES(5)
-    default: return cudaErrorInvalidValue;
-    }
-#undef MFADVR_DTYPE_CASES
-#undef MFADVR_FLAG_CASES
-}
-
-}  // namespace
 
 cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream)
 {
-    return dispatch<RenderOne>(mv.p, mv.dtype, rs.shading != 0, mv.nu != 0, &mv, &rs, counter, stream);
+    switch (mv.p) {
+    case 1: return launch_render_p1(mv, rs, counter, stream);
+    case 2: return launch_render_p2(mv, rs, counter, stream);
+    case 3: return launch_render_p3(mv, rs, counter, stream);
+    case 4: return launch_render_p4(mv, rs, counter, stream);
+    case 5: return launch_render_p5(mv, rs, counter, stream);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_render_batch(int p, int dtype, int grad, int nu, const RenderJob *jobs_dev, int njobs,
                                 int total_tiles, int ctas_per_sm, int *counter, cudaStream_t stream)
 {
-    return dispatch<RenderBatch>(p, dtype, grad != 0, nu != 0, jobs_dev, njobs, total_tiles, ctas_per_sm, counter,
-                                 stream);
+    switch (p) {
+    case 1: return launch_render_batch_p1(dtype, grad, nu, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, stream);
+    case 2: return launch_render_batch_p2(dtype, grad, nu, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, stream);
+    case 3: return launch_render_batch_p3(dtype, grad, nu, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, stream);
+    case 4: return launch_render_batch_p4(dtype, grad, nu, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, stream);
+    case 5: return launch_render_batch_p5(dtype, grad, nu, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, stream);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace mfadvr
