@@ -44,7 +44,7 @@ class Model(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32 * 3), ("n", ctypes.c_int32 * 3),
                 ("ctrl", ctypes.c_void_p),
                 ("box_min", ctypes.c_double * 3), ("box_max", ctypes.c_double * 3),
-                ("knots", ctypes.c_void_p * 3)]
+                ("knots", ctypes.c_void_p * 3), ("weights", ctypes.c_void_p)]
 
 
 class Camera(ctypes.Structure):
@@ -131,11 +131,13 @@ def basis_brute(n: int, p: int, u: float, t=None):
     return N, dN
 
 
-def _model(ctrl: np.ndarray, degree, box_min=(0.0, 0.0, 0.0), box_max=(1.0, 1.0, 1.0), knot_vectors=None):
+def _model(ctrl: np.ndarray, degree, box_min=(0.0, 0.0, 0.0), box_max=(1.0, 1.0, 1.0), knot_vectors=None,
+           weights=None):
     """ctrl: array of shape (n2, n1, n0) (u fastest in memory); FP32
     lattices convert to FP64 exactly.  knot_vectors: None or three entries,
-    each None (uniform) or the axis' n + p + 1 knots.  Returns the ctypes
-    model and the arrays it points into (keep them alive)."""
+    each None (uniform) or the axis' n + p + 1 knots.  weights: None
+    (non-rational) or positive weights shaped like ctrl (NURBS).  Returns the
+    ctypes model and the arrays it points into (keep them alive)."""
     ctrl = np.ascontiguousarray(ctrl, dtype=np.float64)
     if ctrl.ndim != 3:
         raise ValueError("ctrl must be 3-D (n_w, n_v, n_u)")
@@ -153,12 +155,18 @@ def _model(ctrl: np.ndarray, degree, box_min=(0.0, 0.0, 0.0), box_max=(1.0, 1.0,
             t = _knot_vector(m.n[a], m.p[a], t)
             keep.append(t)
             m.knots[a] = t.ctypes.data
+    if weights is not None:
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        if w.shape != ctrl.shape:
+            raise ValueError("weights must have the shape of ctrl")
+        keep.append(w)
+        m.weights = w.ctypes.data
     return m, keep
 
 
-def eval_points(ctrl, degree, uvw, *, brute=False, threads=None, with_spans=True, knot_vectors=None):
+def eval_points(ctrl, degree, uvw, *, brute=False, threads=None, with_spans=True, knot_vectors=None, weights=None):
     """Value and gradient (f, df/du, df/dv, df/dw) in FP64 at FP32 points."""
-    m, keep = _model(ctrl, degree, knot_vectors=knot_vectors)
+    m, keep = _model(ctrl, degree, knot_vectors=knot_vectors, weights=weights)
     uvw = np.ascontiguousarray(uvw, dtype=np.float32).reshape(-1, 3)
     npts = uvw.shape[0]
     out = np.zeros((npts, 4), dtype=np.float64)
@@ -174,10 +182,10 @@ def eval_points(ctrl, degree, uvw, *, brute=False, threads=None, with_spans=True
 
 
 def render(ctrl, degree, camera: dict, params: dict, *, box_min=(0, 0, 0), box_max=(1, 1, 1),
-           row_step=1, threads=None, brute=False, knot_vectors=None):
+           row_step=1, threads=None, brute=False, knot_vectors=None, weights=None):
     """Algorithm 1 in FP64.  Returns dict with rgba (H, W, 4), nsamples,
     nambig, rgba_alt, ns_lo and ns_hi (see orc_render in mfa_oracle.c)."""
-    m, keep = _model(ctrl, degree, box_min, box_max, knot_vectors)
+    m, keep = _model(ctrl, degree, box_min, box_max, knot_vectors, weights)
     cam = Camera()
     cam.kind = int(camera.get("kind", 1))
     cam.eye[:] = [float(x) for x in camera["eye"]]

@@ -15,6 +15,10 @@
  *    unless the model gives its own clamped knot vector for an axis (the
  *    non-uniform knots an adaptive MFA fit places, Sec. 2.3); the span
  *    search and the basis below take any clamped, non-decreasing vector.
+ *  - Rational models (NURBS, Sec. 2.3), when the model gives positive
+ *    weights w_ijk: f = A / W with A = sum w P N N N and W = sum w N N N (the
+ *    homogeneous form), and grad f = (grad A - f grad W) / W (quotient rule).
+ *    Without weights the model is the plain tensor-product B-spline.
  *  - Value and first partial derivatives at a parameter point, computed
  *    together (queryValueMFA / queryGradientMFA of Algorithm 1; Sec. 3.1 asks
  *    for all three derivatives at once).  Two modes:
@@ -149,6 +153,8 @@ typedef struct {
     double box_max[3];
     const double *knots[3]; /* NULL: clamped uniform knots; else the n+p+1
                                clamped, non-decreasing knots of the axis */
+    const double *weights;  /* NULL: non-rational; else n0*n1*n2 positive
+                               weights, indexed like ctrl */
 } orc_model;
 
 typedef struct {
@@ -160,6 +166,11 @@ static int ctx_init(orc_ctx *c, const orc_model *m)
 {
     c->m = m;
     for (int d = 0; d < 3; ++d) c->t[d] = NULL;
+    if (m->weights) { /* weights must be positive and finite */
+        const size_t count = (size_t)m->n[0] * (size_t)m->n[1] * (size_t)m->n[2];
+        for (size_t i = 0; i < count; ++i)
+            if (!(m->weights[i] > 0.0) || !isfinite(m->weights[i])) return -1;
+    }
     for (int d = 0; d < 3; ++d) {
         if (m->p[d] < 1 || m->p[d] > ORC_MAX_DEGREE || m->n[d] < m->p[d] + 1) return -1;
         const int n = m->n[d], p = m->p[d];
@@ -195,6 +206,20 @@ static double ctrl_at(const orc_model *m, int i, int j, int k)
     return m->ctrl[(size_t)i + (size_t)m->n[0] * ((size_t)j + (size_t)m->n[1] * (size_t)k)];
 }
 
+static double weight_at(const orc_model *m, int i, int j, int k)
+{
+    return m->weights[(size_t)i + (size_t)m->n[0] * ((size_t)j + (size_t)m->n[1] * (size_t)k)];
+}
+
+/* Rational model: the value and gradient of A / W from the homogeneous sums
+ * h = (A, A_u, A_v, A_w) and g = (W, W_u, W_v, W_w). */
+static void rational_quotient(const double h[4], const double g[4], double out[4])
+{
+    const double f = h[0] / g[0];
+    out[0] = f;
+    for (int d = 1; d < 4; ++d) out[d] = (h[d] - f * g[d]) / g[0];
+}
+
 /* f, df/du, df/dv, df/dw at parameter point q (already in [0,1]^3), span
  * mode.  The spans are written to s3 when it is not NULL. */
 static void eval_span(const orc_ctx *c, const double q[3], double out[4], int32_t *s3)
@@ -206,6 +231,23 @@ static void eval_span(const orc_ctx *c, const double q[3], double out[4], int32_
         s[d] = orc_find_span(m->n[d], m->p[d], c->t[d], q[d]);
         orc_basis_ders(s[d], q[d], m->p[d], c->t[d], N[d], dN[d]);
         if (s3) s3[d] = s[d];
+    }
+    if (m->weights) {
+        double h[4] = {0, 0, 0, 0}, g[4] = {0, 0, 0, 0};
+        for (int c2 = 0; c2 <= m->p[2]; ++c2)
+            for (int b = 0; b <= m->p[1]; ++b)
+                for (int a = 0; a <= m->p[0]; ++a) {
+                    const int i = s[0] - m->p[0] + a, j = s[1] - m->p[1] + b, k = s[2] - m->p[2] + c2;
+                    const double w = weight_at(m, i, j, k), wP = w * ctrl_at(m, i, j, k);
+                    const double B[4] = {N[0][a] * N[1][b] * N[2][c2], dN[0][a] * N[1][b] * N[2][c2],
+                                         N[0][a] * dN[1][b] * N[2][c2], N[0][a] * N[1][b] * dN[2][c2]};
+                    for (int d = 0; d < 4; ++d) {
+                        h[d] += B[d] * wP;
+                        g[d] += B[d] * w;
+                    }
+                }
+        rational_quotient(h, g, out);
+        return;
     }
     double f = 0, fu = 0, fv = 0, fw = 0;
     for (int c2 = 0; c2 <= m->p[2]; ++c2)
@@ -233,17 +275,20 @@ static void eval_brute(const orc_ctx *c, const double q[3], double out[4])
             dN[d][i] = orc_basis_brute_der(i, m->p[d], q[d], c->t[d], m->n[d]);
         }
     }
-    double f = 0, fu = 0, fv = 0, fw = 0;
+    double h[4] = {0, 0, 0, 0}, g[4] = {0, 0, 0, 0};
     for (int k = 0; k < m->n[2]; ++k)
         for (int j = 0; j < m->n[1]; ++j)
             for (int i = 0; i < m->n[0]; ++i) {
-                double P = ctrl_at(m, i, j, k);
-                f += N[0][i] * N[1][j] * N[2][k] * P;
-                fu += dN[0][i] * N[1][j] * N[2][k] * P;
-                fv += N[0][i] * dN[1][j] * N[2][k] * P;
-                fw += N[0][i] * N[1][j] * dN[2][k] * P;
+                const double w = m->weights ? weight_at(m, i, j, k) : 1.0, wP = w * ctrl_at(m, i, j, k);
+                const double B[4] = {N[0][i] * N[1][j] * N[2][k], dN[0][i] * N[1][j] * N[2][k],
+                                     N[0][i] * dN[1][j] * N[2][k], N[0][i] * N[1][j] * dN[2][k]};
+                for (int d = 0; d < 4; ++d) {
+                    h[d] += B[d] * wP;
+                    g[d] += B[d] * w;
+                }
             }
-    out[0] = f; out[1] = fu; out[2] = fv; out[3] = fw;
+    if (m->weights) rational_quotient(h, g, out);
+    else for (int d = 0; d < 4; ++d) out[d] = h[d];
     for (int d = 0; d < 3; ++d) { free(N[d]); free(dN[d]); }
 }
 
