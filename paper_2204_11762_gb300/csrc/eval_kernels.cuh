@@ -1,0 +1,176 @@
+// mfadvr_eval_points: value and first derivatives of the MFA model at
+// arbitrary parameter points (queryValueMFA + queryGradientMFA of
+// Algorithm 1, computed together as Sec. 3.1 describes), and the kernel that
+// builds a model's row array.  The kernel template lives here; eval_p1.cu ..
+// eval_p5.cu instantiate one degree each and eval_kernels.cu picks the degree
+// and builds the row arrays.
+//
+// One thread per point, grid-stride over a grid sized to the SM count.  The
+// span index is exact integer work (see span_exact); basis and contraction
+// run in FP32 on the FMA pipe; the span block is (p+1) x ceil((p+1)/2) x
+// ceil((p+1)/4) vector loads from the row array (L2-resident for the point
+// workloads), one L2 sector each in FP32.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "mfa_basis.cuh"
+#include "mfa_internal.h"
+
+namespace mfadvr {
+namespace {
+
+// NU: general knots (span search, per-span pieces); otherwise uniform knots
+// (exact floor, uniform pieces or the clamped-pattern table).
+template <int P, typename T, int Q, bool NU>
+__global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const float *__restrict__ params,
+                                                          int64_t n, float *__restrict__ out,
+                                                          int32_t *__restrict__ spans)
+{
+    const float mf0 = static_cast<float>(mv.m[0]);
+    const float mf1 = static_cast<float>(mv.m[1]);
+    const float mf2 = static_cast<float>(mv.m[2]);
+    constexpr float bs = BasisScale<P>::value;
+    const float sv = mv.scale / (bs * bs * bs);
+    const float s0 = sv * mf0, s1 = sv * mf1, s2 = sv * mf2;
+    const int n0 = mv.n[0], n01 = mv.n01;
+
+    for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < n;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        // Points and outputs stream through once: loaded and stored with the
+        // evict-first hint so that they do not push the row array out of L2.
+        // fminf/fmaxf return the non-NaN operand: NaN clamps to 0.
+        const float u = fminf(fmaxf(__ldcs(params + 3 * idx + 0), 0.0f), 1.0f);
+        const float v = fminf(fmaxf(__ldcs(params + 3 * idx + 1), 0.0f), 1.0f);
+        const float w = fminf(fmaxf(__ldcs(params + 3 * idx + 2), 0.0f), 1.0f);
+        int k0, k1, k2;
+        float x0, x1, x2, g0 = s0, g1 = s1, g2 = s2;
+        if constexpr (NU) {
+            k0 = span_search(mv.brk[0], mv.cell[0], mv.grid[0], u);
+            k1 = span_search(mv.brk[1], mv.cell[1], mv.grid[1], v);
+            k2 = span_search(mv.brk[2], mv.cell[2], mv.grid[2], w);
+            const float ih0 = __ldg(mv.ih[0] + k0), ih1 = __ldg(mv.ih[1] + k1), ih2 = __ldg(mv.ih[2] + k2);
+            x0 = (u - __ldg(mv.brk[0] + k0)) * ih0;
+            x1 = (v - __ldg(mv.brk[1] + k1)) * ih1;
+            x2 = (w - __ldg(mv.brk[2] + k2)) * ih2;
+            g0 = sv * ih0;  // d/du = (1 / span width) d/dx
+            g1 = sv * ih1;
+            g2 = sv * ih2;
+        } else {
+            k0 = span_exact(u, mv.m[0], mf0);
+            k1 = span_exact(v, mv.m[1], mf1);
+            k2 = span_exact(w, mv.m[2], mf2);
+            x0 = fmaf(u, mf0, -static_cast<float>(k0));
+            x1 = fmaf(v, mf1, -static_cast<float>(k1));
+            x2 = fmaf(w, mf2, -static_cast<float>(k2));
+        }
+        const int base = k0 + n0 * k1 + n01 * k2;
+        auto basis3 = [&](float *Nu, float *dNu, float *Nv, float *dNv, float *Nw, float *dNw) {
+            if constexpr (NU) {
+                basis_pieces<P>(x0, mv.pieces[0], k0, Nu, dNu);
+                basis_pieces<P>(x1, mv.pieces[1], k1, Nv, dNv);
+                basis_pieces<P>(x2, mv.pieces[2], k2, Nw, dNw);
+            } else {
+                basis<P>(x0, k0, mv.m[0], Nu, dNu);
+                basis<P>(x1, k1, mv.m[1], Nv, dNv);
+                basis<P>(x2, k2, mv.m[2], Nw, dNw);
+            }
+        };
+        float r[4];
+        float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
+        if constexpr (P <= 3) {
+            // the whole block in flight before the basis is evaluated
+            Row q[P + 1][Block<P>::JP][Block<P>::IR];
+            load_block<P, T>(mv.rows, base, n0, n01, q);
+            basis3(Nu, dNu, Nv, dNv, Nw, dNw);
+            contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return block_pair<P>(q, k, jp, i); },
+                           r);
+        } else {
+            basis3(Nu, dNu, Nv, dNv, Nw, dNw);
+            contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw,
+                           [&](int k, int jp, int i) { return row_pair<T>(mv.rows, base, n0, n01, k, jp, i); }, r);
+        }
+        if constexpr (Q == kQueryBoth) {
+            __stcs(reinterpret_cast<float4 *>(out) + idx, make_float4(r[0] * sv, r[1] * g0, r[2] * g1, r[3] * g2));
+        } else if constexpr (Q == kQueryValue) {
+            __stcs(out + idx, r[0] * sv);
+        } else {
+            __stcs(out + 3 * idx + 0, r[1] * g0);
+            __stcs(out + 3 * idx + 1, r[2] * g1);
+            __stcs(out + 3 * idx + 2, r[3] * g2);
+        }
+        if (spans) {
+            __stcs(spans + 3 * idx + 0, k0 + P);
+            __stcs(spans + 3 * idx + 1, k1 + P);
+            __stcs(spans + 3 * idx + 2, k2 + P);
+        }
+    }
+}
+
+template <int P, typename T, int Q, bool NU>
+cudaError_t launch_eval_k(const ModelView &mv, const float *params, int64_t n, float *out, int32_t *spans,
+                          cudaStream_t stream)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval_points_kernel<P, T, Q, NU>, 256, 0);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t need = (n + 255) / 256;
+    const int64_t cap = static_cast<int64_t>(sms) * per_sm;
+    const int blocks = static_cast<int>(need < cap ? need : cap);
+    eval_points_kernel<P, T, Q, NU><<<blocks, 256, 0, stream>>>(mv, params, n, out, spans);
+    return cudaGetLastError();
+}
+
+template <int P, typename T, int Q>
+cudaError_t launch_eval_q(const ModelView &mv, const float *params, int64_t n, float *out, int32_t *spans,
+                          cudaStream_t stream)
+{
+    return mv.nu ? launch_eval_k<P, T, Q, true>(mv, params, n, out, spans, stream)
+                 : launch_eval_k<P, T, Q, false>(mv, params, n, out, spans, stream);
+}
+
+template <int P, typename T>
+cudaError_t launch_eval_t(const ModelView &mv, const float *params, int64_t n, float *out, int query,
+                          int32_t *spans, cudaStream_t stream)
+{
+    switch (query) {
+    case kQueryValue: return launch_eval_q<P, T, kQueryValue>(mv, params, n, out, spans, stream);
+    case kQueryGradient: return launch_eval_q<P, T, kQueryGradient>(mv, params, n, out, spans, stream);
+    case kQueryBoth: return launch_eval_q<P, T, kQueryBoth>(mv, params, n, out, spans, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int P, typename T>
+cudaError_t launch_eval_dtype_p(const ModelView &mv, const float *params, int64_t n, float *out, int query,
+                                int32_t *spans, cudaStream_t stream)
+{
+    return launch_eval_t<P, T>(mv, params, n, out, query, spans, stream);
+}
+
+}  // namespace
+
+// The per-degree launcher one eval_pN.cu defines.
+#define MFADVR_EVAL_DEGREE(PP)                                                                                \
+    cudaError_t launch_eval_p##PP(const ModelView &mv, const float *params, int64_t n, float *out, int query,  \
+                                  int32_t *spans, cudaStream_t stream)                                        \
+    {                                                                                                         \
+        switch (mv.dtype) {                                                                                   \
+        case MFADVR_F32: return launch_eval_dtype_p<PP, float>(mv, params, n, out, query, spans, stream);     \
+        case MFADVR_F16: return launch_eval_dtype_p<PP, __half>(mv, params, n, out, query, spans, stream);    \
+        case MFADVR_BF16:                                                                                     \
+            return launch_eval_dtype_p<PP, __nv_bfloat16>(mv, params, n, out, query, spans, stream);          \
+        default: return cudaErrorInvalidValue;                                                                \
+        }                                                                                                     \
+    }
+
+cudaError_t launch_eval_p1(const ModelView &, const float *, int64_t, float *, int, int32_t *, cudaStream_t);
+cudaError_t launch_eval_p2(const ModelView &, const float *, int64_t, float *, int, int32_t *, cudaStream_t);
+cudaError_t launch_eval_p3(const ModelView &, const float *, int64_t, float *, int, int32_t *, cudaStream_t);
+cudaError_t launch_eval_p4(const ModelView &, const float *, int64_t, float *, int, int32_t *, cudaStream_t);
+cudaError_t launch_eval_p5(const ModelView &, const float *, int64_t, float *, int, int32_t *, cudaStream_t);
+
+}  // namespace mfadvr

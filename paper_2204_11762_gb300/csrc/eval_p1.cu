@@ -1,0 +1,7 @@
+// Point-query kernels of degree 1 (all storage types, query kinds and knot
+// kinds): instantiated here so that the degrees compile in parallel.
+#include "eval_kernels.cuh"
+
+namespace mfadvr {
+MFADVR_EVAL_DEGREE(1)
+}  // namespace mfadvr
