@@ -82,6 +82,13 @@ typedef struct {
                               and take the basis from per-span tables built
                               at load (NULL axes then use j/m rounded to FP32) */
     mfadvr_dtype storage;  /* storage type in HBM                              */
+    const float *weights;  /* NULL (non-rational) or HOST n0*n1*n2 positive
+                              finite weights indexed like ctrl: a rational
+                              model (NURBS, Sec. 2.3), f = sum w P N N N /
+                              sum w N N N.  The library stores w P and w in
+                              the storage type (16-bit: each with its own
+                              max-abs scale) and renders without the
+                              per-lane span cache, so it is slower */
 } mfadvr_model_desc;
 
 /* Camera in world space (the "Ray Definition" step of Sec. 3.1).  Frame:
@@ -128,7 +135,7 @@ MFADVR_API mfadvr_status mfadvr_destroy(mfadvr_ctx *ctx);
  * renderer's input).  Synchronous: the caller may free desc->ctrl on return.
  * *model_id receives a handle >= 0.  EINVAL: bad sizes, box, non-finite
  * control points, a knot vector that is not clamped and strictly increasing
- * inside.  EUNSUPPORTED: degree outside
+ * inside, a weight that is not positive and finite.  EUNSUPPORTED: degree outside
  * 1..MFADVR_MAX_DEGREE or unequal per axis.  ENOMEM: over budget. */
 MFADVR_API mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, int32_t *model_id);
 

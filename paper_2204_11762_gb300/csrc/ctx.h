@@ -28,6 +28,11 @@ struct Model {
     // breakpoints, inverse widths and per-span pieces at these float offsets.
     int nu = 0;
     void *d_knots = nullptr;
+    // Rational model: d_rows holds w P (scale `scale`), d_wrows holds w
+    // (scale wscale), both in the row layout and the storage type.
+    int rational = 0;
+    void *d_wrows = nullptr;
+    float wscale = 1.0f;
     uint64_t knot_bytes = 0;
     size_t brk_off[3] = {0, 0, 0}, ih_off[3] = {0, 0, 0}, cell_off[3] = {0, 0, 0}, pc_off[3] = {0, 0, 0};
 };
@@ -124,11 +129,11 @@ mfadvr_status make_job(mfadvr_ctx *ctx, const mfadvr_render_job &job, int index,
 // One launch of a batched render: jobs dst[first, first+count) of one degree
 // and storage type, `tiles` tiles in all.
 struct BatchGroup {
-    int p, dtype, grad, nu, first, count, tiles;
+    int p, dtype, grad, nu, rat, first, count, tiles;
 };
-// Orders n jobs by (degree, storage type, shading, general knots) into dst,
-// fills their tile fields and returns the launch groups (grad = shading: the
-// gradient is queried; nu: general knots).
+// Orders n jobs by (degree, storage type, shading, general knots, rational)
+// into dst, fills their tile fields and returns the launch groups (grad =
+// shading: the gradient is queried; nu: general knots; rat: weights).
 std::vector<BatchGroup> pack_jobs(const RenderJob *jobs, int n, RenderJob *dst);
 // Tears down a context's serving loop, if one runs (serve.cu).
 void stop_server(mfadvr_ctx *ctx);

@@ -22,8 +22,11 @@ namespace mfadvr {
 namespace {
 
 // NU: general knots (span search, per-span pieces); otherwise uniform knots
-// (exact floor, uniform pieces or the clamped-pattern table).
-template <int P, typename T, int Q, bool NU>
+// (exact floor, uniform pieces or the clamped-pattern table).  R: rational
+// model, rows hold w P and wrows w; f = A / W and grad f = (grad A - f grad W)
+// / W from the two contractions (the weights' gradient only when the
+// gradient is queried).
+template <int P, typename T, int Q, bool NU, bool R>
 __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const float *__restrict__ params,
                                                           int64_t n, float *__restrict__ out,
                                                           int32_t *__restrict__ spans)
@@ -32,9 +35,12 @@ __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const fl
     const float mf1 = static_cast<float>(mv.m[1]);
     const float mf2 = static_cast<float>(mv.m[2]);
     constexpr float bs = BasisScale<P>::value;
-    const float sv = mv.scale / (bs * bs * bs);
-    const float s0 = sv * mf0, s1 = sv * mf1, s2 = sv * mf2;
+    // value scale of a contraction: storage scale / basis scale^3 (a rational
+    // model's A / W carries neither)
+    const float sv = R ? 1.0f : mv.scale / (bs * bs * bs);
     const int n0 = mv.n[0], n01 = mv.n01;
+    // a rational query needs W always and A's value for the gradient too
+    constexpr int QA = R ? (Q == kQueryValue ? kQueryValue : kQueryBoth) : Q;
 
     for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < n;
          idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -45,18 +51,18 @@ __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const fl
         const float v = fminf(fmaxf(__ldcs(params + 3 * idx + 1), 0.0f), 1.0f);
         const float w = fminf(fmaxf(__ldcs(params + 3 * idx + 2), 0.0f), 1.0f);
         int k0, k1, k2;
-        float x0, x1, x2, g0 = s0, g1 = s1, g2 = s2;
+        float x0, x1, x2;
+        float d0 = mf0, d1 = mf1, d2 = mf2;  // d/du = d * d/dx (1 / span width)
         if constexpr (NU) {
             k0 = span_search(mv.brk[0], mv.cell[0], mv.grid[0], u);
             k1 = span_search(mv.brk[1], mv.cell[1], mv.grid[1], v);
             k2 = span_search(mv.brk[2], mv.cell[2], mv.grid[2], w);
-            const float ih0 = __ldg(mv.ih[0] + k0), ih1 = __ldg(mv.ih[1] + k1), ih2 = __ldg(mv.ih[2] + k2);
-            x0 = (u - __ldg(mv.brk[0] + k0)) * ih0;
-            x1 = (v - __ldg(mv.brk[1] + k1)) * ih1;
-            x2 = (w - __ldg(mv.brk[2] + k2)) * ih2;
-            g0 = sv * ih0;  // d/du = (1 / span width) d/dx
-            g1 = sv * ih1;
-            g2 = sv * ih2;
+            d0 = __ldg(mv.ih[0] + k0);
+            d1 = __ldg(mv.ih[1] + k1);
+            d2 = __ldg(mv.ih[2] + k2);
+            x0 = (u - __ldg(mv.brk[0] + k0)) * d0;
+            x1 = (v - __ldg(mv.brk[1] + k1)) * d1;
+            x2 = (w - __ldg(mv.brk[2] + k2)) * d2;
         } else {
             k0 = span_exact(u, mv.m[0], mf0);
             k1 = span_exact(v, mv.m[1], mf1);
@@ -66,7 +72,9 @@ __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const fl
             x2 = fmaf(w, mf2, -static_cast<float>(k2));
         }
         const int base = k0 + n0 * k1 + n01 * k2;
-        auto basis3 = [&](float *Nu, float *dNu, float *Nv, float *dNv, float *Nw, float *dNw) {
+        float r[4];
+        float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
+        auto basis3 = [&]() {
             if constexpr (NU) {
                 basis_pieces<P>(x0, mv.pieces[0], k0, Nu, dNu);
                 basis_pieces<P>(x1, mv.pieces[1], k1, Nv, dNv);
@@ -77,20 +85,31 @@ __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const fl
                 basis<P>(x2, k2, mv.m[2], Nw, dNw);
             }
         };
-        float r[4];
-        float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
-        if constexpr (P <= 3) {
+        if constexpr (P <= 3 && !R) {
             // the whole block in flight before the basis is evaluated
             Row q[P + 1][Block<P>::JP][Block<P>::IR];
             load_block<P, T>(mv.rows, base, n0, n01, q);
-            basis3(Nu, dNu, Nv, dNv, Nw, dNw);
+            basis3();
             contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return block_pair<P>(q, k, jp, i); },
                            r);
         } else {
-            basis3(Nu, dNu, Nv, dNv, Nw, dNw);
-            contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw,
-                           [&](int k, int jp, int i) { return row_pair<T>(mv.rows, base, n0, n01, k, jp, i); }, r);
+            basis3();
+            contract<P, QA>(Nu, dNu, Nv, dNv, Nw, dNw,
+                            [&](int k, int jp, int i) { return row_pair<T>(mv.rows, base, n0, n01, k, jp, i); }, r);
         }
+        if constexpr (R) {
+            float rw[4];
+            contract<P, QA>(Nu, dNu, Nv, dNv, Nw, dNw,
+                            [&](int k, int jp, int i) { return row_pair<T>(mv.wrows, base, n0, n01, k, jp, i); }, rw);
+            // the basis scale cancels in A / W; the storage scales do not
+            const float W = rw[0] * mv.wscale, f = (r[0] * mv.scale) / W;
+            if constexpr (QA == kQueryBoth) {
+#pragma unroll
+                for (int d = 1; d < 4; ++d) r[d] = (r[d] * mv.scale - f * (rw[d] * mv.wscale)) / W;
+            }
+            r[0] = f;
+        }
+        const float g0 = sv * d0, g1 = sv * d1, g2 = sv * d2;
         if constexpr (Q == kQueryBoth) {
             __stcs(reinterpret_cast<float4 *>(out) + idx, make_float4(r[0] * sv, r[1] * g0, r[2] * g1, r[3] * g2));
         } else if constexpr (Q == kQueryValue) {
@@ -108,19 +127,19 @@ __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const fl
     }
 }
 
-template <int P, typename T, int Q, bool NU>
+template <int P, typename T, int Q, bool NU, bool R>
 cudaError_t launch_eval_k(const ModelView &mv, const float *params, int64_t n, float *out, int32_t *spans,
                           cudaStream_t stream)
 {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval_points_kernel<P, T, Q, NU>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval_points_kernel<P, T, Q, NU, R>, 256, 0);
     if (per_sm < 1) per_sm = 1;
     const int64_t need = (n + 255) / 256;
     const int64_t cap = static_cast<int64_t>(sms) * per_sm;
     const int blocks = static_cast<int>(need < cap ? need : cap);
-    eval_points_kernel<P, T, Q, NU><<<blocks, 256, 0, stream>>>(mv, params, n, out, spans);
+    eval_points_kernel<P, T, Q, NU, R><<<blocks, 256, 0, stream>>>(mv, params, n, out, spans);
     return cudaGetLastError();
 }
 
@@ -128,8 +147,11 @@ template <int P, typename T, int Q>
 cudaError_t launch_eval_q(const ModelView &mv, const float *params, int64_t n, float *out, int32_t *spans,
                           cudaStream_t stream)
 {
-    return mv.nu ? launch_eval_k<P, T, Q, true>(mv, params, n, out, spans, stream)
-                 : launch_eval_k<P, T, Q, false>(mv, params, n, out, spans, stream);
+    if (mv.rational)
+        return mv.nu ? launch_eval_k<P, T, Q, true, true>(mv, params, n, out, spans, stream)
+                     : launch_eval_k<P, T, Q, false, true>(mv, params, n, out, spans, stream);
+    return mv.nu ? launch_eval_k<P, T, Q, true, false>(mv, params, n, out, spans, stream)
+                 : launch_eval_k<P, T, Q, false, false>(mv, params, n, out, spans, stream);
 }
 
 template <int P, typename T>

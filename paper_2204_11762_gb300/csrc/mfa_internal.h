@@ -26,6 +26,9 @@ struct ModelView {
     // General (non-uniform) clamped knots when nu != 0; per axis: m+1 span
     // breakpoints, m inverse span widths and per-span basis pieces (layout in
     // mfa_basis.cuh, GeneralPieces).  Null with uniform knots (nu = 0).
+    int rational;        // 1: rows hold w P, wrows the weights w (NURBS)
+    const void *wrows;
+    float wscale;        // storage scale of wrows (1 for FP32)
     int nu;
     int grid[3];  // lookup cells per axis (G = 2m)
     const float *brk[3];
@@ -83,9 +86,10 @@ cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t
 cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream);
 // Batched render of njobs jobs of degree p and storage dtype, all with
 // shading on (grad = 1) or all off (grad = 0), all on general knots (nu = 1)
-// or all on uniform ones (jobs_dev in device memory, sorted by tile_begin,
-// total_tiles tiles in all); `counter` is zeroed on `stream` first.
-cudaError_t launch_render_batch(int p, int dtype, int grad, int nu, const RenderJob *jobs_dev, int njobs,
+// or all on uniform ones, all rational (rat = 1) or none (jobs_dev in device
+// memory, sorted by tile_begin, total_tiles tiles in all); `counter` is
+// zeroed on `stream` first.
+cudaError_t launch_render_batch(int p, int dtype, int grad, int nu, int rat, const RenderJob *jobs_dev, int njobs,
                                 int total_tiles, int ctas_per_sm, int *counter, cudaStream_t stream);
 // Bytes of one row-layout entry (8 control points) in a storage type.
 constexpr size_t row_entry_bytes(int dtype) { return dtype == MFADVR_F32 ? 32 : 16; }

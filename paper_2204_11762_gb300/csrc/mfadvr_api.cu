@@ -77,6 +77,9 @@ ModelView view_of(const Model &m)
         v.n[a] = m.n[a];
         v.m[a] = m.n[a] - m.p;
     }
+    v.rational = m.rational;
+    v.wrows = m.d_wrows;
+    v.wscale = m.wscale;
     v.nu = m.nu;
     const float *k = static_cast<const float *>(m.d_knots);
     for (int a = 0; a < 3; ++a) {
@@ -195,7 +198,9 @@ mfadvr_status make_setup(mfadvr_ctx *ctx, const Model &m, const mfadvr_camera *c
         // knots: parameter units, the span's inverse width applied per sample
         const double units = m.nu ? 1.0 : static_cast<double>(m.n[i] - m.p);
         rs->lat_scale[i] = static_cast<float>(units / ext);
-        rs->grad_scale[i] = static_cast<float>(units * m.scale / ext / bs3);
+        // rational models: the kernel forms f = A / W from scaled sums, so
+        // its value and gradient carry neither the storage nor the basis scale
+        rs->grad_scale[i] = static_cast<float>(units * (m.rational ? 1.0 : m.scale / bs3) / ext);
     }
     rs->sx_scale = static_cast<float>(2.0 * a / W);
     rs->sx_off = static_cast<float>(-a);
@@ -210,7 +215,7 @@ mfadvr_status make_setup(mfadvr_ctx *ctx, const Model &m, const mfadvr_camera *c
     const double hi = std::isnan(rp->tf_hi) ? m.pmax : rp->tf_hi;
     const double last = rp->tf_size > 1 ? rp->tf_size - 1 : 1;
     const double inv_range = hi > lo ? 1.0 / (hi - lo) : 0.0;
-    rs->tf_a = static_cast<float>(static_cast<double>(m.scale) / bs3 * inv_range * last);
+    rs->tf_a = static_cast<float>((m.rational ? 1.0 : static_cast<double>(m.scale) / bs3) * inv_range * last);
     rs->tf_b = static_cast<float>(-lo * inv_range * last);
     rs->shading = rp->shading;
     rs->ka = rp->ka;
@@ -292,16 +297,17 @@ std::vector<BatchGroup> pack_jobs(const RenderJob *jobs, int n, RenderJob *dst)
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     auto key = [&](int a) {
-        return std::make_tuple(jobs[a].mv.p, jobs[a].mv.dtype, jobs[a].rs.shading != 0, jobs[a].mv.nu != 0);
+        return std::make_tuple(jobs[a].mv.p, jobs[a].mv.dtype, jobs[a].rs.shading != 0, jobs[a].mv.nu != 0,
+                               jobs[a].mv.rational != 0);
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
     std::vector<BatchGroup> groups;
     for (int k = 0; k < n; ++k) {
         RenderJob jb = jobs[order[k]];
-        const int grad = jb.rs.shading != 0 ? 1 : 0, nu = jb.mv.nu != 0 ? 1 : 0;
+        const int grad = jb.rs.shading != 0 ? 1 : 0, nu = jb.mv.nu != 0 ? 1 : 0, rat = jb.mv.rational != 0 ? 1 : 0;
         if (groups.empty() || groups.back().p != jb.mv.p || groups.back().dtype != jb.mv.dtype ||
-            groups.back().grad != grad || groups.back().nu != nu)
-            groups.push_back({jb.mv.p, jb.mv.dtype, grad, nu, k, 0, 0});
+            groups.back().grad != grad || groups.back().nu != nu || groups.back().rat != rat)
+            groups.push_back({jb.mv.p, jb.mv.dtype, grad, nu, rat, k, 0, 0});
         BatchGroup &gr = groups.back();
         const int tw = 1 << jb.rs.tile_w_log2, th = 32 / tw;
         jb.tiles_x = (jb.rs.width + tw - 1) / tw;
@@ -553,6 +559,7 @@ mfadvr_status mfadvr_destroy(mfadvr_ctx *ctx)
         for (auto &kv : ctx->models) {
             if (kv.second.d_rows) cudaFree(kv.second.d_rows);
             if (kv.second.d_knots) cudaFree(kv.second.d_knots);
+            if (kv.second.d_wrows) cudaFree(kv.second.d_wrows);
         }
         if (ctx->counters) cudaFree(ctx->counters);
         if (ctx->d_jobs) cudaFree(ctx->d_jobs);
@@ -605,9 +612,30 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
         pmax = v > pmax ? v : pmax;
         pabs = std::fabs(v) > pabs ? std::fabs(v) : pabs;
     }
+    // Rational model: the weighted points w P go to the row array in place
+    // of P, the weights to a second one.  Convex weights keep f inside
+    // [min P, max P], so the TF domain stays that of P.
+    std::vector<float> wctrl;
+    float qabs = pabs, wmax = 1.0f;
+    if (desc->weights) {
+        wctrl.resize(count);
+        qabs = 0.0f;
+        wmax = 0.0f;
+        for (uint64_t i = 0; i < count; ++i) {
+            const float w = desc->weights[i];
+            if (!(w > 0.0f) || !std::isfinite(w))
+                return fail(ctx, MFADVR_EINVAL, "weight %llu is not positive and finite",
+                            static_cast<unsigned long long>(i));
+            wctrl[i] = static_cast<float>(static_cast<double>(w) * desc->ctrl[i]);
+            if (!std::isfinite(wctrl[i])) return fail(ctx, MFADVR_EINVAL, "weight x control point overflows");
+            qabs = std::fabs(wctrl[i]) > qabs ? std::fabs(wctrl[i]) : qabs;
+            wmax = w > wmax ? w : wmax;
+        }
+    }
     Model m;
     m.p = desc->degree[0];
     m.dtype = desc->storage;
+    m.rational = desc->weights ? 1 : 0;
     for (int a = 0; a < 3; ++a) {
         m.n[a] = desc->ncp[a];
         m.box_min[a] = desc->box_min[a];
@@ -616,8 +644,10 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
     m.pmin = pmin;
     m.pmax = pmax;
     m.pabs = pabs;
-    m.scale = (desc->storage == MFADVR_F32 || pabs == 0.0f) ? 1.0f : pabs;
-    m.bytes = count * row_entry_bytes(m.dtype);
+    m.scale = (desc->storage == MFADVR_F32 || qabs == 0.0f) ? 1.0f : qabs;
+    m.wscale = (desc->storage == MFADVR_F32 || !m.rational) ? 1.0f : wmax;
+    const uint64_t rows_b = count * row_entry_bytes(m.dtype);
+    m.bytes = rows_b * (m.rational ? 2 : 1);
     std::vector<float> knot_buf;
     if (desc->knots[0] || desc->knots[1] || desc->knots[2]) {
         m.nu = 1;
@@ -632,7 +662,7 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
 
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
-    cudaError_t e = cudaMalloc(&m.d_rows, m.bytes);
+    cudaError_t e = cudaMalloc(&m.d_rows, rows_b);
     if (e != cudaSuccess) {
         cudaGetLastError();
         m.d_rows = nullptr;
@@ -651,16 +681,27 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
         }
     }
     void *tmp = nullptr;
-    e = cudaMalloc(&tmp, count * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemcpy(tmp, desc->ctrl, count * sizeof(float), cudaMemcpyHostToDevice);
+    if (m.rational) e = cudaMalloc(&m.d_wrows, rows_b);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, count * sizeof(float));
+    const float *rows_src = m.rational ? wctrl.data() : desc->ctrl;
+    if (e == cudaSuccess) e = cudaMemcpy(tmp, rows_src, count * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = launch_build_rows(static_cast<const float *>(tmp), m.d_rows, m.n[0], m.n[1], m.n[2], m.dtype,
                               1.0f / m.scale, nullptr);
+    if (e == cudaSuccess && m.rational) {
+        // the weights' row array (synchronise first: tmp is reused)
+        e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemcpy(tmp, desc->weights, count * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = launch_build_rows(static_cast<const float *>(tmp), m.d_wrows, m.n[0], m.n[1], m.n[2], m.dtype,
+                                  1.0f / m.wscale, nullptr);
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) {
         cudaFree(m.d_rows);
         if (m.d_knots) cudaFree(m.d_knots);
+        if (m.d_wrows) cudaFree(m.d_wrows);
         return cuda_fail(ctx, e, "model upload");
     }
     const int32_t id = ctx->next_id++;
@@ -679,6 +720,7 @@ mfadvr_status mfadvr_unload_model(mfadvr_ctx *ctx, int32_t model_id)
     cudaDeviceSynchronize();
     cudaFree(m->d_rows);
     if (m->d_knots) cudaFree(m->d_knots);
+    if (m->d_wrows) cudaFree(m->d_wrows);
     ctx->used -= m->bytes;
     ctx->models.erase(model_id);
     return MFADVR_OK;
@@ -812,7 +854,7 @@ mfadvr_status mfadvr_render_batch(mfadvr_ctx *ctx, int32_t njobs, const mfadvr_r
     for (const BatchGroup &gr : groups) {
         int *counter = nullptr;
         if (mfadvr_status st = next_counter(ctx, &counter)) return st;
-        e = launch_render_batch(gr.p, gr.dtype, gr.grad, gr.nu, dj + gr.first, gr.count, gr.tiles, 0, counter, s);
+        e = launch_render_batch(gr.p, gr.dtype, gr.grad, gr.nu, gr.rat, dj + gr.first, gr.count, gr.tiles, 0, counter, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "batched render launch");
     }
     e = cudaEventRecord(ctx->job_done[slot], s);

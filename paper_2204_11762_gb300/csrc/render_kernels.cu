@@ -17,15 +17,25 @@ cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, int *count
     }
 }
 
-cudaError_t launch_render_batch(int p, int dtype, int grad, int nu, const RenderJob *jobs_dev, int njobs,
+cudaError_t launch_render_batch(int p, int dtype, int grad, int nu, int rat, const RenderJob *jobs_dev, int njobs,
                                 int total_tiles, int ctas_per_sm, int *counter, cudaStream_t stream)
 {
     switch (p) {
-    case 1: return launch_render_batch_p1(dtype, grad, nu, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, stream);
-    case 2: return launch_render_batch_p2(dtype, grad, nu, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, stream);
-    case 3: return launch_render_batch_p3(dtype, grad, nu, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, stream);
-    case 4: return launch_render_batch_p4(dtype, grad, nu, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, stream);
-    case 5: return launch_render_batch_p5(dtype, grad, nu, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, stream);
+    case 1:
+        return launch_render_batch_p1(dtype, grad, nu, rat, jobs_dev, njobs, total_tiles, ctas_per_sm, counter,
+                                        stream);
+    case 2:
+        return launch_render_batch_p2(dtype, grad, nu, rat, jobs_dev, njobs, total_tiles, ctas_per_sm, counter,
+                                        stream);
+    case 3:
+        return launch_render_batch_p3(dtype, grad, nu, rat, jobs_dev, njobs, total_tiles, ctas_per_sm, counter,
+                                        stream);
+    case 4:
+        return launch_render_batch_p4(dtype, grad, nu, rat, jobs_dev, njobs, total_tiles, ctas_per_sm, counter,
+                                        stream);
+    case 5:
+        return launch_render_batch_p5(dtype, grad, nu, rat, jobs_dev, njobs, total_tiles, ctas_per_sm, counter,
+                                        stream);
     default: return cudaErrorInvalidValue;
     }
 }

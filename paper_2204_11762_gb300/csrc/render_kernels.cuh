@@ -42,20 +42,22 @@ constexpr unsigned kFull = 0xffffffffu;
 __device__ __forceinline__ float clamp01f(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }
 
 // The span block is cached in registers up to degree 4; degree 5 (216
-// values) reads it from the row array at every sample.
-template <int P>
+// values) and rational models (two blocks: w P and w) read it from the row
+// arrays at every sample.
+template <int P, bool R>
 struct CacheCP {
-    static constexpr bool value = P <= 4;
+    static constexpr bool value = P <= 4 && !R;
 };
 
 // Resident CTAs per SM the compiler is asked to fit: four (16 warps, at
 // most 128 registers a thread) up to degree 3, where the 64-value cache
 // fits beside the ray state; three on general knots, whose span bounds and
 // widths take nine more registers; the degree-4 cache needs the whole
-// register file of a thread.
-template <int P, bool NU>
+// register file of a thread; rational models keep no cache and two
+// contractions in flight.
+template <int P, bool NU, bool R>
 struct MinBlocks {
-    static constexpr int value = P <= 3 ? (NU ? 3 : 4) : 1;
+    static constexpr int value = R ? 2 : (P <= 3 ? (NU ? 3 : 4) : 1);
 };
 
 // State of the ray a lane is marching.
@@ -72,9 +74,9 @@ struct LaneRay {
     float r[4];                  // query of sample sf - 1, not yet composited
 };
 
-template <int P>
+template <int P, bool R>
 struct SpanCache {
-    static constexpr bool kOn = CacheCP<P>::value;
+    static constexpr bool kOn = CacheCP<P, R>::value;
     float2 v[kOn ? (P + 1) : 1][kOn ? Block<P>::JP : 1][kOn ? (P + 1) : 1];
 };
 
@@ -195,14 +197,16 @@ __device__ __forceinline__ float lg2_approx(float x)
 // dropped, as is the one past the last sample.  G: the gradient is queried
 // (shading on); without it the value-only contraction runs.  NU: general
 // knots, the ray walked in parameter units, the span found by binary search
-// on a span change and the basis taken from the span's pieces.  Returns true
-// when the ray is finished (pixel written).
-template <int P, typename T, bool G, bool NU, typename Tf>
+// on a span change and the basis taken from the span's pieces.  R: rational
+// model, the value f = A / W and its gradient (grad A - f grad W) / W from the
+// contractions of w P and of w.  Returns true when the ray is finished
+// (pixel written).
+template <int P, typename T, bool G, bool NU, bool R, typename Tf>
 __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSetup &rs, const Tf &tf, LaneRay &ray,
-                                            SpanCache<P> &cache)
+                                            SpanCache<P, R> &cache)
 {
     constexpr int JP = Block<P>::JP;
-    constexpr bool kCache = SpanCache<P>::kOn;
+    constexpr bool kCache = SpanCache<P, R>::kOn;
     const float s = ray.sf;
 
     // ---- span of sample s; positions are clamped to the lattice only when
@@ -324,6 +328,18 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
         const int n0 = mv.n[0], n01 = mv.n01, base = ray.base;
         contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw,
                        [&](int k, int jp, int i) { return row_pair<T>(mv.rows, base, n0, n01, k, jp, i); }, ray.r);
+        if constexpr (R) {
+            float rw[4];
+            contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw,
+                           [&](int k, int jp, int i) { return row_pair<T>(mv.wrows, base, n0, n01, k, jp, i); }, rw);
+            // the basis scale cancels in A / W; the storage scales do not
+            const float W = rw[0] * mv.wscale, f = (ray.r[0] * mv.scale) / W;
+            if constexpr (G) {
+#pragma unroll
+                for (int d = 1; d < 4; ++d) ray.r[d] = (ray.r[d] * mv.scale - f * (rw[d] * mv.wscale)) / W;
+            }
+            ray.r[0] = f;
+        }
     }
     if constexpr (NU && G) {
         // d/du = (1 / span width) d/dx, applied now: the next iteration may
@@ -345,8 +361,8 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
 // ---------------------------------------------------------------------------
 // One image
 // ---------------------------------------------------------------------------
-template <int P, typename T, bool G, bool NU>
-__global__ void __launch_bounds__(kThreads, MinBlocks<P, NU>::value)
+template <int P, typename T, bool G, bool NU, bool R>
+__global__ void __launch_bounds__(kThreads, MinBlocks<P, NU, R>::value)
     render_kernel(ModelView mv, RenderSetup rs, int *__restrict__ counter)
 {
     // transfer function as (entry, next entry - entry) pairs: one FMA per
@@ -372,7 +388,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P, NU>::value)
     bool exhausted = false;
     bool idle = true;
     LaneRay ray;
-    SpanCache<P> cache;
+    SpanCache<P, R> cache;
 
     for (;;) {
         // ---- hand rays to idle lanes ----------------------------------------
@@ -396,15 +412,15 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P, NU>::value)
             if (exhausted && __all_sync(kFull, idle)) break;
         }
         if (idle) continue;
-        if (sample_step<P, T, G, NU>(mv, rs, tf, ray, cache)) idle = true;
+        if (sample_step<P, T, G, NU, R>(mv, rs, tf, ray, cache)) idle = true;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Many images (render jobs) of one degree and storage type
 // ---------------------------------------------------------------------------
-template <int P, typename T, bool G, bool NU>
-__global__ void __launch_bounds__(kThreads, MinBlocks<P, NU>::value)
+template <int P, typename T, bool G, bool NU, bool R>
+__global__ void __launch_bounds__(kThreads, MinBlocks<P, NU, R>::value)
     render_batch_kernel(const RenderJob *__restrict__ jobs, int njobs, int total_tiles, int *__restrict__ counter)
 {
     __shared__ RenderJob s_job[kWarps];  // the current job of each warp
@@ -418,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P, NU>::value)
     bool exhausted = false;
     bool idle = true;
     LaneRay ray;
-    SpanCache<P> cache;
+    SpanCache<P, R> cache;
 
     for (;;) {
         const unsigned need = __ballot_sync(kFull, idle);
@@ -460,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P, NU>::value)
         }
         if (idle) continue;
         const TfGlobal tf{J.rs.tf};
-        if (sample_step<P, T, G, NU>(J.mv, J.rs, tf, ray, cache)) idle = true;
+        if (sample_step<P, T, G, NU, R>(J.mv, J.rs, tf, ray, cache)) idle = true;
     }
 }
 
@@ -472,17 +488,17 @@ int sm_count()
     return sms;
 }
 
-template <int P, typename T, bool G, bool NU>
+template <int P, typename T, bool G, bool NU, bool R>
 cudaError_t launch_render_t(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream)
 {
     const size_t smem = 2 * sizeof(float4) * static_cast<size_t>(rs.tf_size);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(render_kernel<P, T, G, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(render_kernel<P, T, G, NU, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem));
         if (e != cudaSuccess) return e;
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<P, T, G, NU>, kThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<P, T, G, NU, R>, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (rs.ctas_per_sm > 0 && rs.ctas_per_sm < per_sm) per_sm = rs.ctas_per_sm;
@@ -494,16 +510,16 @@ cudaError_t launch_render_t(const ModelView &mv, const RenderSetup &rs, int *cou
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
     if (e != cudaSuccess) return e;
-    render_kernel<P, T, G, NU><<<static_cast<int>(blocks), kThreads, smem, stream>>>(mv, rs, counter);
+    render_kernel<P, T, G, NU, R><<<static_cast<int>(blocks), kThreads, smem, stream>>>(mv, rs, counter);
     return cudaGetLastError();
 }
 
-template <int P, typename T, bool G, bool NU>
+template <int P, typename T, bool G, bool NU, bool R>
 cudaError_t launch_batch_t(const RenderJob *jobs, int njobs, int total_tiles, int ctas_per_sm, int *counter,
                            cudaStream_t stream)
 {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_batch_kernel<P, T, G, NU>, kThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_batch_kernel<P, T, G, NU, R>, kThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
@@ -513,41 +529,54 @@ cudaError_t launch_batch_t(const RenderJob *jobs, int njobs, int total_tiles, in
     if (blocks < 1) return cudaSuccess;
     e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
     if (e != cudaSuccess) return e;
-    render_batch_kernel<P, T, G, NU><<<static_cast<int>(blocks), kThreads, 0, stream>>>(jobs, njobs, total_tiles, counter);
+    render_batch_kernel<P, T, G, NU, R><<<static_cast<int>(blocks), kThreads, 0, stream>>>(jobs, njobs, total_tiles, counter);
     return cudaGetLastError();
 }
 
-template <int P, typename T, bool G, bool NU>
+template <int P, typename T, bool G, bool NU, bool R>
 struct RenderOne {
     static cudaError_t run(const ModelView *mv, const RenderSetup *rs, int *counter, cudaStream_t s)
     {
-        return launch_render_t<P, T, G, NU>(*mv, *rs, counter, s);
+        return launch_render_t<P, T, G, NU, R>(*mv, *rs, counter, s);
     }
 };
-template <int P, typename T, bool G, bool NU>
+template <int P, typename T, bool G, bool NU, bool R>
 struct RenderBatch {
     static cudaError_t run(const RenderJob *jobs, int njobs, int total_tiles, int ctas_per_sm, int *counter,
                            cudaStream_t s)
     {
-        return launch_batch_t<P, T, G, NU>(jobs, njobs, total_tiles, ctas_per_sm, counter, s);
+        return launch_batch_t<P, T, G, NU, R>(jobs, njobs, total_tiles, ctas_per_sm, counter, s);
     }
 };
 
-// Calls F<P, T, G, NU>::run for a fixed degree P and the model's storage
-// type, whether the gradient is queried and whether the knots are general.
-template <int P, template <int, typename, bool, bool> class F, typename... A>
-cudaError_t dispatch_degree(int dtype, bool grad, bool nu, A... args)
+// Calls F<P, T, G, NU, R>::run for a fixed degree P and the model's storage
+// type, whether the gradient is queried, whether the knots are general and
+// whether the model is rational.
+template <int P, typename TT, template <int, typename, bool, bool, bool> class F, typename... A>
+cudaError_t dispatch_flags(bool grad, bool nu, bool rat, A... args)
 {
-#define MFADVR_FLAG_CASES(TT)                                                                    \
-    if (nu) return grad ? F<P, TT, true, true>::run(args...) : F<P, TT, false, true>::run(args...); \
-    return grad ? F<P, TT, true, false>::run(args...) : F<P, TT, false, false>::run(args...);
+    const int k = (grad ? 4 : 0) | (nu ? 2 : 0) | (rat ? 1 : 0);
+    switch (k) {
+    case 0: return F<P, TT, false, false, false>::run(args...);
+    case 1: return F<P, TT, false, false, true>::run(args...);
+    case 2: return F<P, TT, false, true, false>::run(args...);
+    case 3: return F<P, TT, false, true, true>::run(args...);
+    case 4: return F<P, TT, true, false, false>::run(args...);
+    case 5: return F<P, TT, true, false, true>::run(args...);
+    case 6: return F<P, TT, true, true, false>::run(args...);
+    default: return F<P, TT, true, true, true>::run(args...);
+    }
+}
+
+template <int P, template <int, typename, bool, bool, bool> class F, typename... A>
+cudaError_t dispatch_degree(int dtype, bool grad, bool nu, bool rat, A... args)
+{
     switch (dtype) {
-    case MFADVR_F32: MFADVR_FLAG_CASES(float)
-    case MFADVR_F16: MFADVR_FLAG_CASES(__half)
-    case MFADVR_BF16: MFADVR_FLAG_CASES(__nv_bfloat16)
+    case MFADVR_F32: return dispatch_flags<P, float, F>(grad, nu, rat, args...);
+    case MFADVR_F16: return dispatch_flags<P, __half, F>(grad, nu, rat, args...);
+    case MFADVR_BF16: return dispatch_flags<P, __nv_bfloat16, F>(grad, nu, rat, args...);
     default: return cudaErrorInvalidValue;
     }
-#undef MFADVR_FLAG_CASES
 }
 
 }  // namespace
@@ -557,14 +586,15 @@ cudaError_t dispatch_degree(int dtype, bool grad, bool nu, A... args)
     cudaError_t launch_render_p##PP(const ModelView &mv, const RenderSetup &rs, int *counter,                 \
                                     cudaStream_t stream)                                                     \
     {                                                                                                        \
-        return dispatch_degree<PP, RenderOne>(mv.dtype, rs.shading != 0, mv.nu != 0, &mv, &rs, counter,       \
-                                               stream);                                                      \
+        return dispatch_degree<PP, RenderOne>(mv.dtype, rs.shading != 0, mv.nu != 0, mv.rational != 0, &mv, &rs, \
+                                               counter, stream);                                             \
     }                                                                                                        \
-    cudaError_t launch_render_batch_p##PP(int dtype, int grad, int nu, const RenderJob *jobs_dev, int njobs,  \
-                                          int total_tiles, int ctas_per_sm, int *counter, cudaStream_t stream) \
+    cudaError_t launch_render_batch_p##PP(int dtype, int grad, int nu, int rat, const RenderJob *jobs_dev,     \
+                                          int njobs, int total_tiles, int ctas_per_sm, int *counter,           \
+                                          cudaStream_t stream)                                               \
     {                                                                                                        \
-        return dispatch_degree<PP, RenderBatch>(dtype, grad != 0, nu != 0, jobs_dev, njobs, total_tiles,      \
-                                                 ctas_per_sm, counter, stream);                              \
+        return dispatch_degree<PP, RenderBatch>(dtype, grad != 0, nu != 0, rat != 0, jobs_dev, njobs,         \
+                                                 total_tiles, ctas_per_sm, counter, stream);                 \
     }
 
 cudaError_t launch_render_p1(const ModelView &, const RenderSetup &, int *, cudaStream_t);
@@ -572,10 +602,10 @@ cudaError_t launch_render_p2(const ModelView &, const RenderSetup &, int *, cuda
 cudaError_t launch_render_p3(const ModelView &, const RenderSetup &, int *, cudaStream_t);
 cudaError_t launch_render_p4(const ModelView &, const RenderSetup &, int *, cudaStream_t);
 cudaError_t launch_render_p5(const ModelView &, const RenderSetup &, int *, cudaStream_t);
-cudaError_t launch_render_batch_p1(int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);
-cudaError_t launch_render_batch_p2(int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);
-cudaError_t launch_render_batch_p3(int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);
-cudaError_t launch_render_batch_p4(int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);
-cudaError_t launch_render_batch_p5(int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);
+cudaError_t launch_render_batch_p1(int, int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);
+cudaError_t launch_render_batch_p2(int, int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);
+cudaError_t launch_render_batch_p3(int, int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);
+cudaError_t launch_render_batch_p4(int, int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);
+cudaError_t launch_render_batch_p5(int, int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);
 
 }  // namespace mfadvr

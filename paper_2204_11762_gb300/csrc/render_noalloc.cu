@@ -115,7 +115,10 @@ extern "C" MFADVR_API mfadvr_status mfadvr_render_lattice_noalloc(
     mv.dtype = MFADVR_F32;
     mv.scale = 1.0f;
     mv.n01 = n[0] * n[1];
-    mv.nu = 0;  // clamped uniform knots
+    mv.nu = 0;  // clamped uniform knots, non-rational
+    mv.rational = 0;
+    mv.wrows = nullptr;
+    mv.wscale = 1.0f;
     for (int a = 0; a < 3; ++a) {
         mv.n[a] = n[a];
         mv.m[a] = n[a] - degree[0];

@@ -62,7 +62,7 @@ struct Server {
         unsigned slot = 0;
         mfadvr_serve_trace_record rec{};
     };
-    using Signature = std::vector<std::tuple<int, int, int, int>>;
+    using Signature = std::vector<std::tuple<int, int, int, int, int>>;
 
     mfadvr_ctx *ctx = nullptr;
     int device = 0;
@@ -103,7 +103,7 @@ struct Server {
         for (size_t i = 0; i < batch.size(); ++i) src[i] = batch[i].job;
         std::vector<BatchGroup> groups = pack_jobs(src.data(), static_cast<int>(src.size()), hj);
         Signature sig;
-        for (const BatchGroup &g : groups) sig.emplace_back(g.p, g.dtype, g.grad, g.nu);
+        for (const BatchGroup &g : groups) sig.emplace_back(g.p, g.dtype, g.grad, g.nu, g.rat);
         *ngroups = static_cast<int>(groups.size());
 
         cudaStream_t s = streams[k];
@@ -114,7 +114,8 @@ struct Server {
         for (const BatchGroup &g : groups) {
             if (body != cudaSuccess) break;
             int *counter = counters + (next_counter++ % kCounters);
-            body = launch_render_batch(g.p, g.dtype, g.grad, g.nu, dj + g.first, g.count, g.tiles, 0, counter, s);
+            body = launch_render_batch(g.p, g.dtype, g.grad, g.nu, g.rat, dj + g.first, g.count, g.tiles, 0, counter,
+                                       s);
         }
         e = cudaStreamEndCapture(s, &graph);
         if (body != cudaSuccess) e = body;

@@ -46,7 +46,8 @@ class MfadvrError(RuntimeError):
 class ModelDesc(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int32 * 3), ("ncp", ctypes.c_int32 * 3),
                 ("box_min", ctypes.c_float * 3), ("box_max", ctypes.c_float * 3),
-                ("ctrl", ctypes.c_void_p), ("knots", ctypes.c_void_p * 3), ("storage", ctypes.c_int32)]
+                ("ctrl", ctypes.c_void_p), ("knots", ctypes.c_void_p * 3), ("storage", ctypes.c_int32),
+                ("weights", ctypes.c_void_p)]
 
 
 class Camera(ctypes.Structure):
@@ -257,10 +258,11 @@ class Context:
 
     # -- model store ------------------------------------------------------
     def load_model(self, ctrl, degree, storage="f32", box_min=(0.0, 0.0, 0.0), box_max=(1.0, 1.0, 1.0),
-                   knots=None) -> int:
+                   knots=None, weights=None) -> int:
         """ctrl: float32 array (n_w, n_v, n_u), u fastest in memory.  knots:
         None (uniform) or three entries, each None or n_d + p + 1 clamped knots
-        (u, v, w order)."""
+        (u, v, w order).  weights: None or positive weights shaped like ctrl
+        (a rational model)."""
         ctrl = np.ascontiguousarray(ctrl, dtype=np.float32)
         if ctrl.ndim != 3:
             raise ValueError("ctrl must be a 3-D array (n_w, n_v, n_u)")
@@ -278,6 +280,12 @@ class Context:
                 t = np.ascontiguousarray(t, dtype=np.float32).ravel()
                 keep.append(t)
                 d.knots[a] = t.ctypes.data
+        if weights is not None:
+            w = np.ascontiguousarray(weights, dtype=np.float32)
+            if w.shape != ctrl.shape:
+                raise ValueError("weights must have the shape of ctrl")
+            keep.append(w)
+            d.weights = w.ctypes.data
         mid = ctypes.c_int32(-1)
         self._check(self._L.mfadvr_load_model(self._h, ctypes.byref(d), ctypes.byref(mid)))
         return mid.value
