@@ -78,8 +78,12 @@ def lib():
         L.orc_basis_brute.restype = ctypes.c_double
         L.orc_basis_brute_der.argtypes = L.orc_basis_brute.argtypes
         L.orc_basis_brute_der.restype = ctypes.c_double
+        L.orc_basis_brute_dk.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         P(ctypes.c_double), ctypes.c_int]
+        L.orc_basis_brute_dk.restype = ctypes.c_double
         L.orc_eval_points.argtypes = [P(Model), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+        L.orc_eval_hessian.argtypes = [P(Model), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
         L.orc_render.argtypes = [P(Model), P(Camera), P(RenderParams), ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
@@ -162,6 +166,24 @@ def _model(ctrl: np.ndarray, degree, box_min=(0.0, 0.0, 0.0), box_max=(1.0, 1.0,
         keep.append(w)
         m.weights = w.ctypes.data
     return m, keep
+
+
+def eval_hessian(ctrl, degree, uvw, *, knot_vectors=None, weights=None):
+    """(f, f_u, f_v, f_w, f_uu, f_vv, f_ww, f_uv, f_uw, f_vw) in FP64 at FP32
+    points (small cases: the derivatives come from the raw recursion)."""
+    m, keep = _model(ctrl, degree, knot_vectors=knot_vectors, weights=weights)
+    uvw = np.ascontiguousarray(uvw, dtype=np.float32).reshape(-1, 3)
+    out = np.zeros((uvw.shape[0], 10), dtype=np.float64)
+    if lib().orc_eval_hessian(ctypes.byref(m), uvw.shape[0], uvw.ctypes.data, out.ctypes.data) != 0:
+        raise ValueError("oracle: invalid model")
+    del keep
+    return out
+
+
+def basis_dk(n: int, p: int, k: int, u: float, t=None):
+    """k-th derivatives of all n basis functions at u (raw recursion)."""
+    t = _knot_vector(n, p, t)
+    return np.array([lib().orc_basis_brute_dk(i, p, k, float(u), _dptr(t), n) for i in range(n)])
 
 
 def eval_points(ctrl, degree, uvw, *, brute=False, threads=None, with_spans=True, knot_vectors=None, weights=None):

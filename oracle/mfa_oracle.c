@@ -141,6 +141,22 @@ double orc_basis_brute_der(int i, int p, double u, const double *t, int n)
     return v;
 }
 
+/* k-th derivative of N_{i,p} at u by applying the derivative formula of the
+ * definition recursively: D^k N_{i,p} = p (D^{k-1} N_{i,p-1} / (t_{i+p} - t_i)
+ * - D^{k-1} N_{i+1,p-1} / (t_{i+p+1} - t_{i+1})), a term with a zero knot
+ * difference dropped; D^0 is the raw recursion above.  k > p gives 0. */
+double orc_basis_brute_dk(int i, int p, int k, double u, const double *t, int n)
+{
+    if (k == 0) return orc_basis_brute(i, p, u, t, n);
+    if (k > p) return 0.0;
+    double v = 0.0;
+    const double d1 = t[i + p] - t[i];
+    const double d2 = t[i + p + 1] - t[i + 1];
+    if (d1 > 0.0) v += (double)p / d1 * orc_basis_brute_dk(i, p - 1, k - 1, u, t, n);
+    if (d2 > 0.0) v -= (double)p / d2 * orc_basis_brute_dk(i + 1, p - 1, k - 1, u, t, n);
+    return v;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Model and point queries                                                   */
 /* ------------------------------------------------------------------------ */
@@ -334,6 +350,66 @@ int orc_eval_points(const orc_model *m, int64_t npts, const float *uvw, double *
     for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, eval_worker, &jobs[t]);
     eval_worker(&jobs[0]);
     for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+    ctx_free(&c);
+    return 0;
+}
+
+/* Value, gradient and second partial derivatives at npts points uvw (FP32
+ * triples clamped to [0,1]), the higher-order query of Sec. 3.1 (Sec. 2:
+ * derivatives up to the degree are analytic).  out10 per point: f, f_u,
+ * f_v, f_w, f_uu, f_vv, f_ww, f_uv, f_uw, f_vw.  The span comes from the
+ * binary search; the derivatives of order 0..2 of the span's p+1 non-zero
+ * functions from orc_basis_brute_dk.  A rational model differentiates
+ * f = A / W twice: f_i = (A_i - f W_i) / W and
+ * f_ij = (A_ij - f_i W_j - f_j W_i - f W_ij) / W.  Single-threaded (small
+ * cases).  Returns 0 or -1. */
+int orc_eval_hessian(const orc_model *m, int64_t npts, const float *uvw, double *out10)
+{
+    orc_ctx c;
+    if (ctx_init(&c, m)) { ctx_free(&c); return -1; }
+    /* (a, b) derivative orders per output: [out][axis] */
+    static const int ord[10][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
+                                   {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+    for (int64_t q = 0; q < npts; ++q) {
+        double x[3];
+        int s[3];
+        double D[3][3][ORC_MAX_DEGREE + 1]; /* [axis][order][r] */
+        for (int d = 0; d < 3; ++d) {
+            x[d] = clamp01((double)uvw[3 * q + d]);
+            s[d] = orc_find_span(m->n[d], m->p[d], c.t[d], x[d]);
+            for (int k = 0; k < 3; ++k)
+                for (int r = 0; r <= m->p[d]; ++r)
+                    D[d][k][r] = orc_basis_brute_dk(s[d] - m->p[d] + r, m->p[d], k, x[d], c.t[d], m->n[d]);
+        }
+        double h[10] = {0}, g[10] = {0};
+        for (int cc = 0; cc <= m->p[2]; ++cc)
+            for (int b = 0; b <= m->p[1]; ++b)
+                for (int a = 0; a <= m->p[0]; ++a) {
+                    const int i = s[0] - m->p[0] + a, j = s[1] - m->p[1] + b, k = s[2] - m->p[2] + cc;
+                    const double w = m->weights ? weight_at(m, i, j, k) : 1.0, wP = w * ctrl_at(m, i, j, k);
+                    for (int o = 0; o < 10; ++o) {
+                        const double B = D[0][ord[o][0]][a] * D[1][ord[o][1]][b] * D[2][ord[o][2]][cc];
+                        h[o] += B * wP;
+                        g[o] += B * w;
+                    }
+                }
+        double *out = out10 + 10 * q;
+        if (!m->weights) {
+            for (int o = 0; o < 10; ++o) out[o] = h[o];
+            continue;
+        }
+        const double W = g[0], f = h[0] / W;
+        double f1[3];
+        for (int d = 0; d < 3; ++d) f1[d] = (h[1 + d] - f * g[1 + d]) / W;
+        out[0] = f;
+        for (int d = 0; d < 3; ++d) out[1 + d] = f1[d];
+        /* second derivatives: outputs 4..9 with axis pairs (0,0) (1,1) (2,2) (0,1) (0,2) (1,2) */
+        static const int pr[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+        for (int o = 0; o < 6; ++o) {
+            const int di = pr[o][0], dj = pr[o][1];
+            out[4 + o] = (h[4 + o] - f1[di] * g[1 + dj] - f1[dj] * g[1 + di] - f * g[4 + o]) / W;
+        }
+    }
     ctx_free(&c);
     return 0;
 }
