@@ -175,14 +175,20 @@ MFADVR_API mfadvr_status mfadvr_eval_points_host(mfadvr_ctx *ctx, int32_t model_
 typedef enum {
     MFADVR_QUERY_VALUE = 1,    /* out: n FP32 f, 4-byte aligned */
     MFADVR_QUERY_GRADIENT = 2, /* out: n x 3 FP32 (df/du, df/dv, df/dw), 4-byte aligned */
-    MFADVR_QUERY_BOTH = 3      /* out: n x 4 FP32 (f, df/du, df/dv, df/dw), 16-byte aligned */
+    MFADVR_QUERY_BOTH = 3,     /* out: n x 4 FP32 (f, df/du, df/dv, df/dw), 16-byte aligned */
+    MFADVR_QUERY_HESSIAN = 4   /* out: n x 10 FP32 (f, f_u, f_v, f_w, f_uu, f_vv, f_ww, f_uv,
+                                  f_uw, f_vw), 4-byte aligned: the higher-order query of
+                                  Sec. 3.1 (curvature-based transfer functions), analytic
+                                  up to the degree (Sec. 2); 3(p+1)^3 + 6(p+1)^2 + 10(p+1)
+                                  multiply-adds per point */
 } mfadvr_query;
 
 /* mfadvr_eval_points for one mfadvr_query (an int32 here); with
  * MFADVR_QUERY_BOTH it is mfadvr_eval_points.  params_dev and spans_dev as
  * there; out_dev laid out as the query says.  Each output equals the same
- * component of MFADVR_QUERY_BOTH bit for bit.  EINVAL: an unknown query,
- * plus mfadvr_eval_points' cases. */
+ * component of MFADVR_QUERY_BOTH bit for bit (the Hessian query's first
+ * four outputs agree with it to rounding).  EINVAL: an unknown query, plus
+ * mfadvr_eval_points' cases. */
 MFADVR_API mfadvr_status mfadvr_query_points(mfadvr_ctx *ctx, int32_t model_id, const float *params_dev, int64_t n,
                                   int32_t query, float *out_dev, int32_t *spans_dev, void *stream);
 

@@ -72,6 +72,63 @@ __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const fl
             x2 = fmaf(w, mf2, -static_cast<float>(k2));
         }
         const int base = k0 + n0 * k1 + n01 * k2;
+        if constexpr (Q == kQueryHessian) {
+            // value, gradient and the six second partials (Sec. 3.1's
+            // higher-order query); order (a, b, c) scales by d0^a d1^b d2^c
+            float Bu[3][P + 1], Bv[3][P + 1], Bw[3][P + 1];
+            if constexpr (NU) {
+                basis_pieces_d2<P>(x0, mv.pieces[0], k0, Bu[0], Bu[1], Bu[2]);
+                basis_pieces_d2<P>(x1, mv.pieces[1], k1, Bv[0], Bv[1], Bv[2]);
+                basis_pieces_d2<P>(x2, mv.pieces[2], k2, Bw[0], Bw[1], Bw[2]);
+            } else {
+                basis_d2<P>(x0, k0, mv.m[0], Bu[0], Bu[1], Bu[2]);
+                basis_d2<P>(x1, k1, mv.m[1], Bv[0], Bv[1], Bv[2]);
+                basis_d2<P>(x2, k2, mv.m[2], Bw[0], Bw[1], Bw[2]);
+            }
+            float h[10];
+            contract_hessian<P>(Bu, Bv, Bw,
+                                [&](int k, int jp, int i) { return row_pair<T>(mv.rows, base, n0, n01, k, jp, i); }, h);
+            if constexpr (R) {
+                float g[10];
+                contract_hessian<P>(
+                    Bu, Bv, Bw, [&](int k, int jp, int i) { return row_pair<T>(mv.wrows, base, n0, n01, k, jp, i); },
+                    g);
+                // f = A / W, f_i = (A_i - f W_i) / W,
+                // f_ij = (A_ij - f_i W_j - f_j W_i - f W_ij) / W
+#pragma unroll
+                for (int o = 0; o < 10; ++o) {
+                    h[o] *= mv.scale;
+                    g[o] *= mv.wscale;
+                }
+                const float W = g[0], f = h[0] / W;
+                float f1[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) f1[d] = (h[1 + d] - f * g[1 + d]) / W;
+                constexpr int pi[6] = {0, 1, 2, 0, 0, 1}, pj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+                for (int o = 0; o < 6; ++o)
+                    h[4 + o] = (h[4 + o] - f1[pi[o]] * g[1 + pj[o]] - f1[pj[o]] * g[1 + pi[o]] - f * g[4 + o]) / W;
+                h[0] = f;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) h[1 + d] = f1[d];
+            }
+            const float dd[3] = {d0, d1, d2};
+#pragma unroll
+            for (int o = 0; o < 10; ++o) {
+                float sc = sv;
+#pragma unroll
+                for (int axis = 0; axis < 3; ++axis)
+#pragma unroll
+                    for (int e = 0; e < hessian_order(o, axis); ++e) sc *= dd[axis];
+                __stcs(out + 10 * idx + o, h[o] * sc);
+            }
+            if (spans) {
+                __stcs(spans + 3 * idx + 0, k0 + P);
+                __stcs(spans + 3 * idx + 1, k1 + P);
+                __stcs(spans + 3 * idx + 2, k2 + P);
+            }
+            continue;
+        }
         float r[4];
         float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
         auto basis3 = [&]() {
@@ -162,6 +219,7 @@ cudaError_t launch_eval_t(const ModelView &mv, const float *params, int64_t n, f
     case kQueryValue: return launch_eval_q<P, T, kQueryValue>(mv, params, n, out, spans, stream);
     case kQueryGradient: return launch_eval_q<P, T, kQueryGradient>(mv, params, n, out, spans, stream);
     case kQueryBoth: return launch_eval_q<P, T, kQueryBoth>(mv, params, n, out, spans, stream);
+    case kQueryHessian: return launch_eval_q<P, T, kQueryHessian>(mv, params, n, out, spans, stream);
     default: return cudaErrorInvalidValue;
     }
 }

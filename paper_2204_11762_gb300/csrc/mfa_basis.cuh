@@ -344,6 +344,73 @@ __device__ __forceinline__ void basis_pieces(float x, const float *__restrict__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Second derivatives (the Hessian query): basis values, first and second
+// derivatives with respect to the local coordinate, times BasisScale<P>.
+// ---------------------------------------------------------------------------
+
+// Horner's rule for a polynomial sum_e c(e) x^e and its first two derivatives.
+template <int P, typename Coef>
+__device__ __forceinline__ void horner_d2(float x, Coef c, float &v, float &d1, float &d2)
+{
+    v = c(P);
+    d1 = 0.0f;
+    d2 = 0.0f;
+#pragma unroll
+    for (int e = P - 1; e >= 0; --e) {
+        d2 = fmaf(d2, x, 2.0f * d1);
+        d1 = fmaf(d1, x, v);
+        v = fmaf(v, x, c(e));
+    }
+}
+
+// Uniform pieces: the cubic closed form differentiated once more
+// (6N0'' = 6s, 6N1'' = 18t - 12, 6N2'' = 18s - 12, 6N3'' = 6t), Horner on
+// the compile-time pieces for the other degrees.
+template <int P>
+__device__ __forceinline__ void basis_uniform_d2(float x, float N[P + 1], float dN[P + 1], float d2N[P + 1])
+{
+    if constexpr (P == 3) {
+        basis_uniform_scaled<3>(x, N, dN);
+        const float t = x, s = 1.0f - x;
+        d2N[0] = 6.0f * s;
+        d2N[1] = fmaf(18.0f, t, -12.0f);
+        d2N[2] = fmaf(18.0f, s, -12.0f);
+        d2N[3] = 6.0f * t;
+    } else {
+        constexpr UniformPieces<P> U = make_uniform_pieces<P>();
+#pragma unroll
+        for (int r = 0; r <= P; ++r) horner_d2<P>(x, [&](int e) { return U.c[r][e]; }, N[r], dN[r], d2N[r]);
+    }
+}
+
+// Any span of uniform knots: the closed form inside, the clamped-pattern
+// table near the ends.
+template <int P>
+__device__ __forceinline__ void basis_d2(float x, int k, int m, float N[P + 1], float dN[P + 1], float d2N[P + 1])
+{
+    if (span_interior<P>(k, m)) {
+        basis_uniform_d2<P>(x, N, dN, d2N);
+    } else {
+        const int a = max(0, P - 1 - k), b = max(0, k + P - m);
+        const float(&c)[P + 1][P + 1] = span_pieces<P>().c[a * P + b];
+#pragma unroll
+        for (int r = 0; r <= P; ++r) horner_d2<P>(x, [&](int e) { return c[r][e]; }, N[r], dN[r], d2N[r]);
+    }
+}
+
+// General knots: from the span's pieces.
+template <int P>
+__device__ __forceinline__ void basis_pieces_d2(float x, const float *__restrict__ pieces, int k, float N[P + 1],
+                                                float dN[P + 1], float d2N[P + 1])
+{
+    constexpr int S = GeneralPieces<P>::kStride;
+    const float *src = pieces + static_cast<int64_t>(k) * S;
+#pragma unroll
+    for (int r = 0; r <= P; ++r)
+        horner_d2<P>(x, [&](int e) { return __ldg(src + r * (P + 1) + e); }, N[r], dN[r], d2N[r]);
+}
+
 // Exact k = floor(u*m) for FP32 u in [0, 1], clamped to [0, m-1].  The FP32
 // product may round across an integer; a fused multiply-add gives the sign
 // of the exact residual u*m - k (one rounding never changes a sign), which
@@ -420,6 +487,8 @@ struct Block {
 
 // What a query computes: bit 0 the value f, bit 1 the gradient (mfadvr_query).
 constexpr int kQueryValue = 1, kQueryGradient = 2, kQueryBoth = 3;
+// The Hessian query: value, gradient and the six second partial derivatives.
+constexpr int kQueryHessian = 4;
 
 // Multiply-adds of contract<P, Q>: value only (p+1)^3 + (p+1)^2 + (p+1);
 // gradient only 2(p+1)^3 + 3(p+1)^2 + 3(p+1); both 2(p+1)^3 + 3(p+1)^2 + 4(p+1).
@@ -487,6 +556,62 @@ __device__ __forceinline__ void contract(const float Nu[P + 1], const float dNu[
         r[2] = fv;
         r[3] = fw;
     }
+}
+
+// Derivative orders (u, v, w) of the ten outputs of the Hessian query:
+// f, f_u, f_v, f_w, f_uu, f_vv, f_ww, f_uv, f_uw, f_vw.
+__device__ __forceinline__ constexpr int hessian_order(int o, int axis)
+{
+    constexpr int ord[10][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
+                                {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+    return ord[o][axis];
+}
+
+// Sum-factorised contraction for the Hessian query: the u sums for orders
+// 0..2 on packed FMAs, the v sums for the six order pairs of total <= 2, the
+// w sums for the ten outputs.  N*[order][r]; r[o] in span-local units times
+// the product of the basis scales.  Multiply-adds: 3(P+1)^3 + 6(P+1)^2 +
+// 10(P+1) (u sums over padded j pairs when P is even).
+template <int P, typename PairAt>
+__device__ __forceinline__ void contract_hessian(const float (&Nu)[3][P + 1], const float (&Nv)[3][P + 1],
+                                                 const float (&Nw)[3][P + 1], PairAt pair, float r[10])
+{
+    constexpr int JP = Block<P>::JP;
+    float acc[10];
+#pragma unroll
+    for (int o = 0; o < 10; ++o) acc[o] = 0.0f;
+#pragma unroll
+    for (int k = 0; k <= P; ++k) {
+        float c[3][3];  // c[ou][ov], ou + ov <= 2
+#pragma unroll
+        for (int ou = 0; ou < 3; ++ou)
+#pragma unroll
+            for (int ov = 0; ov < 3; ++ov) c[ou][ov] = 0.0f;
+#pragma unroll
+        for (int jp = 0; jp < JP; ++jp) {
+            float2 a[3];
+#pragma unroll
+            for (int ou = 0; ou < 3; ++ou) a[ou] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i <= P; ++i) {
+                const float2 pv = pair(k, jp, i);
+#pragma unroll
+                for (int ou = 0; ou < 3; ++ou) a[ou] = __ffma2_rn(make_float2(Nu[ou][i], Nu[ou][i]), pv, a[ou]);
+            }
+#pragma unroll
+            for (int ou = 0; ou < 3; ++ou)
+#pragma unroll
+                for (int ov = 0; ov + ou < 3; ++ov) {
+                    c[ou][ov] = fmaf(Nv[ov][2 * jp], a[ou].x, c[ou][ov]);
+                    if (2 * jp + 1 <= P) c[ou][ov] = fmaf(Nv[ov][2 * jp + 1], a[ou].y, c[ou][ov]);
+                }
+        }
+#pragma unroll
+        for (int o = 0; o < 10; ++o)
+            acc[o] = fmaf(Nw[hessian_order(o, 2)][k], c[hessian_order(o, 0)][hessian_order(o, 1)], acc[o]);
+    }
+#pragma unroll
+    for (int o = 0; o < 10; ++o) r[o] = acc[o];
 }
 
 // Loads the row entries of the span block whose first control point is

@@ -466,6 +466,7 @@ size_t query_out_bytes(int32_t query)
     case MFADVR_QUERY_VALUE: return 4;
     case MFADVR_QUERY_GRADIENT: return 12;
     case MFADVR_QUERY_BOTH: return 16;
+    case MFADVR_QUERY_HESSIAN: return 40;
     default: return 0;
     }
 }
@@ -476,7 +477,7 @@ mfadvr_status query_device(mfadvr_ctx *ctx, int32_t model_id, const float *param
     if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
     Model *m = nullptr;
     if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
-    if (query_out_bytes(query) == 0) return fail(ctx, MFADVR_EINVAL, "query must be 1 (value), 2 (gradient) or 3");
+    if (query_out_bytes(query) == 0) return fail(ctx, MFADVR_EINVAL, "query must be 1 (value), 2 (gradient), 3 or 4");
     if (n < 0) return fail(ctx, MFADVR_EINVAL, "n must be >= 0");
     if (n == 0) return MFADVR_OK;
     if (!params_dev || !out_dev) return fail(ctx, MFADVR_EINVAL, "params and out must not be NULL");
@@ -502,7 +503,7 @@ mfadvr_status query_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_
     Model *m = nullptr;
     if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
     const size_t per = query_out_bytes(query);
-    if (per == 0) return fail(ctx, MFADVR_EINVAL, "query must be 1 (value), 2 (gradient) or 3");
+    if (per == 0) return fail(ctx, MFADVR_EINVAL, "query must be 1 (value), 2 (gradient), 3 or 4");
     if (n < 0) return fail(ctx, MFADVR_EINVAL, "n must be >= 0");
     if (n == 0) return MFADVR_OK;
     if (!params_host || !out_host) return fail(ctx, MFADVR_EINVAL, "params and out must not be NULL");

@@ -19,7 +19,7 @@ import numpy as np
 from . import build as _build
 
 F32, F16, BF16 = 0, 1, 2
-QUERY_VALUE, QUERY_GRADIENT, QUERY_BOTH = 1, 2, 3
+QUERY_VALUE, QUERY_GRADIENT, QUERY_BOTH, QUERY_HESSIAN = 1, 2, 3, 4
 _DTYPES = {"f32": F32, "float32": F32, "f16": F16, "float16": F16, "bf16": BF16, "bfloat16": BF16}
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTFOUND, ETIMEOUT, EBUSY, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
@@ -316,7 +316,8 @@ class Context:
 
     def query_points(self, model_id, params_dev, n, out_dev, query=QUERY_BOTH, spans_dev=None, stream=None):
         """eval_points for one query: out_dev holds n values (QUERY_VALUE), n x 3
-        gradients (QUERY_GRADIENT) or n x 4 (QUERY_BOTH)."""
+        gradients (QUERY_GRADIENT), n x 4 (QUERY_BOTH) or n x 10 (QUERY_HESSIAN:
+        f, f_u, f_v, f_w, f_uu, f_vv, f_ww, f_uv, f_uw, f_vw)."""
         self._check(self._L.mfadvr_query_points(self._h, int(model_id), _ptr(params_dev), int(n), int(query),
                                                 _ptr(out_dev), _ptr(spans_dev), _stream(stream)))
 
@@ -324,7 +325,7 @@ class Context:
         params = np.ascontiguousarray(params, dtype=np.float32).reshape(-1, 3)
         n = params.shape[0]
         if out is None:
-            shape = {QUERY_VALUE: (n,), QUERY_GRADIENT: (n, 3)}.get(int(query), (n, 4))
+            shape = {QUERY_VALUE: (n,), QUERY_GRADIENT: (n, 3), QUERY_HESSIAN: (n, 10)}.get(int(query), (n, 4))
             out = np.empty(shape, dtype=np.float32)
         self._check(self._L.mfadvr_query_points_host(self._h, int(model_id), _ptr(params), n, int(query),
                                                      _ptr(out), _ptr(spans), _stream(stream)))

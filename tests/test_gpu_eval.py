@@ -208,7 +208,7 @@ def test_query_rejects_bad_query(ctx, torch_cuda):
     mid = ctx.load_model(np.ones((6, 6, 6), dtype=np.float32), 2)
     d_pts = torch.zeros((4, 3), device=dev)
     d_out = torch.zeros((4, 4), device=dev)
-    for q in (0, 4, -1):
+    for q in (0, 5, -1):
         with pytest.raises(mfadvr.MfadvrError) as e:
             ctx.query_points(mid, d_pts, 4, d_out, q)
         assert e.value.status == mfadvr.EINVAL
