@@ -117,6 +117,22 @@ __device__ __forceinline__ void basis_uniform_scaled(float x, float N[P + 1], fl
     }
 }
 
+// The cubic closed form (times 6) on a pair of local coordinates, two axes
+// per packed instruction.
+__device__ __forceinline__ void basis_cubic_pair(float2 x, float2 N[4], float2 dN[4])
+{
+    const float2 t = x, s = __fadd2_rn(make_float2(1.f, 1.f), make_float2(-x.x, -x.y));
+    const float2 t2 = __fmul2_rn(t, t), s2 = __fmul2_rn(s, s);
+    N[0] = __fmul2_rn(s2, s);
+    N[1] = __ffma2_rn(t2, __ffma2_rn(make_float2(3.f, 3.f), t, make_float2(-6.f, -6.f)), make_float2(4.f, 4.f));
+    N[2] = __ffma2_rn(s2, __ffma2_rn(make_float2(3.f, 3.f), s, make_float2(-6.f, -6.f)), make_float2(4.f, 4.f));
+    N[3] = __fmul2_rn(t2, t);
+    dN[0] = __fmul2_rn(make_float2(-3.f, -3.f), s2);
+    dN[1] = __fmul2_rn(t, __ffma2_rn(make_float2(9.f, 9.f), t, make_float2(-12.f, -12.f)));
+    dN[2] = __fmul2_rn(make_float2(-s.x, -s.y), __ffma2_rn(make_float2(9.f, 9.f), s, make_float2(-12.f, -12.f)));
+    dN[3] = __fmul2_rn(make_float2(3.f, 3.f), t2);
+}
+
 // ---------------------------------------------------------------------------
 // Pieces on every span.  The span-local knots kappa(j), j = 1-P..P, depend on
 // the span only through how close it is to the two clamped ends:

@@ -270,10 +270,23 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
         basis_pieces<P>(x[1], mv.pieces[1], ray.kk[1], Nv, dNv);
         basis_pieces<P>(x[2], mv.pieces[2], ray.kk[2], Nw, dNw);
     } else {
-        // uniform pieces, replaced from the piece table on clamped spans
+        // uniform pieces, replaced from the piece table on clamped spans;
+        // the cubic's v and w bases share packed instructions
         basis_uniform_scaled<P>(x[0], Nu, dNu);
-        basis_uniform_scaled<P>(x[1], Nv, dNv);
-        basis_uniform_scaled<P>(x[2], Nw, dNw);
+        if constexpr (P == 3) {
+            float2 Nvw[4], dNvw[4];
+            basis_cubic_pair(make_float2(x[1], x[2]), Nvw, dNvw);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                Nv[r] = Nvw[r].x;
+                dNv[r] = dNvw[r].x;
+                Nw[r] = Nvw[r].y;
+                dNw[r] = dNvw[r].y;
+            }
+        } else {
+            basis_uniform_scaled<P>(x[1], Nv, dNv);
+            basis_uniform_scaled<P>(x[2], Nw, dNw);
+        }
         if (!ray.interior) {
             if (!span_interior<P>(ray.kk[0], mv.m[0])) basis_table<P>(x[0], ray.kk[0], mv.m[0], Nu, dNu);
             if (!span_interior<P>(ray.kk[1], mv.m[1])) basis_table<P>(x[1], ray.kk[1], mv.m[1], Nv, dNv);
