@@ -494,6 +494,27 @@ struct RowLoad<__nv_bfloat16> {
     }
 };
 
+// A row entry of a 16-bit row array as stored: four (j, j+1) pairs, one
+// 32-bit word each (FP16 or BF16 halves), for caches that convert at use.
+__device__ __forceinline__ uint4 row_raw16(const void *rows, int idx)
+{
+    return __ldg(static_cast<const uint4 *>(rows) + idx);
+}
+
+// The FP32 pair of a stored 16-bit pair.
+template <typename T>
+__device__ __forceinline__ float2 pair16_to_float2(unsigned w);
+template <>
+__device__ __forceinline__ float2 pair16_to_float2<__half>(unsigned w)
+{
+    return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+}
+template <>
+__device__ __forceinline__ float2 pair16_to_float2<__nv_bfloat16>(unsigned w)
+{
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
+}
+
 // Pairs per j-column and row entries per i-run of a span block.
 template <int P>
 struct Block {

@@ -74,10 +74,34 @@ struct LaneRay {
     float r[4];                  // query of sample sf - 1, not yet composited
 };
 
-template <int P, bool R>
+// Cached span block: FP32 pairs for FP32 storage; for 16-bit storage the
+// stored pairs themselves (one 32-bit register each, half the registers),
+// converted to FP32 as the contraction uses them.
+template <typename T>
+struct CacheElem {
+    using type = float2;
+    static constexpr bool kPacked = false;
+};
+template <>
+struct CacheElem<__half> {
+    using type = unsigned;
+    static constexpr bool kPacked = true;
+};
+template <>
+struct CacheElem<__nv_bfloat16> {
+    using type = unsigned;
+    static constexpr bool kPacked = true;
+};
+
+template <int P, typename T, bool R>
 struct SpanCache {
     static constexpr bool kOn = CacheCP<P, R>::value;
-    float2 v[kOn ? (P + 1) : 1][kOn ? Block<P>::JP : 1][kOn ? (P + 1) : 1];
+    typename CacheElem<T>::type v[kOn ? (P + 1) : 1][kOn ? Block<P>::JP : 1][kOn ? (P + 1) : 1];
+    __device__ __forceinline__ float2 pair(int k, int jp, int i) const
+    {
+        if constexpr (CacheElem<T>::kPacked) return pair16_to_float2<T>(v[k][jp][i]);
+        else return v[k][jp][i];
+    }
 };
 
 // Pixel of ray slot `slot` (tile = slot / 32, lane-in-tile = slot % 32) for
@@ -203,10 +227,10 @@ __device__ __forceinline__ float lg2_approx(float x)
 // (pixel written).
 template <int P, typename T, bool G, bool NU, bool R, typename Tf>
 __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSetup &rs, const Tf &tf, LaneRay &ray,
-                                            SpanCache<P, R> &cache)
+                                            SpanCache<P, T, R> &cache)
 {
     constexpr int JP = Block<P>::JP;
-    constexpr bool kCache = SpanCache<P, R>::kOn;
+    constexpr bool kCache = SpanCache<P, T, R>::kOn;
     const float s = ray.sf;
 
     // ---- span of sample s; positions are clamped to the lattice only when
@@ -251,14 +275,29 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
         ray.interior = span_interior<P>(ray.kk[0], mv.m[0]) && span_interior<P>(ray.kk[1], mv.m[1]) &&
                        span_interior<P>(ray.kk[2], mv.m[2]);
         if constexpr (kCache) {
-            Row q[P + 1][JP][Block<P>::IR];
-            load_block<P, T>(mv.rows, ray.base, mv.n[0], mv.n01, q);
+            if constexpr (CacheElem<T>::kPacked) {
 #pragma unroll
-            for (int k = 0; k <= P; ++k)
+                for (int k = 0; k <= P; ++k)
 #pragma unroll
-                for (int jp = 0; jp < JP; ++jp)
+                    for (int jp = 0; jp < JP; ++jp)
 #pragma unroll
-                    for (int i = 0; i <= P; ++i) cache.v[k][jp][i] = block_pair<P>(q, k, jp, i);
+                        for (int ir = 0; ir < Block<P>::IR; ++ir) {
+                            const uint4 w = row_raw16(mv.rows, ray.base + 4 * ir + 2 * jp * mv.n[0] + k * mv.n01);
+                            const unsigned ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                            for (int d = 0; d < 4; ++d)
+                                if (4 * ir + d <= P) cache.v[k][jp][4 * ir + d] = ws[d];
+                        }
+            } else {
+                Row q[P + 1][JP][Block<P>::IR];
+                load_block<P, T>(mv.rows, ray.base, mv.n[0], mv.n01, q);
+#pragma unroll
+                for (int k = 0; k <= P; ++k)
+#pragma unroll
+                    for (int jp = 0; jp < JP; ++jp)
+#pragma unroll
+                        for (int i = 0; i <= P; ++i) cache.v[k][jp][i] = block_pair<P>(q, k, jp, i);
+            }
         }
     }
     float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
@@ -336,7 +375,7 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
     // ---- query of sample s (composited by the next iteration) -------------
     constexpr int Q = G ? kQueryBoth : kQueryValue;
     if constexpr (kCache) {
-        contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return cache.v[k][jp][i]; }, ray.r);
+        contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return cache.pair(k, jp, i); }, ray.r);
     } else {
         const int n0 = mv.n[0], n01 = mv.n01, base = ray.base;
         contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw,
@@ -401,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P, NU, R>::value)
     bool exhausted = false;
     bool idle = true;
     LaneRay ray;
-    SpanCache<P, R> cache;
+    SpanCache<P, T, R> cache;
 
     for (;;) {
         // ---- hand rays to idle lanes ----------------------------------------
@@ -447,7 +486,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P, NU, R>::value)
     bool exhausted = false;
     bool idle = true;
     LaneRay ray;
-    SpanCache<P, R> cache;
+    SpanCache<P, T, R> cache;
 
     for (;;) {
         const unsigned need = __ballot_sync(kFull, idle);
