@@ -20,33 +20,40 @@ __device__ __forceinline__ unsigned pack2(float a, float b, __nv_bfloat16)
     return *reinterpret_cast<const unsigned *>(&h);
 }
 
-// One thread per lattice point (i, j, k): gathers P(i..i+3, j..j+1, k) as
-// (j, j+1) pairs, zero past the lattice, scales by inv_scale, rounds to the
-// storage type.
+// One thread per lattice point (i, j, k): gathers P(i..i+3, j..j+1, k)
+// (FP32) or P(i..i+3, j..j+3, k) (FP16/BF16) as (j, j+1) pairs in the entry
+// order of mfa_basis.cuh, zero past the lattice, scaled by inv_scale and
+// rounded to the storage type.
 template <typename T>
 __global__ void build_rows_kernel(const float *__restrict__ src, void *__restrict__ dst, int n0, int n1, int n2,
                                   float inv_scale)
 {
+    constexpr int H = sizeof(T) == 4 ? 1 : 2;  // j pairs per entry
     const int64_t total = static_cast<int64_t>(n0) * n1 * n2;
     for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
          e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int i = static_cast<int>(e % n0);
         const int j = static_cast<int>((e / n0) % n1);
-        const bool rj = j + 1 < n1;
-        float v[8];
+        float v[H][4][2];  // [h][d][j + 2h + c]
 #pragma unroll
-        for (int d = 0; d < 4; ++d) {
-            const bool ri = i + d < n0;
-            v[2 * d] = ri ? src[e + d] * inv_scale : 0.0f;
-            v[2 * d + 1] = (ri && rj) ? src[e + d + n0] * inv_scale : 0.0f;
-        }
+        for (int h = 0; h < H; ++h)
+#pragma unroll
+            for (int d = 0; d < 4; ++d)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const bool in = i + d < n0 && j + 2 * h + c < n1;
+                    v[h][d][c] = in ? src[e + d + static_cast<int64_t>(2 * h + c) * n0] * inv_scale : 0.0f;
+                }
         if constexpr (sizeof(T) == 4) {
             float4 *q = static_cast<float4 *>(dst) + 2 * e;
-            q[0] = make_float4(v[0], v[1], v[2], v[3]);
-            q[1] = make_float4(v[4], v[5], v[6], v[7]);
+            q[0] = make_float4(v[0][0][0], v[0][0][1], v[0][1][0], v[0][1][1]);
+            q[1] = make_float4(v[0][2][0], v[0][2][1], v[0][3][0], v[0][3][1]);
         } else {
-            static_cast<uint4 *>(dst)[e] =
-                make_uint4(pack2(v[0], v[1], T()), pack2(v[2], v[3], T()), pack2(v[4], v[5], T()), pack2(v[6], v[7], T()));
+            uint4 *q = static_cast<uint4 *>(dst) + 2 * e;
+            q[0] = make_uint4(pack2(v[0][0][0], v[0][0][1], T()), pack2(v[0][1][0], v[0][1][1], T()),
+                              pack2(v[0][2][0], v[0][2][1], T()), pack2(v[0][3][0], v[0][3][1], T()));
+            q[1] = make_uint4(pack2(v[H - 1][0][0], v[H - 1][0][1], T()), pack2(v[H - 1][1][0], v[H - 1][1][1], T()),
+                              pack2(v[H - 1][2][0], v[H - 1][2][1], T()), pack2(v[H - 1][3][0], v[H - 1][3][1], T()));
         }
     }
 }

@@ -144,11 +144,11 @@ __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const fl
         };
         if constexpr (P <= 3 && !R) {
             // the whole block in flight before the basis is evaluated
-            Row q[P + 1][Block<P>::JP][Block<P>::IR];
+            typename Entries<P, T>::E q[P + 1][Entries<P, T>::JE][Block<P>::IR];
             load_block<P, T>(mv.rows, base, n0, n01, q);
             basis3();
-            contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return block_pair<P>(q, k, jp, i); },
-                           r);
+            contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw,
+                           [&](int k, int jp, int i) { return block_pair<P, T>(q, k, jp, i); }, r);
         } else {
             basis3();
             contract<P, QA>(Nu, dNu, Nv, dNv, Nw, dNw,

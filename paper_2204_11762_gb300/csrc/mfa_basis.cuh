@@ -10,6 +10,8 @@
 // point touched by the span is index k.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -440,65 +442,44 @@ __device__ __forceinline__ int span_exact(float u, int m, float mf)
 }
 
 // ---------------------------------------------------------------------------
-// Row layout of the control points.  Entry (i, j, k) of the row array holds
-// the 4 x 2 points P(i+d, j+e, k), d = 0..3, e = 0..1, as the four pairs
-//   (P(i+d, j, k), P(i+d, j+1, k)),   d = 0..3
-// (zero where i+d or j+1 runs past the lattice).  A (p+1) x (p+1) k-slice of
-// the block under a span is then ceil((p+1)/2) x ceil((p+1)/4) entries, and
-// every entry yields pairs ready for packed FMAs.  FP32 entries are 32 bytes
-// (one 256-bit load, one L2 sector); FP16/BF16 entries 16 bytes.
+// Row layout of the control points.  Every entry is 32 bytes (one L2 sector,
+// one 256-bit load) and holds the pairs (P(i+d, j+2h, k), P(i+d, j+2h+1, k)),
+// zero where i+d or j+2h+1 runs past the lattice:
+//  - FP32: entry (i, j, k) holds d = 0..3, h = 0 (4 x 2 points);
+//  - FP16/BF16: entry (i, j, k) holds d = 0..3, h = 0..1 (4 x 4 points),
+//    word (d + 4h) the 16-bit pair.
+// A k-slice of the block under a span is ceil((p+1)/4) entries along i by
+// ceil((p+1)/2) (FP32) or ceil((p+1)/4) (16-bit) along j, and every entry
+// yields pairs ready for packed FMAs: 8 loads per degree-3 block in FP32, 4
+// in 16 bits.
 // ---------------------------------------------------------------------------
 struct Row {
     float2 p[4];
 };
-
-template <typename T>
-struct RowLoad;
-template <>
-struct RowLoad<float> {
-    static __device__ __forceinline__ Row at(const void *rows, int idx)
-    {
-        const float *a = static_cast<const float *>(rows) + 8 * static_cast<int64_t>(idx);
-        Row r;
-        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-            : "=f"(r.p[0].x), "=f"(r.p[0].y), "=f"(r.p[1].x), "=f"(r.p[1].y), "=f"(r.p[2].x), "=f"(r.p[2].y),
-              "=f"(r.p[3].x), "=f"(r.p[3].y)
-            : "l"(a));
-        return r;
-    }
-};
-template <>
-struct RowLoad<__half> {
-    static __device__ __forceinline__ Row at(const void *rows, int idx)
-    {
-        const uint4 raw = __ldg(static_cast<const uint4 *>(rows) + idx);
-        Row r;
-        r.p[0] = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
-        r.p[1] = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
-        r.p[2] = __half22float2(*reinterpret_cast<const __half2 *>(&raw.z));
-        r.p[3] = __half22float2(*reinterpret_cast<const __half2 *>(&raw.w));
-        return r;
-    }
-};
-template <>
-struct RowLoad<__nv_bfloat16> {
-    static __device__ __forceinline__ Row at(const void *rows, int idx)
-    {
-        const uint4 raw = __ldg(static_cast<const uint4 *>(rows) + idx);
-        Row r;
-        r.p[0] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.x));
-        r.p[1] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.y));
-        r.p[2] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.z));
-        r.p[3] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.w));
-        return r;
-    }
+struct Row16 {
+    unsigned w[8];
 };
 
-// A row entry of a 16-bit row array as stored: four (j, j+1) pairs, one
-// 32-bit word each (FP16 or BF16 halves), for caches that convert at use.
-__device__ __forceinline__ uint4 row_raw16(const void *rows, int idx)
+__device__ __forceinline__ Row row32_at(const void *rows, int idx)
 {
-    return __ldg(static_cast<const uint4 *>(rows) + idx);
+    const float *a = static_cast<const float *>(rows) + 8 * static_cast<int64_t>(idx);
+    Row r;
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(r.p[0].x), "=f"(r.p[0].y), "=f"(r.p[1].x), "=f"(r.p[1].y), "=f"(r.p[2].x), "=f"(r.p[2].y),
+          "=f"(r.p[3].x), "=f"(r.p[3].y)
+        : "l"(a));
+    return r;
+}
+
+__device__ __forceinline__ Row16 row16_at(const void *rows, int idx)
+{
+    const unsigned *a = static_cast<const unsigned *>(rows) + 8 * static_cast<int64_t>(idx);
+    Row16 r;
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r.w[0]), "=r"(r.w[1]), "=r"(r.w[2]), "=r"(r.w[3]), "=r"(r.w[4]), "=r"(r.w[5]), "=r"(r.w[6]),
+          "=r"(r.w[7])
+        : "l"(a));
+    return r;
 }
 
 // The FP32 pair of a stored 16-bit pair.
@@ -521,6 +502,23 @@ struct Block {
     static constexpr int JP = (P + 2) / 2;  // j pairs (the last one padded when P is even)
     static constexpr int IR = (P + 4) / 4;  // row entries along i
 };
+
+// Entry geometry of the storage type: j pairs per entry and entries along j.
+template <int P, typename T>
+struct Entries {
+    static constexpr bool k16 = sizeof(T) == 2;
+    static constexpr int JPE = k16 ? 2 : 1;                          // j pairs per entry
+    static constexpr int JE = (Block<P>::JP + JPE - 1) / JPE;        // entries along j
+    using E = typename std::conditional<k16, Row16, Row>::type;
+};
+
+// Index of the entry holding pair (k, jp, i) of the block at entry `base`,
+// and the pair's place in it.
+template <typename T>
+__device__ __forceinline__ int entry_of(int base, int n0, int n01, int k, int jp, int i)
+{
+    return sizeof(T) == 2 ? base + (i & ~3) + 4 * (jp >> 1) * n0 + k * n01 : base + (i & ~3) + 2 * jp * n0 + k * n01;
+}
 
 // What a query computes: bit 0 the value f, bit 1 the gradient (mfadvr_query).
 constexpr int kQueryValue = 1, kQueryGradient = 2, kQueryBoth = 3;
@@ -651,33 +649,48 @@ __device__ __forceinline__ void contract_hessian(const float (&Nu)[3][P + 1], co
     for (int o = 0; o < 10; ++o) r[o] = acc[o];
 }
 
-// Loads the row entries of the span block whose first control point is
-// entry index `base` (= i0 + n0*(j0 + n1*k0)) into q[k][jp][ir].
+// Loads the entries of the span block whose first control point is entry
+// index `base` (= i0 + n0*(j0 + n1*k0)) into q[k][je][ir].
 template <int P, typename T>
 __device__ __forceinline__ void load_block(const void *rows, int base, int n0, int n01,
-                                           Row (&q)[P + 1][Block<P>::JP][Block<P>::IR])
+                                           typename Entries<P, T>::E (&q)[P + 1][Entries<P, T>::JE][Block<P>::IR])
 {
 #pragma unroll
     for (int k = 0; k <= P; ++k)
 #pragma unroll
-        for (int jp = 0; jp < Block<P>::JP; ++jp)
+        for (int je = 0; je < Entries<P, T>::JE; ++je)
 #pragma unroll
-            for (int ir = 0; ir < Block<P>::IR; ++ir)
-                q[k][jp][ir] = RowLoad<T>::at(rows, base + 4 * ir + 2 * jp * n0 + k * n01);
+            for (int ir = 0; ir < Block<P>::IR; ++ir) {
+                const int idx = base + 4 * ir + 2 * Entries<P, T>::JPE * je * n0 + k * n01;
+                if constexpr (Entries<P, T>::k16) q[k][je][ir] = row16_at(rows, idx);
+                else q[k][je][ir] = row32_at(rows, idx);
+            }
 }
 
-// Pair (P(i0+i, j0+2jp, k0+k), P(i0+i, j0+2jp+1, k0+k)) of a loaded block.
-template <int P>
-__device__ __forceinline__ float2 block_pair(const Row (&q)[P + 1][Block<P>::JP][Block<P>::IR], int k, int jp, int i)
+// The stored word of pair (k, jp, i) in a loaded 16-bit block.
+template <int P, typename T>
+__device__ __forceinline__ unsigned block_word(const Row16 (&q)[P + 1][Entries<P, T>::JE][Block<P>::IR], int k,
+                                               int jp, int i)
 {
-    return q[k][jp][i >> 2].p[i & 3];
+    return q[k][jp >> 1][i >> 2].w[(i & 3) + 4 * (jp & 1)];
+}
+
+// Pair (P(i0+i, j0+2jp, k0+k), P(i0+i, j0+2jp+1, k0+k)) of a loaded block, in FP32.
+template <int P, typename T>
+__device__ __forceinline__ float2 block_pair(
+    const typename Entries<P, T>::E (&q)[P + 1][Entries<P, T>::JE][Block<P>::IR], int k, int jp, int i)
+{
+    if constexpr (Entries<P, T>::k16) return pair16_to_float2<T>(block_word<P, T>(q, k, jp, i));
+    else return q[k][jp][i >> 2].p[i & 3];
 }
 
 // The same pair read from the row array directly (no block in registers).
 template <typename T>
 __device__ __forceinline__ float2 row_pair(const void *rows, int base, int n0, int n01, int k, int jp, int i)
 {
-    return RowLoad<T>::at(rows, base + (i & ~3) + 2 * jp * n0 + k * n01).p[i & 3];
+    const int idx = entry_of<T>(base, n0, n01, k, jp, i);
+    if constexpr (sizeof(T) == 2) return pair16_to_float2<T>(row16_at(rows, idx).w[(i & 3) + 4 * (jp & 1)]);
+    else return row32_at(rows, idx).p[i & 3];
 }
 
 }  // namespace mfadvr

@@ -14,7 +14,8 @@ constexpr float basis_scale_host(int p) { return p == 3 ? 6.0f : 1.0f; }
 
 // A resident model as the kernels see it.  The control points live in the
 // row layout (see mfa_basis.cuh): entry (i, j, k) at i + n[0]*(j + n[1]*k)
-// holds the pairs (P(i+d,j,k), P(i+d,j+1,k)), d = 0..3, in the storage type.
+// holds the pairs (P(i+d,j+2h,k), P(i+d,j+2h+1,k)), d = 0..3, h = 0 (FP32) or
+// h = 0..1 (FP16/BF16), in the storage type.
 struct ModelView {
     const void *rows;
     int n[3];       // control points per axis
@@ -91,8 +92,8 @@ cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, int *count
 // zeroed on `stream` first.
 cudaError_t launch_render_batch(int p, int dtype, int grad, int nu, int rat, const RenderJob *jobs_dev, int njobs,
                                 int total_tiles, int ctas_per_sm, int *counter, cudaStream_t stream);
-// Bytes of one row-layout entry (8 control points) in a storage type.
-constexpr size_t row_entry_bytes(int dtype) { return dtype == MFADVR_F32 ? 32 : 16; }
+// Bytes of one row-layout entry (4 x 2 FP32 or 4 x 4 16-bit control points).
+constexpr size_t row_entry_bytes(int) { return 32; }
 // Builds the row array of an n0 x n1 x n2 FP32 lattice (device memory),
 // scaling by inv_scale and rounding to the storage type.
 cudaError_t launch_build_rows(const float *src, void *rows, int n0, int n1, int n2, int dtype, float inv_scale,

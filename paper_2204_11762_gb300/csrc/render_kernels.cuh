@@ -275,29 +275,17 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
         ray.interior = span_interior<P>(ray.kk[0], mv.m[0]) && span_interior<P>(ray.kk[1], mv.m[1]) &&
                        span_interior<P>(ray.kk[2], mv.m[2]);
         if constexpr (kCache) {
-            if constexpr (CacheElem<T>::kPacked) {
+            typename Entries<P, T>::E q[P + 1][Entries<P, T>::JE][Block<P>::IR];
+            load_block<P, T>(mv.rows, ray.base, mv.n[0], mv.n01, q);
 #pragma unroll
-                for (int k = 0; k <= P; ++k)
+            for (int k = 0; k <= P; ++k)
 #pragma unroll
-                    for (int jp = 0; jp < JP; ++jp)
+                for (int jp = 0; jp < JP; ++jp)
 #pragma unroll
-                        for (int ir = 0; ir < Block<P>::IR; ++ir) {
-                            const uint4 w = row_raw16(mv.rows, ray.base + 4 * ir + 2 * jp * mv.n[0] + k * mv.n01);
-                            const unsigned ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                            for (int d = 0; d < 4; ++d)
-                                if (4 * ir + d <= P) cache.v[k][jp][4 * ir + d] = ws[d];
-                        }
-            } else {
-                Row q[P + 1][JP][Block<P>::IR];
-                load_block<P, T>(mv.rows, ray.base, mv.n[0], mv.n01, q);
-#pragma unroll
-                for (int k = 0; k <= P; ++k)
-#pragma unroll
-                    for (int jp = 0; jp < JP; ++jp)
-#pragma unroll
-                        for (int i = 0; i <= P; ++i) cache.v[k][jp][i] = block_pair<P>(q, k, jp, i);
-            }
+                    for (int i = 0; i <= P; ++i) {
+                        if constexpr (CacheElem<T>::kPacked) cache.v[k][jp][i] = block_word<P, T>(q, k, jp, i);
+                        else cache.v[k][jp][i] = block_pair<P, T>(q, k, jp, i);
+                    }
         }
     }
     float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];

@@ -79,7 +79,7 @@ def test_eval_parity_16bit_storage(ctx, torch_cuda, orc, storage, p):
     mid = ctx.load_model(ctrl, p, storage=storage)
     info = ctx.model_info(mid)
     assert info["scale"] == pytest.approx(float(np.abs(ctrl).max()))
-    assert info["bytes"] == ctrl.size * 16  # row layout: 8 16-bit values per lattice point
+    assert info["bytes"] == ctrl.size * 32  # row layout: 16 16-bit values per lattice point
     got, sp = _run(ctx, torch_cuda, mid, pts)
     deq = dequantize(ctrl, storage)
     ref, ref_sp = orc.eval_points(deq, p, pts)
