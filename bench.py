@@ -48,12 +48,13 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--workload", default="gauss128",
-                    choices=["gauss128", "noise512", "multi16", "serve48", "sweep"],
+                    choices=["gauss128", "noise512", "multi16", "serve48", "sweep", "variants"],
                     help="gauss128: 128^3 degree-3 render + 2^24 points (default); "
                          "noise512: 512^3 degree-4 render at 3840x2160; "
                          "multi16: one batched render of 16 models of degree 2-5; "
                          "serve48: 2000 Poisson requests over 48 resident models through the serving loop; "
-                         "sweep: value / gradient / combined query time vs lattice size and degree")
+                         "sweep: value / gradient / combined query time vs lattice size and degree; "
+                         "variants: the default frame and points per storage, shading, knot kind, weights, query")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 16-bit storage comparison")
@@ -568,18 +569,13 @@ def run_multi16(args, jobs):
 
 SWEEP_DEGREES = (1, 2, 3, 4, 5)
 SWEEP_SIZES = (32, 64, 128, 256, 512)
-SWEEP_MODES = (("value", 1), ("gradient", 2), ("both", 3))
-
-
-def _query_fma(p, mode):
-    a = p + 1
-    return {1: a ** 3 + a * a + a, 2: 2 * a ** 3 + 3 * a * a + 3 * a, 3: 2 * a ** 3 + 3 * a * a + 4 * a}[mode]
+SWEEP_MODES = (("value", 1), ("gradient", 2), ("both", 3), ("hessian", 4))
 
 
 def run_sweep(args):
     """Query-time sweep of the MFA parameter study (Sec. 4.3.3, Fig. 12): the
-    time of one value query, one gradient query and one combined query, per
-    point, for the Gaussian beam (Eq. 1) on n^3 control points, n in
+    time of one value query, one gradient query, one combined query and one
+    Hessian query (Sec. 3.1's higher-order query), per point, for the Gaussian beam (Eq. 1) on n^3 control points, n in
     {32..512}, degrees 1-5, over 2^24 U[0,1]^3 points (inputs larger than L2).
     The headline value is the combined query at degree 3 on 256^3, the
     paper's beam size."""
@@ -597,7 +593,7 @@ def run_sweep(args):
     rng = np.random.default_rng(workloads.seed_for(6))
     pts = workloads.uniform_points(rng, npts)
     d_pts = torch.from_numpy(pts).to(dev)
-    d_out = torch.empty((npts, 4), device=dev)
+    d_out = torch.empty((npts, 10), device=dev)
     table, launches = {}, 0
     clocks = ClockSampler(local)
     clocks.start()
@@ -632,7 +628,7 @@ def run_sweep(args):
     line = {"metric": METRIC, "value": head["queries_per_s"], "unit": UNIT, "n_gpus": world, "steps": steps,
             "warmup": 3, "ms_per_step": npts / head["queries_per_s"] * 1000.0, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "sweep: query time of mfadvr_query_points (value / gradient / both) on the "
+            "config": {"workload": "sweep: query time of mfadvr_query_points (value / gradient / both / hessian) on the "
                                    "Gaussian beam (Eq. 1) at the Greville abscissae, n^3 control points for n in "
                                    f"{list(SWEEP_SIZES)}, degrees {list(SWEEP_DEGREES)}, 2^24 U[0,1]^3 points; "
                                    "headline: both, degree 3, 256^3",
@@ -646,6 +642,105 @@ def run_sweep(args):
             "clocks": clk, "sweep": table}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_variants(args):
+    """The default workload (128^3 Gaussian sum, 1024^2 frame at step 1/1024,
+    2^24 points) on each model and query variant the library supports: FP32 /
+    FP16 / BF16 storage, shading off (value-only kernel), graded non-uniform
+    knots (span widths U[0.2, 1.8] normalised, all axes), rational weights
+    U[0.5, 2], and the value-only, gradient-only and Hessian point queries.
+    Render and query times are medians of CUDA-event timings with the L2
+    flushed between launches; launch shapes from the autotuner."""
+    import numpy as np
+    import torch
+
+    from paper_2204_11762_gb300 import mfadvr, workloads
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    wl = workloads.gaussian_sum_workload()
+    p, prm = wl["degree"], wl["params"]
+    H, W = prm["height"], prm["width"]
+    rng = np.random.default_rng(workloads.seed_for(7))
+    knots = [workloads.graded_knots(rng, 128, p) for _ in range(3)]
+    weights = rng.uniform(0.5, 2.0, size=wl["ctrl"].shape).astype(np.float32)
+    npts = wl["points"].shape[0]
+    d_pts = torch.from_numpy(wl["points"]).to(dev)
+    d_out = torch.empty((npts, 10), device=dev)
+    d_tf = torch.from_numpy(wl["tf"]).to(dev)
+    d_img = torch.empty((H, W, 4), device=dev)
+    d_ns = torch.empty((H, W), dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    steps = max(3, min(args.steps, 20))
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+    variants = [("f32", {}, 1), ("f16", {"storage": "f16"}, 1), ("bf16", {"storage": "bf16"}, 1),
+                ("f32 shading off", {}, 0), ("f32 graded knots", {"knots": knots}, 1),
+                ("f32 rational", {"weights": weights}, 1)]
+    table, launches = {}, 0
+    clocks = ClockSampler(local)
+    clocks.start()
+    with mfadvr.Context(local) as ctx:
+        for name, kw, shading in variants:
+            mid = ctx.load_model(wl["ctrl"], p, **kw)
+            pv = dict(prm, shading=shading)
+            ctx.autotune(mid, wl["camera"], pv, d_tf, wl["tf"].shape[0], d_img, d_ns, stream=stream)
+            r_ms = timed(lambda: ctx.render(mid, wl["camera"], pv, d_tf, wl["tf"].shape[0], d_img, d_ns,
+                                            stream=stream))
+            samples = int(d_ns.sum(dtype=torch.int64).item())
+            q_ms = timed(lambda: ctx.query_points(mid, d_pts, npts, d_out, 3, stream=stream))
+            launches += 2 * steps
+            row = {"render_ms": r_ms, "samples": samples, "render_samples_per_s": samples / (r_ms / 1e3),
+                   "query_both_ms": q_ms, "query_points_per_s": npts / (q_ms / 1e3)}
+            if name == "f32":
+                for qn, q in (("value", 1), ("gradient", 2), ("hessian", 4)):
+                    ms = timed(lambda: ctx.query_points(mid, d_pts, npts, d_out, q, stream=stream))
+                    launches += steps
+                    row[f"query_{qn}_ms"] = ms
+                    row[f"query_{qn}_tflops"] = npts * _query_fma(p, q) * 2 / (ms / 1e3) / 1e12
+            table[name] = row
+            ctx.unload_model(mid)
+    clk = clocks.stop()
+    head = table["f32"]
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = (clk or {}).get("sm_max_mhz") or _measured_peaks().get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    tflops = head["samples"] * C_FMA[p] * 2 / (head["render_ms"] / 1e3) / 1e12
+    line = {"metric": METRIC, "value": (head["samples"] + npts) / ((head["render_ms"] + head["query_both_ms"]) / 1e3),
+            "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": 3,
+            "ms_per_step": head["render_ms"] + head["query_both_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "variants: the 128^3 degree-3 Gaussian-sum frame (1024^2, step 1/1024) and 2^24 "
+                                   "points per storage type, shading, knot kind, rational weights and query kind",
+                       "l2": "flushed between launches (256 MiB write outside the timed events)"},
+            "gpu_launches": launches,
+            "roofline": {"kernel": "render_kernel", "bound": "alu", "achieved": tflops, "peak": peak,
+                         "unit": "TFLOP/s", "frac": tflops / peak, "traffic": None,
+                         "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 FLOP x "
+                                        f"{sm_max:.0f} MHz", "per_unit": f"{C_FMA[p]} FMA per sample"},
+            "clocks": clk, "variants": table}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _query_fma(p, mode):
+    a = p + 1
+    return {1: a ** 3 + a * a + a, 2: 2 * a ** 3 + 3 * a * a + 3 * a, 3: 2 * a ** 3 + 3 * a * a + 4 * a,
+            4: 3 * a ** 3 + 6 * a * a + 10 * a}[mode]
 
 
 def _pct(xs, q):
@@ -819,6 +914,13 @@ def main():
                                                                    "default workload only"}))
             return
         run_multi16(args, workloads.multi_model_workload())
+        return
+    if args.workload == "variants":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm is timed on the "
+                                                                   "default workload only"}))
+            return
+        run_variants(args)
         return
     if args.workload == "sweep":
         if args.impl == "reference":
