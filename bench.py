@@ -575,10 +575,10 @@ SWEEP_MODES = (("value", 1), ("gradient", 2), ("both", 3), ("hessian", 4))
 def run_sweep(args):
     """Query-time sweep of the MFA parameter study (Sec. 4.3.3, Fig. 12): the
     time of one value query, one gradient query, one combined query and one
-    Hessian query (Sec. 3.1's higher-order query), per point, for the Gaussian beam (Eq. 1) on n^3 control points, n in
-    {32..512}, degrees 1-5, over 2^24 U[0,1]^3 points (inputs larger than L2).
-    The headline value is the combined query at degree 3 on 256^3, the
-    paper's beam size."""
+    Hessian query (Sec. 3.1's higher-order query), per point, for the Gaussian
+    beam (Eq. 1) on n^3 control points, n in {32..512}, degrees 1-5, over 2^24
+    U[0,1]^3 points (inputs larger than L2).  The headline value is the
+    combined query at degree 3 on 256^3, the paper's beam size."""
     import numpy as np
     import torch
 
