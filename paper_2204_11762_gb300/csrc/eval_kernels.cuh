@@ -1,15 +1,15 @@
-// mfadvr_eval_points: value and first derivatives of the MFA model at
-// arbitrary parameter points (queryValueMFA + queryGradientMFA of
-// Algorithm 1, computed together as Sec. 3.1 describes), and the kernel that
-// builds a model's row array.  The kernel template lives here; eval_p1.cu ..
-// eval_p5.cu instantiate one degree each and eval_kernels.cu picks the degree
-// and builds the row arrays.
+// mfadvr_eval_points / mfadvr_query_points: the value, the first
+// derivatives, both (queryValueMFA + queryGradientMFA of Algorithm 1,
+// computed together as Sec. 3.1 describes) or the second derivatives too
+// (Sec. 3.1's higher-order query) at arbitrary parameter points.  The kernel
+// template lives here; eval_p1.cu .. eval_p5.cu instantiate one degree each
+// and eval_kernels.cu picks the degree and builds the row arrays.
 //
 // One thread per point, grid-stride over a grid sized to the SM count.  The
-// span index is exact integer work (see span_exact); basis and contraction
-// run in FP32 on the FMA pipe; the span block is (p+1) x ceil((p+1)/2) x
-// ceil((p+1)/4) vector loads from the row array (L2-resident for the point
-// workloads), one L2 sector each in FP32.
+// span index is exact integer work (span_exact on uniform knots, span_search
+// on general ones); basis and contraction run in FP32 on the FMA pipe; the
+// span block is gathered from the row array, one 32-byte sector per entry
+// (8 entries at degree 3 in FP32, 4 in 16 bits).
 #pragma once
 
 #include <cuda_bf16.h>

@@ -14,11 +14,13 @@
 // 32/tile_w pixels) from a global counter; every lane owns one ray and, when
 // its ray ends (exit or early termination), takes the next ray of the warp's
 // tile pool, so lanes stay busy however unequal the ray lengths are.  Each
-// lane walks its ray in lattice units (one FMA per axis per sample), keeps
-// the control points of its current span block in registers and reloads
-// them (ceil((p+1)/2) x ceil((p+1)/4) x (p+1) vector loads from the row
-// array) only when a sample leaves the span.  The contraction runs on packed
-// FP32 FMAs.
+// lane walks its ray in lattice units (one FMA per axis per sample; parameter
+// units on general knots), keeps the control points of its current span
+// block in registers (FP32 pairs, or the stored 16-bit pairs) and reloads
+// them (8 256-bit loads at degree 3 in FP32, 4 in 16 bits) only when a
+// sample leaves the span.  One iteration contracts sample s while it
+// composites sample s-1.  The contraction runs on packed FP32 FMAs.  Template
+// flags: G (gradient queried: shading on), NU (general knots), R (rational).
 //
 // The batched kernel runs the same per-ray code over the concatenated tiles
 // of many render jobs (one image of one model each).  A warp keeps its
