@@ -91,6 +91,12 @@ struct mfadvr_ctx {
     unsigned next_jobs = 0;
     std::map<TuneKey, mfadvr_tuning> tuning;
     mfadvr::api::Server *server = nullptr;
+    // Host-buffer point queries: chunks are copied in, evaluated and copied
+    // out on these streams in turn, so that the two copy directions and the
+    // kernels of neighbouring chunks overlap (created on first use).
+    static constexpr int kPipes = 3;
+    cudaStream_t pipe[kPipes] = {};
+    cudaEvent_t pipe_start = nullptr;
 };
 
 namespace mfadvr {

@@ -519,12 +519,40 @@ mfadvr_status query_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_
     float *d_in = static_cast<float *>(ctx->st_in.ptr);
     float *d_out = static_cast<float *>(ctx->st_out.ptr);
     int32_t *d_sp = spans_host ? reinterpret_cast<int32_t *>(static_cast<char *>(ctx->st_out.ptr) + out_b) : nullptr;
-    e = cudaMemcpyAsync(d_in, params_host, in_b, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_eval_points(view_of(*m), d_in, n, d_out, query, d_sp, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(out_host, d_out, static_cast<size_t>(n) * per, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && d_sp) e = cudaMemcpyAsync(spans_host, d_sp, sp_b, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // The points go through in chunks on the context's pipe streams: chunk c
+    // is copied in, evaluated and copied out on pipe[c % kPipes], so the
+    // copy-in of one chunk, the kernel of another and the copy-out of a third
+    // overlap.  The pipes start after the work already queued on `s`, and the
+    // call returns when all of them have finished.
+    for (int q = 0; q < mfadvr_ctx::kPipes && e == cudaSuccess; ++q)
+        if (!ctx->pipe[q]) e = cudaStreamCreateWithFlags(&ctx->pipe[q], cudaStreamNonBlocking);
+    if (e == cudaSuccess && !ctx->pipe_start) e = cudaEventCreateWithFlags(&ctx->pipe_start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->pipe_start, s);
+    for (int q = 0; q < mfadvr_ctx::kPipes && e == cudaSuccess; ++q)
+        e = cudaStreamWaitEvent(ctx->pipe[q], ctx->pipe_start, 0);
+    const int64_t kChunks = n >= (int64_t(1) << 20) ? 8 : 1;
+    const int64_t chunk = (n + kChunks - 1) / kChunks;
+    const ModelView mv = view_of(*m);
+    for (int64_t c = 0, off = 0; off < n && e == cudaSuccess; ++c, off += chunk) {
+        const int64_t cnt = n - off < chunk ? n - off : chunk;
+        cudaStream_t ps = ctx->pipe[c % mfadvr_ctx::kPipes];
+        const size_t o = static_cast<size_t>(off);
+        e = cudaMemcpyAsync(d_in + 3 * o, params_host + 3 * o, static_cast<size_t>(cnt) * 12, cudaMemcpyHostToDevice,
+                            ps);
+        float *dout = reinterpret_cast<float *>(reinterpret_cast<char *>(d_out) + o * per);
+        if (e == cudaSuccess)
+            e = launch_eval_points(mv, d_in + 3 * o, cnt, dout, query, d_sp ? d_sp + 3 * o : nullptr, ps);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(reinterpret_cast<char *>(out_host) + o * per, dout, static_cast<size_t>(cnt) * per,
+                                cudaMemcpyDeviceToHost, ps);
+        if (e == cudaSuccess && d_sp)
+            e = cudaMemcpyAsync(spans_host + 3 * o, d_sp + 3 * o, static_cast<size_t>(cnt) * 12, cudaMemcpyDeviceToHost,
+                                ps);
+    }
+    for (int q = 0; q < mfadvr_ctx::kPipes; ++q) {
+        const cudaError_t e2 = cudaStreamSynchronize(ctx->pipe[q]);
+        if (e == cudaSuccess) e = e2;
+    }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "eval_points_host");
     return MFADVR_OK;
 }
@@ -567,6 +595,9 @@ mfadvr_status mfadvr_destroy(mfadvr_ctx *ctx)
         if (ctx->h_jobs) cudaFreeHost(ctx->h_jobs);
         for (auto &e : ctx->job_done)
             if (e) cudaEventDestroy(e);
+        for (auto &q : ctx->pipe)
+            if (q) cudaStreamDestroy(q);
+        if (ctx->pipe_start) cudaEventDestroy(ctx->pipe_start);
         ctx->st_in.release();
         ctx->st_out.release();
         ctx->st_aux.release();

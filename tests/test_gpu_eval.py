@@ -219,3 +219,28 @@ def test_query_rejects_bad_query(ctx, torch_cuda):
     torch.cuda.synchronize()
     assert np.allclose(d_out.view(-1)[1:4].cpu().numpy(), 1.0)
     ctx.unload_model(mid)
+
+
+def test_host_query_pipeline_matches_device_path(ctx, torch_cuda):
+    """Host-buffer queries of 2^20 points or more run in chunks on the
+    context's pipe streams; every chunk, the ragged last one included, must
+    give the device-buffer bits, spans too."""
+    from paper_2204_11762_gb300 import mfadvr
+    torch = torch_cuda
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(1234)
+    ctrl = rng.normal(size=(21, 19, 23)).astype(np.float32)
+    mid = ctx.load_model(ctrl, 3)
+    k = (1 << 20) + 7
+    pts = rng.uniform(-0.05, 1.05, size=(k, 3)).astype(np.float32)
+    d_out = torch.empty((k, 4), device=dev)
+    d_sp = torch.empty((k, 3), dtype=torch.int32, device=dev)
+    ctx.eval_points(mid, torch.from_numpy(pts).to(dev), k, d_out, d_sp)
+    torch.cuda.synchronize()
+    sp = np.empty((k, 3), dtype=np.int32)
+    got = ctx.eval_points_host(mid, pts, spans=sp)
+    np.testing.assert_array_equal(got, d_out.cpu().numpy())
+    np.testing.assert_array_equal(sp, d_sp.cpu().numpy())
+    hv = ctx.query_points_host(mid, pts, mfadvr.QUERY_VALUE)
+    np.testing.assert_array_equal(hv, d_out.cpu().numpy()[:, 0])
+    ctx.unload_model(mid)
