@@ -519,7 +519,7 @@ mfadvr_status query_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_
     float *d_in = static_cast<float *>(ctx->st_in.ptr);
     float *d_out = static_cast<float *>(ctx->st_out.ptr);
     int32_t *d_sp = spans_host ? reinterpret_cast<int32_t *>(static_cast<char *>(ctx->st_out.ptr) + out_b) : nullptr;
-    // The points go through in chunks on the context's pipe streams: chunk c
+    // The points go through in 16 chunks on the context's pipe streams: chunk c
     // is copied in, evaluated and copied out on pipe[c % kPipes], so the
     // copy-in of one chunk, the kernel of another and the copy-out of a third
     // overlap.  The pipes start after the work already queued on `s`, and the
@@ -530,7 +530,7 @@ mfadvr_status query_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_
     if (e == cudaSuccess) e = cudaEventRecord(ctx->pipe_start, s);
     for (int q = 0; q < mfadvr_ctx::kPipes && e == cudaSuccess; ++q)
         e = cudaStreamWaitEvent(ctx->pipe[q], ctx->pipe_start, 0);
-    const int64_t kChunks = n >= (int64_t(1) << 20) ? 8 : 1;
+    const int64_t kChunks = n >= (int64_t(1) << 20) ? 16 : 1;
     const int64_t chunk = (n + kChunks - 1) / kChunks;
     const ModelView mv = view_of(*m);
     for (int64_t c = 0, off = 0; off < n && e == cudaSuccess; ++c, off += chunk) {
