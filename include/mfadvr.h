@@ -162,10 +162,11 @@ MFADVR_API mfadvr_status mfadvr_eval_points(mfadvr_ctx *ctx, int32_t model_id, c
 
 /* As mfadvr_eval_points with HOST buffers: copies params in, evaluates and
  * copies the results back through library-owned staging memory, then
- * synchronises.  From 2^20 points up the work runs in 16 chunks on three
- * streams of the context, ordered after the work already queued on `stream`,
- * so that copies in, kernels and copies out of neighbouring chunks overlap;
- * pinned host buffers make the copies asynchronous. */
+ * synchronises.  Page-locked (pinned) host buffers are read and written by
+ * the kernel directly, with no staging copies.  Other buffers go through
+ * staging: from 2^20 points up in 16 chunks on three streams of the context,
+ * ordered after the work already queued on `stream`, so that copies in,
+ * kernels and copies out of neighbouring chunks overlap. */
 MFADVR_API mfadvr_status mfadvr_eval_points_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_host,
                                       int64_t n, float *out_host, int32_t *spans_host, void *stream);
 

@@ -510,6 +510,31 @@ mfadvr_status query_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        // Pinned (page-locked, registered) host buffers: the kernel reads the
+        // points from and writes the results to them directly over the
+        // host link, with no staging copies.  Other buffers take the chunked
+        // copy pipeline below.
+        auto dev_alias = [](const void *h) -> void * {
+            cudaPointerAttributes a;
+            if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+        };
+        const void *zin = dev_alias(params_host);
+        void *zout = dev_alias(out_host);
+        void *zsp = spans_host ? dev_alias(spans_host) : nullptr;
+        const bool aligned = query != MFADVR_QUERY_BOTH || reinterpret_cast<uintptr_t>(zout) % 16 == 0;
+        if (zin && zout && (!spans_host || zsp) && aligned) {
+            cudaError_t e = launch_eval_points(view_of(*m), static_cast<const float *>(zin), n,
+                                               static_cast<float *>(zout), query, static_cast<int32_t *>(zsp), s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "eval_points_host");
+            return MFADVR_OK;
+        }
+    }
     const size_t in_b = static_cast<size_t>(n) * 12;
     const size_t out_b = (static_cast<size_t>(n) * per + 15) / 16 * 16;
     const size_t sp_b = spans_host ? static_cast<size_t>(n) * 12 : 0;

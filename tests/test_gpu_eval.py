@@ -244,3 +244,29 @@ def test_host_query_pipeline_matches_device_path(ctx, torch_cuda):
     hv = ctx.query_points_host(mid, pts, mfadvr.QUERY_VALUE)
     np.testing.assert_array_equal(hv, d_out.cpu().numpy()[:, 0])
     ctx.unload_model(mid)
+
+
+def test_host_query_on_pinned_buffers_matches_device_path(ctx, torch_cuda):
+    """Pinned host buffers are read and written by the kernel directly (no
+    staging); the results must be the device-buffer bits, spans too."""
+    from paper_2204_11762_gb300 import mfadvr
+    torch = torch_cuda
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(4321)
+    ctrl = rng.normal(size=(17, 22, 19)).astype(np.float32)
+    mid = ctx.load_model(ctrl, 4, storage="bf16")
+    k = 300001
+    h_pts = torch.from_numpy(rng.uniform(0, 1, size=(k, 3)).astype(np.float32)).pin_memory()
+    h_out = torch.full((k, 4), float("nan")).pin_memory()
+    h_sp = torch.full((k, 3), -1, dtype=torch.int32).pin_memory()
+    ctx.eval_points_host(mid, h_pts.numpy(), out=h_out.numpy(), spans=h_sp.numpy())
+    d_out = torch.empty((k, 4), device=dev)
+    d_sp = torch.empty((k, 3), dtype=torch.int32, device=dev)
+    ctx.eval_points(mid, h_pts.to(dev), k, d_out, d_sp)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(h_out.numpy(), d_out.cpu().numpy())
+    np.testing.assert_array_equal(h_sp.numpy(), d_sp.cpu().numpy())
+    h_val = torch.empty(k).pin_memory()
+    ctx.query_points_host(mid, h_pts.numpy(), mfadvr.QUERY_VALUE, out=h_val.numpy())
+    np.testing.assert_array_equal(h_val.numpy(), d_out.cpu().numpy()[:, 0])
+    ctx.unload_model(mid)
