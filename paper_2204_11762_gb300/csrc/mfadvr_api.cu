@@ -459,6 +459,18 @@ mfadvr_status mfadvr::fail_noctx(mfadvr_status st, const char *msg) { return fai
 
 namespace {
 
+// The device address of a page-locked (pinned, registered) host buffer, or
+// NULL for any other pointer.
+void *pinned_alias(const void *h)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // Output bytes per point of a query, 0 for an unknown query.
 size_t query_out_bytes(int32_t query)
 {
@@ -515,17 +527,9 @@ mfadvr_status query_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_
         // points from and writes the results to them directly over the
         // host link, with no staging copies.  Other buffers take the chunked
         // copy pipeline below.
-        auto dev_alias = [](const void *h) -> void * {
-            cudaPointerAttributes a;
-            if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
-                cudaGetLastError();
-                return nullptr;
-            }
-            return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
-        };
-        const void *zin = dev_alias(params_host);
-        void *zout = dev_alias(out_host);
-        void *zsp = spans_host ? dev_alias(spans_host) : nullptr;
+        const void *zin = pinned_alias(params_host);
+        void *zout = pinned_alias(out_host);
+        void *zsp = spans_host ? pinned_alias(spans_host) : nullptr;
         const bool aligned = query != MFADVR_QUERY_BOTH || reinterpret_cast<uintptr_t>(zout) % 16 == 0;
         if (zin && zout && (!spans_host || zsp) && aligned) {
             cudaError_t e = launch_eval_points(view_of(*m), static_cast<const float *>(zin), n,
@@ -865,15 +869,25 @@ mfadvr_status mfadvr_render_host(mfadvr_ctx *ctx, int32_t model_id, const mfadvr
     if (mfadvr_status st = stage_tf(ctx, params->tf_rgba, params->tf_size, true, &rs, s)) return st;
     const size_t npix = static_cast<size_t>(params->width) * params->height;
     const size_t img_b = npix * 16, ns_b = nsamples_host ? npix * 4 : 0;
-    cudaError_t e = ctx->st_out.reserve(img_b + ns_b);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "staging allocation");
-    rs.out = static_cast<float4 *>(ctx->st_out.ptr);
-    rs.nsamples = nsamples_host ? reinterpret_cast<int32_t *>(static_cast<char *>(ctx->st_out.ptr) + img_b) : nullptr;
+    // page-locked outputs are written by the kernel directly; others staged
+    void *zimg = pinned_alias(rgba_host), *zns = nsamples_host ? pinned_alias(nsamples_host) : nullptr;
+    const bool direct = zimg && reinterpret_cast<uintptr_t>(zimg) % 16 == 0 && (!nsamples_host || zns);
+    cudaError_t e = cudaSuccess;
+    if (direct) {
+        rs.out = static_cast<float4 *>(zimg);
+        rs.nsamples = static_cast<int32_t *>(zns);
+    } else {
+        e = ctx->st_out.reserve(img_b + ns_b);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "staging allocation");
+        rs.out = static_cast<float4 *>(ctx->st_out.ptr);
+        rs.nsamples =
+            nsamples_host ? reinterpret_cast<int32_t *>(static_cast<char *>(ctx->st_out.ptr) + img_b) : nullptr;
+    }
     int *counter = nullptr;
     if (mfadvr_status st = next_counter(ctx, &counter)) return st;
     e = launch_render(view_of(*m), rs, counter, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(rgba_host, rs.out, img_b, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && nsamples_host)
+    if (e == cudaSuccess && !direct) e = cudaMemcpyAsync(rgba_host, rs.out, img_b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && !direct && nsamples_host)
         e = cudaMemcpyAsync(nsamples_host, rs.nsamples, ns_b, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "render_host");

@@ -159,6 +159,13 @@ def test_render_host_buffers_match_device(ctx, torch_cuda):
     img_h = ctx.render_host(mid, wl["camera"], wl["params"], wl["tf"], nsamples=ns_h)
     np.testing.assert_array_equal(img, img_h)
     np.testing.assert_array_equal(ns, ns_h)
+    # page-locked outputs are written by the kernel directly: the same bits
+    torch = torch_cuda
+    img_p = torch.full(img.shape, float("nan")).pin_memory()
+    ns_p = torch.full(ns.shape, -1, dtype=torch.int32).pin_memory()
+    ctx.render_host(mid, wl["camera"], wl["params"], wl["tf"], rgba=img_p.numpy(), nsamples=ns_p.numpy())
+    np.testing.assert_array_equal(img, img_p.numpy())
+    np.testing.assert_array_equal(ns, ns_p.numpy())
     ctx.unload_model(mid)
 
 
