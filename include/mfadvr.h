@@ -215,7 +215,9 @@ MFADVR_API mfadvr_status mfadvr_render(mfadvr_ctx *ctx, int32_t model_id, const 
 
 /* As mfadvr_render with HOST buffers (params->tf_rgba is then a host
  * pointer): copies the table in, renders, copies the image (and sample
- * counts, if requested) back and synchronises the stream. */
+ * counts, if requested) back and synchronises the stream.  Page-locked
+ * output buffers (16-byte aligned for rgba) are written by the kernel
+ * directly instead. */
 MFADVR_API mfadvr_status mfadvr_render_host(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_camera *camera,
                                  const mfadvr_render_params *params, float *rgba_host,
                                  int32_t *nsamples_host, void *stream);
