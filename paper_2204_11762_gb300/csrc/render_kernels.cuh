@@ -48,7 +48,7 @@ __device__ __forceinline__ float clamp01f(float x) { return fminf(fmaxf(x, 0.0f)
 // arrays at every sample.
 template <int P, bool R>
 struct CacheCP {
-    static constexpr bool value = P <= 4 && !R;
+    static constexpr bool value = R ? P <= 3 : P <= 4;
 };
 
 // Resident CTAs per SM the compiler is asked to fit: four (16 warps, at
@@ -98,12 +98,17 @@ struct CacheElem<__nv_bfloat16> {
 template <int P, typename T, bool R>
 struct SpanCache {
     static constexpr bool kOn = CacheCP<P, R>::value;
-    typename CacheElem<T>::type v[kOn ? (P + 1) : 1][kOn ? Block<P>::JP : 1][kOn ? (P + 1) : 1];
-    __device__ __forceinline__ float2 pair(int k, int jp, int i) const
+    static constexpr int K = kOn ? P + 1 : 1, J = kOn ? Block<P>::JP : 1, KW = kOn && R ? P + 1 : 1;
+    typename CacheElem<T>::type v[K][J][K];    // the block (rational models: w P)
+    typename CacheElem<T>::type w[KW][J][KW];  // rational models: the weights' block
+    template <typename E>
+    static __device__ __forceinline__ float2 to_pair(E e)
     {
-        if constexpr (CacheElem<T>::kPacked) return pair16_to_float2<T>(v[k][jp][i]);
-        else return v[k][jp][i];
+        if constexpr (CacheElem<T>::kPacked) return pair16_to_float2<T>(e);
+        else return e;
     }
+    __device__ __forceinline__ float2 pair(int k, int jp, int i) const { return to_pair(v[k][jp][i]); }
+    __device__ __forceinline__ float2 wpair(int k, int jp, int i) const { return to_pair(w[k][jp][i]); }
 };
 
 // Pixel of ray slot `slot` (tile = slot / 32, lane-in-tile = slot % 32) for
@@ -288,6 +293,18 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
                         if constexpr (CacheElem<T>::kPacked) cache.v[k][jp][i] = block_word<P, T>(q, k, jp, i);
                         else cache.v[k][jp][i] = block_pair<P, T>(q, k, jp, i);
                     }
+            if constexpr (R) {
+                load_block<P, T>(mv.wrows, ray.base, mv.n[0], mv.n01, q);
+#pragma unroll
+                for (int k = 0; k <= P; ++k)
+#pragma unroll
+                    for (int jp = 0; jp < JP; ++jp)
+#pragma unroll
+                        for (int i = 0; i <= P; ++i) {
+                            if constexpr (CacheElem<T>::kPacked) cache.w[k][jp][i] = block_word<P, T>(q, k, jp, i);
+                            else cache.w[k][jp][i] = block_pair<P, T>(q, k, jp, i);
+                        }
+            }
         }
     }
     float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
@@ -370,10 +387,19 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
         const int n0 = mv.n[0], n01 = mv.n01, base = ray.base;
         contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw,
                        [&](int k, int jp, int i) { return row_pair<T>(mv.rows, base, n0, n01, k, jp, i); }, ray.r);
-        if constexpr (R) {
+    }
+    if constexpr (R) {
+        {
             float rw[4];
-            contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw,
-                           [&](int k, int jp, int i) { return row_pair<T>(mv.wrows, base, n0, n01, k, jp, i); }, rw);
+            if constexpr (kCache) {
+                contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return cache.wpair(k, jp, i); },
+                               rw);
+            } else {
+                const int n0 = mv.n[0], n01 = mv.n01, base = ray.base;
+                contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw,
+                               [&](int k, int jp, int i) { return row_pair<T>(mv.wrows, base, n0, n01, k, jp, i); },
+                               rw);
+            }
             // the basis scale cancels in A / W; the storage scales do not
             const float W = rw[0] * mv.wscale, f = (ray.r[0] * mv.scale) / W;
             if constexpr (G) {

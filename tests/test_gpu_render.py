@@ -171,11 +171,21 @@ def test_render_host_buffers_match_device(ctx, torch_cuda):
 
 def test_full_size_gaussian_workload_sampled_rows(ctx, torch_cuda, orc):
     """The 128^3 Gaussian-sum model at 1024^2, step 1/1024, in the launch the
-    benchmark times; every 64th row against the oracle."""
+    benchmark times (the autotuner's shape); every 64th row against the
+    oracle.  The default launch shape gives the same bits (per-ray arithmetic
+    does not depend on the tiles)."""
     from paper_2204_11762_gb300 import workloads
+    torch = torch_cuda
     wl = workloads.gaussian_sum_workload(with_points=False)
     mid = ctx.load_model(wl["ctrl"], wl["degree"])
-    img, ns = _render(ctx, torch_cuda, mid, wl["camera"], wl["params"], wl["tf"])
+    img0, ns0 = _render(ctx, torch, mid, wl["camera"], wl["params"], wl["tf"])
+    dev = torch.device("cuda:0")
+    H, W = wl["params"]["height"], wl["params"]["width"]
+    ctx.autotune(mid, wl["camera"], wl["params"], torch.from_numpy(wl["tf"]).to(dev), wl["tf"].shape[0],
+                 torch.empty((H, W, 4), device=dev), torch.empty((H, W), dtype=torch.int32, device=dev))
+    img, ns = _render(ctx, torch, mid, wl["camera"], wl["params"], wl["tf"])
+    np.testing.assert_array_equal(img, img0)
+    np.testing.assert_array_equal(ns, ns0)
     ref = orc.render(wl["ctrl"], wl["degree"], wl["camera"], dict(wl["params"], tf=wl["tf"]), row_step=64)
     rows = np.arange(0, wl["params"]["height"], 64)
     assert_render_parity(img, ns, ref, rows=rows)
