@@ -87,8 +87,8 @@ typedef struct {
                               model (NURBS, Sec. 2.3), f = sum w P N N N /
                               sum w N N N.  The library stores w P and w in
                               the storage type (16-bit: each with its own
-                              max-abs scale) and renders without the
-                              per-lane span cache, so it is slower */
+                              max-abs scale); two contractions per query
+                              make it about half the plain model's speed */
 } mfadvr_model_desc;
 
 /* Camera in world space (the "Ray Definition" step of Sec. 3.1).  Frame:
