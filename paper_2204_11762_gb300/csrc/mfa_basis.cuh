@@ -534,6 +534,10 @@ constexpr int contract_fma(int p, int q)
                             : (q == kQueryGradient ? 2 * a * a * a + 3 * a * a + 3 * a : 2 * a * a * a + 3 * a * a + 4 * a);
 }
 
+static_assert(contract_fma(3, kQueryBoth) == 192 && contract_fma(4, kQueryBoth) == 345 &&
+                  contract_fma(3, kQueryValue) == 84 && contract_fma(3, kQueryGradient) == 188,
+              "multiply-add counts of the contraction");
+
 // Sum-factorised contraction of the (P+1)^3 control points under a span
 // with the tensor-product basis:
 //   f = sum N_i N_j N_k P_ijk,  f_u = sum N'_i N_j N_k P_ijk, f_v, f_w alike.
