@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 # DRAM bytes (read + write) of one render_kernel<3, float> launch on the
 # 128^3 workload from one ncu capture (profiles/render_kernel_gauss128_p3_persp1024.md),
 # valid only for the kernel sources it was taken on.
-RENDER_TRAFFIC = {"sources_sha256_16": "0821e78c0b761687", "bytes": 78303232}
+RENDER_TRAFFIC = {"sources_sha256_16": "7cc195096e84e16a", "bytes": 78253568}
 RENDER_SOURCES = ("paper_2204_11762_gb300/csrc/render_kernels.cuh", "paper_2204_11762_gb300/csrc/mfa_basis.cuh",
                   "paper_2204_11762_gb300/csrc/mfa_internal.h")
 
