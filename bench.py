@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 # DRAM bytes (read + write) of one render_kernel<3, float> launch on the
 # 128^3 workload from one ncu capture (profiles/render_kernel_gauss128_p3_persp1024.md),
 # valid only for the kernel sources it was taken on.
-RENDER_TRAFFIC = {"sources_sha256_16": "7cc195096e84e16a", "bytes": 78253568}
+RENDER_TRAFFIC = {"sources_sha256_16": "07c236724c1d2827", "bytes": 78253568}
 RENDER_SOURCES = ("paper_2204_11762_gb300/csrc/render_kernels.cuh", "paper_2204_11762_gb300/csrc/mfa_basis.cuh",
                   "paper_2204_11762_gb300/csrc/mfa_internal.h")
 
@@ -363,20 +363,40 @@ def run_ours(args, wl):
         tf_np = h_tf.numpy()
         img_np = h_img.numpy()
         k2 = max(3, min(args.steps, 10))
-        for _ in range(2):
+        # One step: the point query, queued first on its own stream, reads the
+        # points from and writes the results to the pinned buffers over the
+        # host link on a few SMs; the frame renders beside it on the others
+        # and is written to the pinned image.  Both calls are the library's
+        # host-buffer entry points; the step ends when both streams are done.
+        q_stream = torch.cuda.Stream(device=dev)
+
+        def e2e_step(cap):
+            ctx.query_points_host_async(mid, h_pts, npts, h_out, max_ctas=cap, stream=q_stream.cuda_stream)
             ctx.render_host(mid, wl["camera"], prm, tf_np, rgba=img_np, stream=stream)
-            ctx.eval_points_host(mid, h_pts.numpy(), out=h_out.numpy(), stream=stream)
+            q_stream.synchronize()
+
+        # untimed set-up: the share of the GPU the point query gets
+        trial = {}
+        for cap in (16, 24, 32, 48, 64, 0):
+            e2e_step(cap)
+            t0 = time.perf_counter()
+            for _ in range(3):
+                e2e_step(cap)
+            trial[cap] = time.perf_counter() - t0
+        cap = min(trial, key=trial.get)
+        for _ in range(2):
+            e2e_step(cap)
         barrier()
         t0 = time.perf_counter()
         for _ in range(k2):
-            ctx.render_host(mid, wl["camera"], prm, tf_np, rgba=img_np, stream=stream)
-            ctx.eval_points_host(mid, h_pts.numpy(), out=h_out.numpy(), stream=stream)
+            e2e_step(cap)
         t1 = time.perf_counter()
         dt = max_over_ranks(t1 - t0, dev)
         line["e2e"] = {"value": whole_job_value(units_per_step, k2, dt * 1000.0, world), "unit": UNIT,
                        "h2d_bytes_per_step": npts * 12 + wl["tf"].nbytes,
                        "d2h_bytes_per_step": npts * 16 + H * W * 16, "steps": k2,
-                       "ms_per_step": 1000 * dt / k2}
+                       "ms_per_step": 1000 * dt / k2,
+                       "overlap": {"query_max_ctas": cap, "query_stream": "separate, queued before the frame"}}
 
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 at N = 1 ---
     if not args.no_cpu_baseline and world == 1:

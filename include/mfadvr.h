@@ -201,6 +201,26 @@ MFADVR_API mfadvr_status mfadvr_query_points_host(mfadvr_ctx *ctx, int32_t model
                                        int64_t n, int32_t query, float *out_host, int32_t *spans_host,
                                        void *stream);
 
+/* Stream-ordered mfadvr_query_points_host for page-locked host buffers
+ * (cudaHostAlloc, cudaHostRegister, pinned tensors): the query is queued on
+ * `stream` and the call returns without waiting.  The kernel reads params_host
+ * and writes out_host (and spans_host) over the host link; the results are in
+ * place once the stream's work up to this call has completed, and the buffers
+ * must stay allocated until then.  Results equal mfadvr_query_points' bit for
+ * bit.
+ *  max_ctas: at most this many 256-thread blocks serve the query, 0 = as many
+ *            as fill the GPU.  A query on host buffers waits on the host link
+ *            and on its gathers more than on the SMs, so a few blocks keep most
+ *            of its rate and leave the other SMs to work queued on other
+ *            streams after it, e.g. a render: that is how the point query of a
+ *            step overlaps the step's frame.
+ * EINVAL: a buffer that is not page-locked, out not aligned as
+ * mfadvr_query_points requires, max_ctas < 0, plus mfadvr_query_points' cases.
+ * n = 0 is a no-op. */
+MFADVR_API mfadvr_status mfadvr_query_points_host_async(mfadvr_ctx *ctx, int32_t model_id, const float *params_host,
+                                             int64_t n, int32_t query, float *out_host, int32_t *spans_host,
+                                             int32_t max_ctas, void *stream);
+
 /* Ray-cast one image (Algorithm 1): per pixel, march the ray through the
  * model's world box, query value (+ gradient when shading), map through the
  * transfer function, shade, composite front to back and stop early once the

@@ -61,15 +61,15 @@ __global__ void build_rows_kernel(const float *__restrict__ src, void *__restric
 }  // namespace
 
 cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t n, float *out, int query,
-                               int32_t *spans, cudaStream_t stream)
+                               int32_t *spans, cudaStream_t stream, int max_blocks)
 {
     if (n <= 0) return cudaSuccess;
     switch (mv.p) {
-    case 1: return launch_eval_p1(mv, params, n, out, query, spans, stream);
-    case 2: return launch_eval_p2(mv, params, n, out, query, spans, stream);
-    case 3: return launch_eval_p3(mv, params, n, out, query, spans, stream);
-    case 4: return launch_eval_p4(mv, params, n, out, query, spans, stream);
-    case 5: return launch_eval_p5(mv, params, n, out, query, spans, stream);
+    case 1: return launch_eval_p1(mv, params, n, out, query, spans, stream, max_blocks);
+    case 2: return launch_eval_p2(mv, params, n, out, query, spans, stream, max_blocks);
+    case 3: return launch_eval_p3(mv, params, n, out, query, spans, stream, max_blocks);
+    case 4: return launch_eval_p4(mv, params, n, out, query, spans, stream, max_blocks);
+    case 5: return launch_eval_p5(mv, params, n, out, query, spans, stream, max_blocks);
     default: return cudaErrorInvalidValue;
     }
 }

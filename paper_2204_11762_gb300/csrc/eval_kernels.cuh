@@ -21,6 +21,9 @@
 namespace mfadvr {
 namespace {
 
+// Points whose parameters a thread loads ahead of the one it evaluates.
+constexpr int kPointsAhead = 1;
+
 // NU: general knots (span search, per-span pieces); otherwise uniform knots
 // (exact floor, uniform pieces or the clamped-pattern table).  R: rational
 // model, rows hold w P and wrows w; f = A / W and grad f = (grad A - f grad W)
@@ -42,14 +45,33 @@ __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const fl
     // a rational query needs W always and A's value for the gradient too
     constexpr int QA = R ? (Q == kQueryValue ? kQueryValue : kQueryBoth) : Q;
 
-    for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < n;
-         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        // Points and outputs stream through once: loaded and stored with the
-        // evict-first hint so that they do not push the row array out of L2.
+    // Points and outputs stream through once: loaded and stored with the
+    // evict-first hint so that they do not push the row array out of L2.  A
+    // thread keeps the parameters of its next kPointsAhead points in flight
+    // while it evaluates the current one (the points may sit in host memory,
+    // a few microseconds away).
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    float ahead[kPointsAhead + 1][3];
+#pragma unroll
+    for (int q = 0; q < kPointsAhead; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            ahead[q][c] = idx + q * stride < n ? __ldcs(params + 3 * (idx + q * stride) + c) : 0.0f;
+    for (; idx < n; idx += stride) {
+        {
+            const int64_t j = idx + kPointsAhead * stride;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ahead[kPointsAhead][c] = j < n ? __ldcs(params + 3 * j + c) : 0.0f;
+        }
         // fminf/fmaxf return the non-NaN operand: NaN clamps to 0.
-        const float u = fminf(fmaxf(__ldcs(params + 3 * idx + 0), 0.0f), 1.0f);
-        const float v = fminf(fmaxf(__ldcs(params + 3 * idx + 1), 0.0f), 1.0f);
-        const float w = fminf(fmaxf(__ldcs(params + 3 * idx + 2), 0.0f), 1.0f);
+        const float u = fminf(fmaxf(ahead[0][0], 0.0f), 1.0f);
+        const float v = fminf(fmaxf(ahead[0][1], 0.0f), 1.0f);
+        const float w = fminf(fmaxf(ahead[0][2], 0.0f), 1.0f);
+#pragma unroll
+        for (int q = 0; q < kPointsAhead; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ahead[q][c] = ahead[q + 1][c];
         int k0, k1, k2;
         float x0, x1, x2;
         float d0 = mf0, d1 = mf1, d2 = mf2;  // d/du = d * d/dx (1 / span width)
@@ -186,7 +208,7 @@ __global__ void __launch_bounds__(256) eval_points_kernel(ModelView mv, const fl
 
 template <int P, typename T, int Q, bool NU, bool R>
 cudaError_t launch_eval_k(const ModelView &mv, const float *params, int64_t n, float *out, int32_t *spans,
-                          cudaStream_t stream)
+                          cudaStream_t stream, int max_blocks)
 {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -194,7 +216,8 @@ cudaError_t launch_eval_k(const ModelView &mv, const float *params, int64_t n, f
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval_points_kernel<P, T, Q, NU, R>, 256, 0);
     if (per_sm < 1) per_sm = 1;
     const int64_t need = (n + 255) / 256;
-    const int64_t cap = static_cast<int64_t>(sms) * per_sm;
+    int64_t cap = static_cast<int64_t>(sms) * per_sm;
+    if (max_blocks > 0 && max_blocks < cap) cap = max_blocks;
     const int blocks = static_cast<int>(need < cap ? need : cap);
     eval_points_kernel<P, T, Q, NU, R><<<blocks, 256, 0, stream>>>(mv, params, n, out, spans);
     return cudaGetLastError();
@@ -202,55 +225,60 @@ cudaError_t launch_eval_k(const ModelView &mv, const float *params, int64_t n, f
 
 template <int P, typename T, int Q>
 cudaError_t launch_eval_q(const ModelView &mv, const float *params, int64_t n, float *out, int32_t *spans,
-                          cudaStream_t stream)
+                          cudaStream_t stream, int max_blocks)
 {
     if (mv.rational)
-        return mv.nu ? launch_eval_k<P, T, Q, true, true>(mv, params, n, out, spans, stream)
-                     : launch_eval_k<P, T, Q, false, true>(mv, params, n, out, spans, stream);
-    return mv.nu ? launch_eval_k<P, T, Q, true, false>(mv, params, n, out, spans, stream)
-                 : launch_eval_k<P, T, Q, false, false>(mv, params, n, out, spans, stream);
+        return mv.nu ? launch_eval_k<P, T, Q, true, true>(mv, params, n, out, spans, stream, max_blocks)
+                     : launch_eval_k<P, T, Q, false, true>(mv, params, n, out, spans, stream, max_blocks);
+    return mv.nu ? launch_eval_k<P, T, Q, true, false>(mv, params, n, out, spans, stream, max_blocks)
+                 : launch_eval_k<P, T, Q, false, false>(mv, params, n, out, spans, stream, max_blocks);
 }
 
 template <int P, typename T>
 cudaError_t launch_eval_t(const ModelView &mv, const float *params, int64_t n, float *out, int query,
-                          int32_t *spans, cudaStream_t stream)
+                          int32_t *spans, cudaStream_t stream, int max_blocks)
 {
     switch (query) {
-    case kQueryValue: return launch_eval_q<P, T, kQueryValue>(mv, params, n, out, spans, stream);
-    case kQueryGradient: return launch_eval_q<P, T, kQueryGradient>(mv, params, n, out, spans, stream);
-    case kQueryBoth: return launch_eval_q<P, T, kQueryBoth>(mv, params, n, out, spans, stream);
-    case kQueryHessian: return launch_eval_q<P, T, kQueryHessian>(mv, params, n, out, spans, stream);
+    case kQueryValue: return launch_eval_q<P, T, kQueryValue>(mv, params, n, out, spans, stream, max_blocks);
+    case kQueryGradient:
+        return launch_eval_q<P, T, kQueryGradient>(mv, params, n, out, spans, stream, max_blocks);
+    case kQueryBoth: return launch_eval_q<P, T, kQueryBoth>(mv, params, n, out, spans, stream, max_blocks);
+    case kQueryHessian:
+        return launch_eval_q<P, T, kQueryHessian>(mv, params, n, out, spans, stream, max_blocks);
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <int P, typename T>
 cudaError_t launch_eval_dtype_p(const ModelView &mv, const float *params, int64_t n, float *out, int query,
-                                int32_t *spans, cudaStream_t stream)
+                                int32_t *spans, cudaStream_t stream, int max_blocks)
 {
-    return launch_eval_t<P, T>(mv, params, n, out, query, spans, stream);
+    return launch_eval_t<P, T>(mv, params, n, out, query, spans, stream, max_blocks);
 }
 
 }  // namespace
 
 // The per-degree launcher one eval_pN.cu defines.
-#define MFADVR_EVAL_DEGREE(PP)                                                                                \
-    cudaError_t launch_eval_p##PP(const ModelView &mv, const float *params, int64_t n, float *out, int query,  \
-                                  int32_t *spans, cudaStream_t stream)                                        \
-    {                                                                                                         \
-        switch (mv.dtype) {                                                                                   \
-        case MFADVR_F32: return launch_eval_dtype_p<PP, float>(mv, params, n, out, query, spans, stream);     \
-        case MFADVR_F16: return launch_eval_dtype_p<PP, __half>(mv, params, n, out, query, spans, stream);    \
-        case MFADVR_BF16:                                                                                     \
-            return launch_eval_dtype_p<PP, __nv_bfloat16>(mv, params, n, out, query, spans, stream);          \
-        default: return cudaErrorInvalidValue;                                                                \
-        }                                                                                                     \
+#define MFADVR_EVAL_DEGREE(PP)                                                                               \
+    cudaError_t launch_eval_p##PP(const ModelView &mv, const float *params, int64_t n, float *out, int query, \
+                                  int32_t *spans, cudaStream_t stream, int max_blocks)                       \
+    {                                                                                                        \
+        switch (mv.dtype) {                                                                                  \
+        case MFADVR_F32:                                                                                     \
+            return launch_eval_dtype_p<PP, float>(mv, params, n, out, query, spans, stream, max_blocks);     \
+        case MFADVR_F16:                                                                                     \
+            return launch_eval_dtype_p<PP, __half>(mv, params, n, out, query, spans, stream, max_blocks);    \
+        case MFADVR_BF16:                                                                                    \
+            return launch_eval_dtype_p<PP, __nv_bfloat16>(mv, params, n, out, query, spans, stream,          \
+                                                          max_blocks);                                       \
+        default: return cudaErrorInvalidValue;                                                               \
+        }                                                                                                    \
     }
 
-cudaError_t launch_eval_p1(const ModelView &, const float *, int64_t, float *, int, int32_t *, cudaStream_t);
-cudaError_t launch_eval_p2(const ModelView &, const float *, int64_t, float *, int, int32_t *, cudaStream_t);
-cudaError_t launch_eval_p3(const ModelView &, const float *, int64_t, float *, int, int32_t *, cudaStream_t);
-cudaError_t launch_eval_p4(const ModelView &, const float *, int64_t, float *, int, int32_t *, cudaStream_t);
-cudaError_t launch_eval_p5(const ModelView &, const float *, int64_t, float *, int, int32_t *, cudaStream_t);
+cudaError_t launch_eval_p1(const ModelView &, const float *, int64_t, float *, int, int32_t *, cudaStream_t, int);
+cudaError_t launch_eval_p2(const ModelView &, const float *, int64_t, float *, int, int32_t *, cudaStream_t, int);
+cudaError_t launch_eval_p3(const ModelView &, const float *, int64_t, float *, int, int32_t *, cudaStream_t, int);
+cudaError_t launch_eval_p4(const ModelView &, const float *, int64_t, float *, int, int32_t *, cudaStream_t, int);
+cudaError_t launch_eval_p5(const ModelView &, const float *, int64_t, float *, int, int32_t *, cudaStream_t, int);
 
 }  // namespace mfadvr

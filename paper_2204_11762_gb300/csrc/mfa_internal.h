@@ -77,10 +77,11 @@ struct RenderJob {
 static_assert(sizeof(RenderJob) % 8 == 0, "RenderJob is copied in 8-byte words");
 
 // Kernel launchers (asynchronous on `stream`).
-// query is an mfadvr_query: out holds n floats (value), 3n (gradient) or n
-// float4 (both).
+// query is an mfadvr_query: out holds n floats (value), 3n (gradient), n
+// float4 (both) or 10n (Hessian).  The point-query grid is the SM count
+// times the resident CTAs per SM, capped at max_blocks CTAs when that is > 0.
 cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t n, float *out, int query,
-                               int32_t *spans, cudaStream_t stream);
+                               int32_t *spans, cudaStream_t stream, int max_blocks = 0);
 // `counter` is one device int the render kernel's warps take ray tiles from;
 // the launcher zeroes it on `stream` first.  The value-only kernel runs when
 // rs.shading is 0 (no gradient is needed).

@@ -508,17 +508,67 @@ mfadvr_status query_device(mfadvr_ctx *ctx, int32_t model_id, const float *param
     return MFADVR_OK;
 }
 
+// Device addresses of a query's page-locked host buffers.
+struct HostAliases {
+    const float *params = nullptr;
+    float *out = nullptr;
+    int32_t *spans = nullptr;
+};
+
+// True when params, out (and spans, when given) are page-locked host memory
+// and out is aligned for the query's output rows.
+bool host_aliases(const float *params_host, float *out_host, int32_t *spans_host, int32_t query, HostAliases *a)
+{
+    a->params = static_cast<const float *>(pinned_alias(params_host));
+    a->out = static_cast<float *>(pinned_alias(out_host));
+    a->spans = spans_host ? static_cast<int32_t *>(pinned_alias(spans_host)) : nullptr;
+    const uintptr_t align = query == MFADVR_QUERY_BOTH ? 16 : 4;
+    return a->params && a->out && (!spans_host || a->spans) && reinterpret_cast<uintptr_t>(a->out) % align == 0 &&
+           reinterpret_cast<uintptr_t>(a->params) % 4 == 0 && reinterpret_cast<uintptr_t>(a->spans) % 4 == 0;
+}
+
+// Argument checks shared by the host-buffer queries; *skip is set for n = 0.
+mfadvr_status check_host_query(mfadvr_ctx *ctx, int32_t model_id, const float *params_host, int64_t n,
+                               int32_t query, const float *out_host, Model **m, bool *skip)
+{
+    *skip = false;
+    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
+    if (mfadvr_status st = find_model(ctx, model_id, m)) return st;
+    if (query_out_bytes(query) == 0) return fail(ctx, MFADVR_EINVAL, "query must be 1 (value), 2 (gradient), 3 or 4");
+    if (n < 0) return fail(ctx, MFADVR_EINVAL, "n must be >= 0");
+    *skip = n == 0;
+    if (n > 0 && (!params_host || !out_host)) return fail(ctx, MFADVR_EINVAL, "params and out must not be NULL");
+    return MFADVR_OK;
+}
+
+mfadvr_status query_host_async(mfadvr_ctx *ctx, int32_t model_id, const float *params_host, int64_t n,
+                               int32_t query, float *out_host, int32_t *spans_host, int32_t max_ctas, void *stream)
+{
+    Model *m = nullptr;
+    bool skip = false;
+    if (mfadvr_status st = check_host_query(ctx, model_id, params_host, n, query, out_host, &m, &skip)) return st;
+    if (max_ctas < 0) return fail(ctx, MFADVR_EINVAL, "max_ctas must be >= 0");
+    if (skip) return MFADVR_OK;
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
+    HostAliases z;
+    if (!host_aliases(params_host, out_host, spans_host, query, &z))
+        return fail(ctx, MFADVR_EINVAL, "params, out and spans must be page-locked host memory, out aligned to %d bytes",
+                    query == MFADVR_QUERY_BOTH ? 16 : 4);
+    const cudaError_t e = launch_eval_points(view_of(*m), z.params, n, z.out, query, z.spans,
+                                             static_cast<cudaStream_t>(stream), max_ctas);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "query_points_host_async");
+    return MFADVR_OK;
+}
+
 mfadvr_status query_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_host, int64_t n, int32_t query,
                          float *out_host, int32_t *spans_host, void *stream)
 {
-    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
     Model *m = nullptr;
-    if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
+    bool skip = false;
+    if (mfadvr_status st = check_host_query(ctx, model_id, params_host, n, query, out_host, &m, &skip)) return st;
+    if (skip) return MFADVR_OK;
     const size_t per = query_out_bytes(query);
-    if (per == 0) return fail(ctx, MFADVR_EINVAL, "query must be 1 (value), 2 (gradient), 3 or 4");
-    if (n < 0) return fail(ctx, MFADVR_EINVAL, "n must be >= 0");
-    if (n == 0) return MFADVR_OK;
-    if (!params_host || !out_host) return fail(ctx, MFADVR_EINVAL, "params and out must not be NULL");
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -527,13 +577,9 @@ mfadvr_status query_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_
         // points from and writes the results to them directly over the
         // host link, with no staging copies.  Other buffers take the chunked
         // copy pipeline below.
-        const void *zin = pinned_alias(params_host);
-        void *zout = pinned_alias(out_host);
-        void *zsp = spans_host ? pinned_alias(spans_host) : nullptr;
-        const bool aligned = query != MFADVR_QUERY_BOTH || reinterpret_cast<uintptr_t>(zout) % 16 == 0;
-        if (zin && zout && (!spans_host || zsp) && aligned) {
-            cudaError_t e = launch_eval_points(view_of(*m), static_cast<const float *>(zin), n,
-                                               static_cast<float *>(zout), query, static_cast<int32_t *>(zsp), s);
+        HostAliases z;
+        if (host_aliases(params_host, out_host, spans_host, query, &z)) {
+            cudaError_t e = launch_eval_points(view_of(*m), z.params, n, z.out, query, z.spans, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "eval_points_host");
             return MFADVR_OK;
@@ -822,6 +868,13 @@ mfadvr_status mfadvr_query_points_host(mfadvr_ctx *ctx, int32_t model_id, const 
                                        int32_t query, float *out_host, int32_t *spans_host, void *stream)
 {
     return query_host(ctx, model_id, params_host, n, query, out_host, spans_host, stream);
+}
+
+mfadvr_status mfadvr_query_points_host_async(mfadvr_ctx *ctx, int32_t model_id, const float *params_host, int64_t n,
+                                             int32_t query, float *out_host, int32_t *spans_host, int32_t max_ctas,
+                                             void *stream)
+{
+    return query_host_async(ctx, model_id, params_host, n, query, out_host, spans_host, max_ctas, stream);
 }
 
 mfadvr_status mfadvr_render(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_camera *camera,

@@ -32,7 +32,7 @@ EXPORTS = ("mfadvr_create", "mfadvr_destroy", "mfadvr_load_model", "mfadvr_unloa
            "mfadvr_status_string", "mfadvr_last_error", "mfadvr_render_lattice_noalloc", "mfadvr_render_batch",
            "mfadvr_autotune", "mfadvr_tuning_save", "mfadvr_tuning_load", "mfadvr_serve_start", "mfadvr_serve_stop",
            "mfadvr_submit", "mfadvr_wait", "mfadvr_serve_stats", "mfadvr_serve_trace", "mfadvr_query_points",
-           "mfadvr_query_points_host")
+           "mfadvr_query_points_host", "mfadvr_query_points_host_async")
 MAX_BATCH = 256
 NOALLOC_MAX_POINTS = 1 << 19
 
@@ -109,6 +109,7 @@ def load_library(build_if_missing: bool = True):
         "mfadvr_eval_points_host": [vp, i32, vp, i64, vp, vp, vp],
         "mfadvr_query_points": [vp, i32, vp, i64, i32, vp, vp, vp],
         "mfadvr_query_points_host": [vp, i32, vp, i64, i32, vp, vp, vp],
+        "mfadvr_query_points_host_async": [vp, i32, vp, i64, i32, vp, vp, i32, vp],
         "mfadvr_render": [vp, i32, P(Camera), P(RenderParams), vp, vp, vp],
         "mfadvr_render_host": [vp, i32, P(Camera), P(RenderParams), vp, vp, vp],
     }
@@ -330,6 +331,16 @@ class Context:
         self._check(self._L.mfadvr_query_points_host(self._h, int(model_id), _ptr(params), n, int(query),
                                                      _ptr(out), _ptr(spans), _stream(stream)))
         return out
+
+    def query_points_host_async(self, model_id, params_pinned, n, out_pinned, query=QUERY_BOTH, spans_pinned=None,
+                                max_ctas=0, stream=None):
+        """query_points on page-locked host buffers (pinned tensors or arrays in
+        page-locked memory), queued on `stream` without waiting: the results are
+        in out_pinned once the stream has reached this call.  max_ctas caps the
+        256-thread blocks that serve it (0: the whole GPU)."""
+        self._check(self._L.mfadvr_query_points_host_async(self._h, int(model_id), _ptr(params_pinned), int(n),
+                                                           int(query), _ptr(out_pinned), _ptr(spans_pinned),
+                                                           int(max_ctas), _stream(stream)))
 
     def render(self, model_id, camera: dict, params: dict, tf_dev, tf_size, rgba_dev, nsamples_dev=None,
                stream=None):

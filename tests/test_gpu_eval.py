@@ -270,3 +270,88 @@ def test_host_query_on_pinned_buffers_matches_device_path(ctx, torch_cuda):
     ctx.query_points_host(mid, h_pts.numpy(), mfadvr.QUERY_VALUE, out=h_val.numpy())
     np.testing.assert_array_equal(h_val.numpy(), d_out.cpu().numpy()[:, 0])
     ctx.unload_model(mid)
+
+
+@pytest.mark.parametrize("max_ctas", [0, 3])
+def test_async_host_query_matches_device_path(ctx, torch_cuda, max_ctas):
+    """The stream-ordered host query on pinned buffers, on the whole GPU or
+    on a few blocks (each block then strides over many points), must give the
+    device-buffer bits for every query kind, spans too."""
+    from paper_2204_11762_gb300 import mfadvr
+    torch = torch_cuda
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(777)
+    ctrl = rng.normal(size=(23, 18, 20)).astype(np.float32)
+    mid = ctx.load_model(ctrl, 3)
+    k = 100003
+    h_pts = torch.from_numpy(rng.uniform(-0.05, 1.05, size=(k, 3)).astype(np.float32)).pin_memory()
+    d_pts = h_pts.to(dev)
+    s = torch.cuda.Stream(device=dev)
+    widths = {mfadvr.QUERY_VALUE: 1, mfadvr.QUERY_GRADIENT: 3, mfadvr.QUERY_BOTH: 4, mfadvr.QUERY_HESSIAN: 10}
+    for q, wdt in widths.items():
+        h_out = torch.full((k, wdt), float("nan")).pin_memory()
+        h_sp = torch.full((k, 3), -1, dtype=torch.int32).pin_memory()
+        ctx.query_points_host_async(mid, h_pts, k, h_out, q, h_sp, max_ctas=max_ctas, stream=s.cuda_stream)
+        d_out = torch.empty((k, wdt), device=dev)
+        d_sp = torch.empty((k, 3), dtype=torch.int32, device=dev)
+        ctx.query_points(mid, d_pts, k, d_out, q, d_sp)
+        s.synchronize()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(h_out.numpy(), d_out.cpu().numpy())
+        np.testing.assert_array_equal(h_sp.numpy(), d_sp.cpu().numpy())
+    ctx.unload_model(mid)
+
+
+def test_async_host_query_rejects_pageable_buffers(ctx, torch_cuda):
+    from paper_2204_11762_gb300 import mfadvr
+    torch = torch_cuda
+    rng = np.random.default_rng(5)
+    mid = ctx.load_model(rng.normal(size=(8, 8, 8)).astype(np.float32), 2)
+    k = 1000
+    pts = rng.uniform(0, 1, size=(k, 3)).astype(np.float32)
+    h_pts = torch.from_numpy(pts).pin_memory()
+    h_out = torch.empty((k, 4)).pin_memory()
+    with pytest.raises(RuntimeError, match="page-locked"):
+        ctx.query_points_host_async(mid, pts, k, h_out)
+    with pytest.raises(RuntimeError, match="page-locked"):
+        ctx.query_points_host_async(mid, h_pts, k, np.empty((k, 4), dtype=np.float32))
+    with pytest.raises(RuntimeError, match="max_ctas"):
+        ctx.query_points_host_async(mid, h_pts, k, h_out, max_ctas=-1)
+    with pytest.raises(RuntimeError):
+        ctx.query_points_host_async(mid, h_pts, k, h_out, query=5)
+    ctx.query_points_host_async(mid, h_pts, 0, h_out)  # n = 0: no work, no error
+    torch.cuda.synchronize()
+    ctx.unload_model(mid)
+
+
+def test_async_host_query_beside_a_render(ctx, torch_cuda):
+    """A capped host query queued on one stream with a render on another (the
+    end-to-end step): both results equal those of the same calls run alone."""
+    from paper_2204_11762_gb300 import mfadvr, workloads
+    torch = torch_cuda
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(99)
+    ctrl = workloads.gaussian_sum_lattice((48, 40, 44), 3, rng)
+    mid = ctx.load_model(ctrl, 3)
+    k = 1 << 18
+    h_pts = torch.from_numpy(rng.uniform(0, 1, size=(k, 3)).astype(np.float32)).pin_memory()
+    h_out = torch.empty((k, 4)).pin_memory()
+    tf = workloads.transfer_function(rng, 256)
+    prm = {"width": 160, "height": 120, "step": 1 / 512, "max_opacity": 0.99, "shading": 1}
+    cam = workloads.sphere_camera(rng)
+    ref_img = ctx.render_host(mid, cam, prm, tf)
+    d_out = torch.empty((k, 4), device=dev)
+    ctx.eval_points(mid, h_pts.to(dev), k, d_out)
+    torch.cuda.synchronize()
+    ref_out = d_out.cpu().numpy()
+    h_img = torch.empty((120, 160, 4)).pin_memory()
+    sq, sr = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    for cap in (8, 0):
+        h_out.fill_(float("nan"))
+        h_img.fill_(float("nan"))
+        ctx.query_points_host_async(mid, h_pts, k, h_out, mfadvr.QUERY_BOTH, max_ctas=cap, stream=sq.cuda_stream)
+        ctx.render_host(mid, cam, prm, tf, rgba=h_img.numpy(), stream=sr.cuda_stream)
+        sq.synchronize()
+        np.testing.assert_array_equal(h_out.numpy(), ref_out)
+        np.testing.assert_array_equal(h_img.numpy(), ref_img)
+    ctx.unload_model(mid)
