@@ -67,6 +67,24 @@ typedef int32_t mfadvr_status;
  * FP32, accumulates in FP32 and multiplies the result by s. */
 typedef enum { MFADVR_F32 = 0, MFADVR_F16 = 1, MFADVR_BF16 = 2 } mfadvr_dtype;
 
+/* How the render kernels evaluate a model (the point queries always use the
+ * B-spline form).  Within one knot-span cell the model is a polynomial of the
+ * cell's local coordinates; the POWER form stores, per cell, its monomial
+ * coefficients about the cell centre (FP32, computed in FP64 from the basis
+ * pieces at load) and evaluates value and gradient by nested Horner sums:
+ * no basis per sample, and at degree 3 123 multiply-adds on 83 instructions
+ * instead of 192 on 128 plus the basis, for (p+1)^3 floats per cell (at degree 3 and 128^3 control points:
+ * 500 MB beside the 67 MB row array).  It applies to FP32 storage, uniform
+ * knots, non-rational models of degree <= 3; results agree with the B-spline
+ * form to FP32 rounding. */
+typedef enum {
+    MFADVR_FORM_AUTO = 0,    /* POWER where it applies, fits the HBM budget and
+                                takes at most 4 GiB; the B-spline form else   */
+    MFADVR_FORM_BSPLINE = 1, /* the basis and the sum-factorised contraction    */
+    MFADVR_FORM_POWER = 2    /* required: EUNSUPPORTED where it does not apply,
+                                ENOMEM where it does not fit                    */
+} mfadvr_render_form;
+
 /* An MFA model (Sec. 2.3): degree, control-point lattice, knots, and the
  * world box that maps onto the parameter box [0,1]^3. */
 typedef struct {
@@ -89,6 +107,7 @@ typedef struct {
                               the storage type (16-bit: each with its own
                               max-abs scale); two contractions per query
                               make it about half the plain model's speed */
+    int32_t render_form;   /* mfadvr_render_form; 0 (AUTO) when zeroed      */
 } mfadvr_model_desc;
 
 /* Camera in world space (the "Ray Definition" step of Sec. 3.1).  Frame:
@@ -144,7 +163,9 @@ MFADVR_API mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_d
 MFADVR_API mfadvr_status mfadvr_unload_model(mfadvr_ctx *ctx, int32_t model_id);
 
 /* Value range [min P, max P] of the loaded control points (the default TF
- * domain) and the storage scale s.  Any output pointer may be NULL. */
+ * domain), the storage scale s and the model's resident bytes (row arrays,
+ * knot tables and, in the POWER render form, the span polynomials).  Any
+ * output pointer may be NULL. */
 MFADVR_API mfadvr_status mfadvr_model_info(mfadvr_ctx *ctx, int32_t model_id, float *pmin, float *pmax,
                                 float *scale, uint64_t *bytes);
 

@@ -35,6 +35,10 @@ struct Model {
     float wscale = 1.0f;
     uint64_t knot_bytes = 0;
     size_t brk_off[3] = {0, 0, 0}, ih_off[3] = {0, 0, 0}, cell_off[3] = {0, 0, 0}, pc_off[3] = {0, 0, 0};
+    // POWER render form: the span polynomials (layout in mfa_basis.cuh,
+    // PolyCell), null in the B-spline form.
+    void *d_poly = nullptr;
+    uint64_t poly_bytes = 0;
 };
 
 // Device buffer owned by the context, grown on demand (host-buffer calls).

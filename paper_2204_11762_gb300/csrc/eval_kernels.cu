@@ -1,5 +1,6 @@
 // mfadvr_eval_points' launcher (picks the per-degree instantiation of the
-// kernel in eval_kernels.cuh) and the kernel that builds a model's row array.
+// kernel in eval_kernels.cuh) and the kernels that build a model's row array
+// and its span polynomials.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -58,6 +59,60 @@ __global__ void build_rows_kernel(const float *__restrict__ src, void *__restric
     }
 }
 
+// One thread per span cell (i, j, k) of a uniform-knot FP32 model of degree
+// P: the coefficients of the cell's polynomial about its centre (PolyCell in
+// mfa_basis.cuh), A = (Cu x Cv x Cw) applied to the (P+1)^3 control points
+// P(i.., j.., k..) one axis at a time, in FP64, each rounded once to FP32.
+template <int P>
+__global__ void build_poly_kernel(const float *__restrict__ src, float2 *__restrict__ poly, int n0, int n1, int n2)
+{
+    constexpr int K = P + 1, JP = Block<P>::JP, S = PolyCell<P>::kSectors;
+    const int m0 = n0 - P, m1 = n1 - P, m2 = n2 - P;
+    const int64_t cells = static_cast<int64_t>(m0) * m1 * m2;
+    for (int64_t cell = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; cell < cells;
+         cell += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int i = static_cast<int>(cell % m0);
+        const int j = static_cast<int>((cell / m0) % m1);
+        const int k = static_cast<int>(cell / (static_cast<int64_t>(m0) * m1));
+        double cu[K][K], cv[K][K], cw[K][K];
+        centred_pieces<P>(i, m0, cu);
+        centred_pieces<P>(j, m1, cv);
+        centred_pieces<P>(k, m2, cw);
+        double t[K][K][K];  // t[a][s][q] = sum_r cu[r][a] P(i+r, j+s, k+q)
+        for (int q = 0; q < K; ++q)
+            for (int s = 0; s < K; ++s) {
+                const float *row = src + i + static_cast<int64_t>(n0) * (j + s + static_cast<int64_t>(n1) * (k + q));
+                for (int a = 0; a < K; ++a) {
+                    double acc = 0.0;
+                    for (int r = 0; r < K; ++r) acc += cu[r][a] * static_cast<double>(row[r]);
+                    t[a][s][q] = acc;
+                }
+            }
+        double w[K][K][K];  // w[a][b][q] = sum_s cv[s][b] t[a][s][q]
+        for (int a = 0; a < K; ++a)
+            for (int b = 0; b < K; ++b)
+                for (int q = 0; q < K; ++q) {
+                    double acc = 0.0;
+                    for (int s = 0; s < K; ++s) acc += cv[s][b] * t[a][s][q];
+                    w[a][b][q] = acc;
+                }
+        float2 *out = poly + cell * (4 * S);
+        for (int f = 0; f < 4 * S; ++f) {
+            const int c = f / (JP * K), h = (f / K) % JP, a = f % K;
+            float2 pr = make_float2(0.0f, 0.0f);
+            if (f < PolyCell<P>::kPairs) {
+                double lo = 0.0, hi = 0.0;  // A[a][2h][c], A[a][2h+1][c]
+                for (int q = 0; q < K; ++q) {
+                    lo += cw[q][c] * w[a][2 * h][q];
+                    if (2 * h + 1 < K) hi += cw[q][c] * w[a][2 * h + 1][q];
+                }
+                pr = make_float2(static_cast<float>(lo), static_cast<float>(hi));
+            }
+            out[f] = pr;
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t n, float *out, int query,
@@ -72,6 +127,21 @@ cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t
     case 5: return launch_eval_p5(mv, params, n, out, query, spans, stream, max_blocks);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_build_poly(const float *src, void *poly, int p, int n0, int n1, int n2, cudaStream_t stream)
+{
+    const int64_t cells = static_cast<int64_t>(n0 - p) * (n1 - p) * (n2 - p);
+    if (cells <= 0) return cudaSuccess;
+    const int blocks = static_cast<int>((cells + 127) / 128 < 152 * 32 ? (cells + 127) / 128 : 152 * 32);
+    float2 *dst = static_cast<float2 *>(poly);
+    switch (p) {
+    case 1: build_poly_kernel<1><<<blocks, 128, 0, stream>>>(src, dst, n0, n1, n2); break;
+    case 2: build_poly_kernel<2><<<blocks, 128, 0, stream>>>(src, dst, n0, n1, n2); break;
+    case 3: build_poly_kernel<3><<<blocks, 128, 0, stream>>>(src, dst, n0, n1, n2); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_build_rows(const float *src, void *rows, int n0, int n1, int n2, int dtype, float inv_scale,

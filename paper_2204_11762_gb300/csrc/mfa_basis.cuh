@@ -597,6 +597,131 @@ __device__ __forceinline__ void contract(const float Nu[P + 1], const float dNu[
     }
 }
 
+// ---------------------------------------------------------------------------
+// Span polynomials (the POWER render form).  On span cell (i, j, k) the model
+// is a polynomial of the cell's local coordinates; with t = x - 1/2 per axis
+// (the offset from the cell centre),
+//   BasisScale^3 f = sum_{a,b,c} A[a][b][c] tu^a tv^b tw^c,
+//   A[a][b][c] = sum_{r,s,q} Cu[r][a] Cv[s][b] Cw[q][c] P(i+r, j+s, k+q),
+// where C[r][e] is the coefficient of t^e in BasisScale N_r on the span: the
+// pieces of the span's knot pattern (as in the clamped-span tables), shifted
+// to the centre.  A cell stores the pairs (A[a][2h][c], A[a][2h+1][c]) in the
+// order [c][h][a], the last h padded with 0 when P is even, in whole 32-byte
+// sectors: the order of the render kernel's span cache.
+// ---------------------------------------------------------------------------
+template <int P>
+struct PolyCell {
+    static constexpr int JP = Block<P>::JP;
+    static constexpr int kPairs = (P + 1) * JP * (P + 1);
+    static constexpr int kSectors = (kPairs + 3) / 4;
+};
+static_assert(PolyCell<1>::kSectors * 32 == poly_cell_bytes(1) && PolyCell<2>::kSectors * 32 == poly_cell_bytes(2) &&
+                  PolyCell<3>::kSectors * 32 == poly_cell_bytes(3),
+              "span-polynomial cell sizes of host and device differ");
+
+// Coefficients of t^e (t = x - 1/2) of BasisScale<P> N_r on span s of an
+// axis with m uniform clamped spans, in FP64: the span's knot pattern as in
+// make_span_pieces, the pieces from pieces_from_knots, then the Taylor shift
+// x^e = sum_f binom(e, f) 2^(f-e) t^f.
+template <int P>
+__host__ __device__ constexpr void centred_pieces(int s, int m, double (&c)[P + 1][P + 1])
+{
+    const int a = s < P - 1 ? P - 1 - s : 0, b = s + P > m ? s + P - m : 0;
+    double kap[2 * P] = {};
+    for (int j = 1 - P; j <= P; ++j) {
+        const int v = j < -(P - 1 - a) ? -(P - 1 - a) : j;
+        kap[j + P - 1] = v > P - b ? P - b : v;
+    }
+    double x[P + 1][P + 1] = {};
+    pieces_from_knots<P>(kap, BasisScale<P>::value, x);
+    for (int r = 0; r <= P; ++r)
+        for (int f = 0; f <= P; ++f) {
+            double sum = 0.0, binom = 1.0, half = 1.0;  // binom(e, f), 2^(f-e) for e = f, f+1, ...
+            for (int e = f; e <= P; ++e) {
+                sum += x[r][e] * binom * half;
+                binom = binom * (e + 1) / (e + 1 - f);
+                half *= 0.5;
+            }
+            c[r][f] = sum;
+        }
+}
+
+// Loads span cell `cell` of the polynomial array into v[c][h][a] (PolyCell).
+template <int P>
+__device__ __forceinline__ void load_poly(const float *poly, int64_t cell, float2 (&v)[P + 1][Block<P>::JP][P + 1])
+{
+    constexpr int S = PolyCell<P>::kSectors, JP = Block<P>::JP;
+    const float *base = poly + cell * (8 * S);
+    Row q[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) q[k] = row32_at(base, k);
+#pragma unroll
+    for (int f = 0; f < PolyCell<P>::kPairs; ++f) v[f / (JP * (P + 1))][(f / (P + 1)) % JP][f % (P + 1)] = q[f / 4].p[f % 4];
+}
+
+// Value and local gradient (times BasisScale^3, like contract<P, Q>) of a span
+// cell's polynomial at centred coordinates (tu, tv, tw) in [-1/2, 1/2]:
+// Horner's rule in tu on the coefficient pairs (packed, two tv powers per
+// instruction), then in tv for each tw power, then in tw; each level carries
+// the derivative sums the gradient needs (for p(t) = sum A_e t^e, the
+// recurrences p <- p t + A_e and d <- d t + p give p and p').  At degree 3:
+// 40 packed and 43 scalar multiply-adds for value and gradient, 24 packed
+// and 15 scalar for the value alone.
+template <int P, int Q, typename PairAt>
+__device__ __forceinline__ void contract_poly(PairAt pair, float tu, float tv, float tw, float r[4])
+{
+    constexpr int JP = Block<P>::JP;
+    constexpr bool kG = (Q & kQueryGradient) != 0;
+    static_assert(Q == kQueryValue || Q == kQueryBoth, "span polynomials serve value or value+gradient queries");
+    const float2 uu = make_float2(tu, tu);
+    float Fv[P + 1], Fu[P + 1], Fvv[P + 1];  // per tw power: value, d/du and d/dv of the (u, v) polynomial
+#pragma unroll
+    for (int c = 0; c <= P; ++c) {
+        float pv[2 * JP], pu[2 * JP];
+#pragma unroll
+        for (int h = 0; h < JP; ++h) {
+            float2 p = pair(c, h, P), d = p;
+#pragma unroll
+            for (int a = P - 1; a >= 0; --a) {
+                if (kG && a < P - 1) d = __ffma2_rn(d, uu, p);
+                p = __ffma2_rn(p, uu, pair(c, h, a));
+            }
+            pv[2 * h] = p.x;
+            pv[2 * h + 1] = p.y;
+            pu[2 * h] = d.x;
+            pu[2 * h + 1] = d.y;
+        }
+        float q = pv[P], qv = q, qu = pu[P];
+#pragma unroll
+        for (int b = P - 1; b >= 0; --b) {
+            if (kG) {
+                if (b < P - 1) qv = fmaf(qv, tv, q);
+                qu = fmaf(qu, tv, pu[b]);
+            }
+            q = fmaf(q, tv, pv[b]);
+        }
+        Fv[c] = q;
+        Fvv[c] = qv;
+        Fu[c] = qu;
+    }
+    float f = Fv[P], fw = f, fv = Fvv[P], fu = Fu[P];
+#pragma unroll
+    for (int c = P - 1; c >= 0; --c) {
+        if (kG) {
+            if (c < P - 1) fw = fmaf(fw, tw, f);
+            fv = fmaf(fv, tw, Fvv[c]);
+            fu = fmaf(fu, tw, Fu[c]);
+        }
+        f = fmaf(f, tw, Fv[c]);
+    }
+    r[0] = f;
+    if constexpr (kG) {
+        r[1] = fu;
+        r[2] = fv;
+        r[3] = fw;
+    }
+}
+
 // Derivative orders (u, v, w) of the ten outputs of the Hessian query:
 // f, f_u, f_v, f_w, f_uu, f_vv, f_ww, f_uv, f_uw, f_vw.
 __device__ __forceinline__ constexpr int hessian_order(int o, int axis)

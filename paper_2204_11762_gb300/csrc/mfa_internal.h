@@ -30,6 +30,9 @@ struct ModelView {
     int rational;        // 1: rows hold w P, wrows the weights w (NURBS)
     const void *wrows;
     float wscale;        // storage scale of wrows (1 for FP32)
+    // POWER render form: per span cell the monomial coefficients of the
+    // model about the cell centre (PolyCell in mfa_basis.cuh); null otherwise
+    const float *poly;
     int nu;
     int grid[3];  // lookup cells per axis (G = 2m)
     const float *brk[3];
@@ -76,6 +79,15 @@ struct RenderJob {
 };
 static_assert(sizeof(RenderJob) % 8 == 0, "RenderJob is copied in 8-byte words");
 
+// Dispatch key of the render kernels: the storage type, or kPolyForm when
+// the model's span polynomials are evaluated (the POWER render form).
+constexpr int kPolyForm = 16;
+inline int render_form_key(const ModelView &v) { return v.poly ? kPolyForm : v.dtype; }
+
+// Bytes of one span cell's coefficients in the POWER form (degree p <= 3):
+// (p+1) x ceil((p+1)/2) x (p+1) coefficient pairs, in whole 32-byte sectors.
+constexpr int poly_cell_bytes(int p) { return ((p + 1) * ((p + 2) / 2) * (p + 1) * 8 + 31) / 32 * 32; }
+
 // Kernel launchers (asynchronous on `stream`).
 // query is an mfadvr_query: out holds n floats (value), 3n (gradient), n
 // float4 (both) or 10n (Hessian).  The point-query grid is the SM count
@@ -99,6 +111,10 @@ constexpr size_t row_entry_bytes(int) { return 32; }
 // scaling by inv_scale and rounding to the storage type.
 cudaError_t launch_build_rows(const float *src, void *rows, int n0, int n1, int n2, int dtype, float inv_scale,
                               cudaStream_t stream);
+// Span polynomials of a uniform-knot FP32 model of degree p <= 3 from its
+// control points (src, as for launch_build_rows) into poly (m0 m1 m2 cells of
+// poly_cell_bytes(p)).
+cudaError_t launch_build_poly(const float *src, void *poly, int p, int n0, int n1, int n2, cudaStream_t stream);
 
 // Render setup for a caller-owned FP32 lattice outside any context, and the
 // context-free error sink (mfadvr_last_error(NULL)); both in mfadvr_api.cu.

@@ -78,6 +78,7 @@ ModelView view_of(const Model &m)
         v.m[a] = m.n[a] - m.p;
     }
     v.rational = m.rational;
+    v.poly = static_cast<const float *>(m.d_poly);
     v.wrows = m.d_wrows;
     v.wscale = m.wscale;
     v.nu = m.nu;
@@ -266,7 +267,8 @@ int ilog2_u64(uint64_t v)
 TuneKey tune_key(const Model &m, int width, int height)
 {
     const uint64_t pts = static_cast<uint64_t>(m.n[0]) * m.n[1] * m.n[2];
-    return TuneKey(m.p, m.dtype, ilog2_u64(pts), ilog2_u64(static_cast<uint64_t>(width) * height));
+    return TuneKey(m.p, m.d_poly ? kPolyForm : m.dtype, ilog2_u64(pts),
+                   ilog2_u64(static_cast<uint64_t>(width) * height));
 }
 
 // Launch shape from the tuning table, if this key has been tuned.
@@ -297,17 +299,18 @@ std::vector<BatchGroup> pack_jobs(const RenderJob *jobs, int n, RenderJob *dst)
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     auto key = [&](int a) {
-        return std::make_tuple(jobs[a].mv.p, jobs[a].mv.dtype, jobs[a].rs.shading != 0, jobs[a].mv.nu != 0,
-                               jobs[a].mv.rational != 0);
+        return std::make_tuple(jobs[a].mv.p, render_form_key(jobs[a].mv), jobs[a].rs.shading != 0,
+                               jobs[a].mv.nu != 0, jobs[a].mv.rational != 0);
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
     std::vector<BatchGroup> groups;
     for (int k = 0; k < n; ++k) {
         RenderJob jb = jobs[order[k]];
         const int grad = jb.rs.shading != 0 ? 1 : 0, nu = jb.mv.nu != 0 ? 1 : 0, rat = jb.mv.rational != 0 ? 1 : 0;
-        if (groups.empty() || groups.back().p != jb.mv.p || groups.back().dtype != jb.mv.dtype ||
+        const int form = render_form_key(jb.mv);
+        if (groups.empty() || groups.back().p != jb.mv.p || groups.back().dtype != form ||
             groups.back().grad != grad || groups.back().nu != nu || groups.back().rat != rat)
-            groups.push_back({jb.mv.p, jb.mv.dtype, grad, nu, rat, k, 0, 0});
+            groups.push_back({jb.mv.p, form, grad, nu, rat, k, 0, 0});
         BatchGroup &gr = groups.back();
         const int tw = 1 << jb.rs.tile_w_log2, th = 32 / tw;
         jb.tiles_x = (jb.rs.width + tw - 1) / tw;
@@ -634,6 +637,10 @@ mfadvr_status query_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_
 
 }  // namespace
 
+// Largest span-polynomial array the AUTO render form builds (MFADVR_FORM_POWER
+// builds any size within the HBM budget).
+constexpr uint64_t kAutoPolyBytes = uint64_t(4) << 30;
+
 extern "C" {
 
 mfadvr_status mfadvr_create(mfadvr_ctx **out, int device, uint64_t hbm_budget_bytes)
@@ -664,6 +671,7 @@ mfadvr_status mfadvr_destroy(mfadvr_ctx *ctx)
             if (kv.second.d_rows) cudaFree(kv.second.d_rows);
             if (kv.second.d_knots) cudaFree(kv.second.d_knots);
             if (kv.second.d_wrows) cudaFree(kv.second.d_wrows);
+            if (kv.second.d_poly) cudaFree(kv.second.d_poly);
         }
         if (ctx->counters) cudaFree(ctx->counters);
         if (ctx->d_jobs) cudaFree(ctx->d_jobs);
@@ -701,6 +709,8 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
         return fail(ctx, MFADVR_EUNSUPPORTED, "degree above %d", MFADVR_MAX_DEGREE);
     if (desc->degree[0] != desc->degree[1] || desc->degree[0] != desc->degree[2])
         return fail(ctx, MFADVR_EUNSUPPORTED, "degrees must be equal on the three axes");
+    if (desc->render_form < MFADVR_FORM_AUTO || desc->render_form > MFADVR_FORM_POWER)
+        return fail(ctx, MFADVR_EINVAL, "unknown render form %d", static_cast<int>(desc->render_form));
     for (int a = 0; a < 3; ++a) {
         if (!desc->knots[a]) continue;
         const std::string why = knot_problem(desc->knots[a], desc->ncp[a], desc->degree[a]);
@@ -766,6 +776,22 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
         return fail(ctx, MFADVR_ENOMEM, "model of %llu bytes exceeds the HBM budget (%llu of %llu used)",
                     static_cast<unsigned long long>(m.bytes), static_cast<unsigned long long>(ctx->used),
                     static_cast<unsigned long long>(ctx->budget));
+    // POWER render form: span polynomials beside the row array, where the
+    // model allows them (AUTO: and where they fit the budget).
+    const bool poly_ok = m.dtype == MFADVR_F32 && !m.nu && !m.rational && m.p <= 3;
+    const uint64_t poly_b = poly_ok ? static_cast<uint64_t>(m.n[0] - m.p) * (m.n[1] - m.p) * (m.n[2] - m.p) *
+                                          static_cast<uint64_t>(poly_cell_bytes(m.p))
+                                    : 0;
+    if (desc->render_form == MFADVR_FORM_POWER && !poly_ok)
+        return fail(ctx, MFADVR_EUNSUPPORTED,
+                    "the power render form needs FP32 storage, uniform knots, no weights and degree <= 3");
+    const bool poly_fits = !ctx->budget || ctx->used + m.bytes + poly_b <= ctx->budget;
+    if (desc->render_form == MFADVR_FORM_POWER && !poly_fits)
+        return fail(ctx, MFADVR_ENOMEM, "span polynomials of %llu bytes exceed the HBM budget",
+                    static_cast<unsigned long long>(poly_b));
+    const bool want_poly = poly_ok && poly_fits &&
+                           (desc->render_form == MFADVR_FORM_POWER ||
+                            (desc->render_form == MFADVR_FORM_AUTO && poly_b <= kAutoPolyBytes));
 
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
@@ -803,12 +829,26 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
             e = launch_build_rows(static_cast<const float *>(tmp), m.d_wrows, m.n[0], m.n[1], m.n[2], m.dtype,
                                   1.0f / m.wscale, nullptr);
     }
+    if (e == cudaSuccess && want_poly) {
+        // AUTO drops to the B-spline form when the allocation fails
+        const cudaError_t ep = cudaMalloc(&m.d_poly, poly_b);
+        if (ep == cudaSuccess) {
+            m.poly_bytes = poly_b;
+            m.bytes += poly_b;
+            e = launch_build_poly(static_cast<const float *>(tmp), m.d_poly, m.p, m.n[0], m.n[1], m.n[2], nullptr);
+        } else {
+            cudaGetLastError();
+            m.d_poly = nullptr;
+            if (desc->render_form == MFADVR_FORM_POWER) e = ep;
+        }
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) {
         cudaFree(m.d_rows);
         if (m.d_knots) cudaFree(m.d_knots);
         if (m.d_wrows) cudaFree(m.d_wrows);
+        if (m.d_poly) cudaFree(m.d_poly);
         return cuda_fail(ctx, e, "model upload");
     }
     const int32_t id = ctx->next_id++;
@@ -828,6 +868,7 @@ mfadvr_status mfadvr_unload_model(mfadvr_ctx *ctx, int32_t model_id)
     cudaFree(m->d_rows);
     if (m->d_knots) cudaFree(m->d_knots);
     if (m->d_wrows) cudaFree(m->d_wrows);
+    if (m->d_poly) cudaFree(m->d_poly);
     ctx->used -= m->bytes;
     ctx->models.erase(model_id);
     return MFADVR_OK;

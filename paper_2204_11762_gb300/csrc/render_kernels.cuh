@@ -76,6 +76,11 @@ struct LaneRay {
     float r[4];                  // query of sample sf - 1, not yet composited
 };
 
+// Storage tag of the POWER render form: the lane caches its span cell's
+// polynomial coefficients (FP32 pairs, PolyCell in mfa_basis.cuh) and
+// evaluates them by Horner's rule; no basis per sample.
+struct PolyF32 {};
+
 // Cached span block: FP32 pairs for FP32 storage; for 16-bit storage the
 // stored pairs themselves (one 32-bit register each, half the registers),
 // converted to FP32 as the contraction uses them.
@@ -232,12 +237,44 @@ __device__ __forceinline__ float lg2_approx(float x)
 // model, the value f = A / W and its gradient (grad A - f grad W) / W from the
 // contractions of w P and of w.  Returns true when the ray is finished
 // (pixel written).
+// Loads the span block whose first row entry is `base` into the lane's cache
+// (and, for a rational model, the weights' block).
+template <int P, typename T, bool R>
+__device__ __forceinline__ void reload_block(const ModelView &mv, int base, SpanCache<P, T, R> &cache)
+{
+    constexpr int JP = Block<P>::JP;
+    typename Entries<P, T>::E q[P + 1][Entries<P, T>::JE][Block<P>::IR];
+    load_block<P, T>(mv.rows, base, mv.n[0], mv.n01, q);
+#pragma unroll
+    for (int k = 0; k <= P; ++k)
+#pragma unroll
+        for (int jp = 0; jp < JP; ++jp)
+#pragma unroll
+            for (int i = 0; i <= P; ++i) {
+                if constexpr (CacheElem<T>::kPacked) cache.v[k][jp][i] = block_word<P, T>(q, k, jp, i);
+                else cache.v[k][jp][i] = block_pair<P, T>(q, k, jp, i);
+            }
+    if constexpr (R) {
+        load_block<P, T>(mv.wrows, base, mv.n[0], mv.n01, q);
+#pragma unroll
+        for (int k = 0; k <= P; ++k)
+#pragma unroll
+            for (int jp = 0; jp < JP; ++jp)
+#pragma unroll
+                for (int i = 0; i <= P; ++i) {
+                    if constexpr (CacheElem<T>::kPacked) cache.w[k][jp][i] = block_word<P, T>(q, k, jp, i);
+                    else cache.w[k][jp][i] = block_pair<P, T>(q, k, jp, i);
+                }
+    }
+}
+
 template <int P, typename T, bool G, bool NU, bool R, typename Tf>
 __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSetup &rs, const Tf &tf, LaneRay &ray,
                                             SpanCache<P, T, R> &cache)
 {
-    constexpr int JP = Block<P>::JP;
     constexpr bool kCache = SpanCache<P, T, R>::kOn;
+    constexpr bool kPoly = std::is_same<T, PolyF32>::value;
+    static_assert(!kPoly || (P <= 3 && !NU && !R && kCache), "span polynomials: degree <= 3, uniform, plain");
     const float s = ray.sf;
 
     // ---- span of sample s; positions are clamped to the lattice only when
@@ -278,37 +315,21 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
                 ray.kk[a] = static_cast<int>(ray.kf[a]);
             }
         }
-        ray.base = ray.kk[0] + mv.n[0] * ray.kk[1] + mv.n01 * ray.kk[2];
-        ray.interior = span_interior<P>(ray.kk[0], mv.m[0]) && span_interior<P>(ray.kk[1], mv.m[1]) &&
-                       span_interior<P>(ray.kk[2], mv.m[2]);
-        if constexpr (kCache) {
-            typename Entries<P, T>::E q[P + 1][Entries<P, T>::JE][Block<P>::IR];
-            load_block<P, T>(mv.rows, ray.base, mv.n[0], mv.n01, q);
-#pragma unroll
-            for (int k = 0; k <= P; ++k)
-#pragma unroll
-                for (int jp = 0; jp < JP; ++jp)
-#pragma unroll
-                    for (int i = 0; i <= P; ++i) {
-                        if constexpr (CacheElem<T>::kPacked) cache.v[k][jp][i] = block_word<P, T>(q, k, jp, i);
-                        else cache.v[k][jp][i] = block_pair<P, T>(q, k, jp, i);
-                    }
-            if constexpr (R) {
-                load_block<P, T>(mv.wrows, ray.base, mv.n[0], mv.n01, q);
-#pragma unroll
-                for (int k = 0; k <= P; ++k)
-#pragma unroll
-                    for (int jp = 0; jp < JP; ++jp)
-#pragma unroll
-                        for (int i = 0; i <= P; ++i) {
-                            if constexpr (CacheElem<T>::kPacked) cache.w[k][jp][i] = block_word<P, T>(q, k, jp, i);
-                            else cache.w[k][jp][i] = block_pair<P, T>(q, k, jp, i);
-                        }
-            }
+        if constexpr (kPoly) {
+            const int64_t cell =
+                ray.kk[0] + static_cast<int64_t>(mv.m[0]) * (ray.kk[1] + static_cast<int64_t>(mv.m[1]) * ray.kk[2]);
+            load_poly<P>(mv.poly, cell, cache.v);
+        } else {
+            ray.base = ray.kk[0] + mv.n[0] * ray.kk[1] + mv.n01 * ray.kk[2];
+            ray.interior = span_interior<P>(ray.kk[0], mv.m[0]) && span_interior<P>(ray.kk[1], mv.m[1]) &&
+                           span_interior<P>(ray.kk[2], mv.m[2]);
+            if constexpr (kCache) reload_block<P, T, R>(mv, ray.base, cache);
         }
     }
     float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
-    if constexpr (NU) {
+    if constexpr (kPoly) {
+        // no basis: the cell's polynomial is evaluated directly below
+    } else if constexpr (NU) {
         // local coordinate on the span, basis from the span's pieces
 #pragma unroll
         for (int a = 0; a < 3; ++a) x[a] = (x[a] - ray.lo[a]) * ray.ih[a];
@@ -381,7 +402,10 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
 
     // ---- query of sample s (composited by the next iteration) -------------
     constexpr int Q = G ? kQueryBoth : kQueryValue;
-    if constexpr (kCache) {
+    if constexpr (kPoly) {
+        contract_poly<P, Q>([&](int k, int jp, int i) { return cache.v[k][jp][i]; }, x[0] - 0.5f, x[1] - 0.5f,
+                            x[2] - 0.5f, ray.r);
+    } else if constexpr (kCache) {
         contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return cache.pair(k, jp, i); }, ray.r);
     } else {
         const int n0 = mv.n[0], n01 = mv.n01, base = ray.base;
@@ -640,6 +664,15 @@ template <int P, template <int, typename, bool, bool, bool> class F, typename...
 cudaError_t dispatch_degree(int dtype, bool grad, bool nu, bool rat, A... args)
 {
     switch (dtype) {
+    case kPolyForm:
+        // span polynomials exist only for uniform-knot plain models of degree <= 3
+        if constexpr (P <= 3) {
+            if (nu || rat) return cudaErrorInvalidValue;
+            return grad ? F<P, PolyF32, true, false, false>::run(args...)
+                        : F<P, PolyF32, false, false, false>::run(args...);
+        } else {
+            return cudaErrorInvalidValue;
+        }
     case MFADVR_F32: return dispatch_flags<P, float, F>(grad, nu, rat, args...);
     case MFADVR_F16: return dispatch_flags<P, __half, F>(grad, nu, rat, args...);
     case MFADVR_BF16: return dispatch_flags<P, __nv_bfloat16, F>(grad, nu, rat, args...);
@@ -654,8 +687,8 @@ cudaError_t dispatch_degree(int dtype, bool grad, bool nu, bool rat, A... args)
     cudaError_t launch_render_p##PP(const ModelView &mv, const RenderSetup &rs, int *counter,                 \
                                     cudaStream_t stream)                                                     \
     {                                                                                                        \
-        return dispatch_degree<PP, RenderOne>(mv.dtype, rs.shading != 0, mv.nu != 0, mv.rational != 0, &mv, &rs, \
-                                               counter, stream);                                             \
+        return dispatch_degree<PP, RenderOne>(render_form_key(mv), rs.shading != 0, mv.nu != 0, mv.rational != 0, \
+                                               &mv, &rs, counter, stream);                                    \
     }                                                                                                        \
     cudaError_t launch_render_batch_p##PP(int dtype, int grad, int nu, int rat, const RenderJob *jobs_dev,     \
                                           int njobs, int total_tiles, int ctas_per_sm, int *counter,           \

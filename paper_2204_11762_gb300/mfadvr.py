@@ -20,6 +20,8 @@ from . import build as _build
 
 F32, F16, BF16 = 0, 1, 2
 QUERY_VALUE, QUERY_GRADIENT, QUERY_BOTH, QUERY_HESSIAN = 1, 2, 3, 4
+# mfadvr_render_form
+FORM_AUTO, FORM_BSPLINE, FORM_POWER = 0, 1, 2
 _DTYPES = {"f32": F32, "float32": F32, "f16": F16, "float16": F16, "bf16": BF16, "bfloat16": BF16}
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTFOUND, ETIMEOUT, EBUSY, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
@@ -47,7 +49,7 @@ class ModelDesc(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int32 * 3), ("ncp", ctypes.c_int32 * 3),
                 ("box_min", ctypes.c_float * 3), ("box_max", ctypes.c_float * 3),
                 ("ctrl", ctypes.c_void_p), ("knots", ctypes.c_void_p * 3), ("storage", ctypes.c_int32),
-                ("weights", ctypes.c_void_p)]
+                ("weights", ctypes.c_void_p), ("render_form", ctypes.c_int32)]
 
 
 class Camera(ctypes.Structure):
@@ -259,11 +261,12 @@ class Context:
 
     # -- model store ------------------------------------------------------
     def load_model(self, ctrl, degree, storage="f32", box_min=(0.0, 0.0, 0.0), box_max=(1.0, 1.0, 1.0),
-                   knots=None, weights=None) -> int:
+                   knots=None, weights=None, render_form=FORM_AUTO) -> int:
         """ctrl: float32 array (n_w, n_v, n_u), u fastest in memory.  knots:
         None (uniform) or three entries, each None or n_d + p + 1 clamped knots
         (u, v, w order).  weights: None or positive weights shaped like ctrl
-        (a rational model)."""
+        (a rational model).  render_form: FORM_AUTO, FORM_BSPLINE or FORM_POWER
+        (span polynomials for the render kernels)."""
         ctrl = np.ascontiguousarray(ctrl, dtype=np.float32)
         if ctrl.ndim != 3:
             raise ValueError("ctrl must be a 3-D array (n_w, n_v, n_u)")
@@ -287,6 +290,7 @@ class Context:
                 raise ValueError("weights must have the shape of ctrl")
             keep.append(w)
             d.weights = w.ctypes.data
+        d.render_form = int(render_form)
         mid = ctypes.c_int32(-1)
         self._check(self._L.mfadvr_load_model(self._h, ctypes.byref(d), ctypes.byref(mid)))
         return mid.value

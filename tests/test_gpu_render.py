@@ -54,16 +54,17 @@ def test_small_marschner_lobb_workload(ctx, torch_cuda, orc):
     ctx.unload_model(mid)
 
 
+@pytest.mark.parametrize("form", [0, 1])  # AUTO (span polynomials up to degree 3), B-spline
 @pytest.mark.parametrize("p,n,W,H,shading", [(1, 4, 4, 4, 0), (2, 5, 8, 8, 1), (3, 6, 8, 8, 1), (3, 4, 5, 7, 0),
                                              (4, 7, 9, 6, 1), (5, 8, 6, 9, 1)])
-def test_tiny_images(ctx, torch_cuda, orc, p, n, W, H, shading):
+def test_tiny_images(ctx, torch_cuda, orc, p, n, W, H, shading, form):
     from paper_2204_11762_gb300 import workloads
     rng = np.random.default_rng(200 + p * 3 + n)
     ctrl = rng.uniform(0, 1, size=(n, n + 1, n + 2)).astype(np.float32)
     tf = workloads.transfer_function(rng, 32)
     cam = _persp((1.9, 1.4, 1.7))
     prm = {"width": W, "height": H, "step": 1 / 48, "max_opacity": 0.99, "shading": shading}
-    mid = ctx.load_model(ctrl, p)
+    mid = ctx.load_model(ctrl, p, render_form=form)
     img, ns = _render(ctx, torch_cuda, mid, cam, prm, tf)
     ref = orc.render(ctrl, p, cam, dict(prm, tf=tf))
     assert_render_parity(img, ns, ref)
@@ -73,7 +74,8 @@ def test_tiny_images(ctx, torch_cuda, orc, p, n, W, H, shading):
 @pytest.mark.parametrize("case", ["ortho_oblique", "inside_box", "opacity_correction", "tf_size_1",
                                   "no_ert", "ragged", "world_box", "high_opacity", "explicit_tf_range",
                                   "shading_off"])
-def test_render_variants(ctx, torch_cuda, orc, case):
+@pytest.mark.parametrize("form", [0, 1])  # AUTO (span polynomials), B-spline
+def test_render_variants(ctx, torch_cuda, orc, case, form):
     from paper_2204_11762_gb300 import workloads
     import zlib
     rng = np.random.default_rng(zlib.crc32(case.encode()))
@@ -106,7 +108,7 @@ def test_render_variants(ctx, torch_cuda, orc, case):
         prm["tf_lo"], prm["tf_hi"] = -1.0, 1.5
     elif case == "shading_off":
         prm["shading"] = 0
-    mid = ctx.load_model(ctrl, p, box_min=box[0], box_max=box[1])
+    mid = ctx.load_model(ctrl, p, box_min=box[0], box_max=box[1], render_form=form)
     img, ns = _render(ctx, torch_cuda, mid, cam, prm, tf)
     ref = orc.render(ctrl, p, cam, dict(prm, tf=tf), box_min=box[0], box_max=box[1])
     assert_render_parity(img, ns, ref)
