@@ -30,13 +30,17 @@ sys.path.insert(0, ROOT)
 # DRAM bytes (read + write) of one render_kernel<3, float> launch on the
 # 128^3 workload from one ncu capture (profiles/render_kernel_gauss128_p3_persp1024.md),
 # valid only for the kernel sources it was taken on.
-RENDER_TRAFFIC = {"sources_sha256_16": "07c236724c1d2827", "bytes": 78253568}
+RENDER_TRAFFIC = {"sources_sha256_16": "13dd54b7becdad51", "bytes": 517646848}
 RENDER_SOURCES = ("paper_2204_11762_gb300/csrc/render_kernels.cuh", "paper_2204_11762_gb300/csrc/mfa_basis.cuh",
                   "paper_2204_11762_gb300/csrc/mfa_internal.h")
 
 METRIC = "MFA value+grad samples/s"
 UNIT = "samples/s"
 C_FMA = {p: 2 * (p + 1) ** 3 + 3 * (p + 1) ** 2 + 4 * (p + 1) for p in range(1, 6)}
+# multiply-adds the power render form executes per value+gradient sample
+# (Horner in u on packed pairs, padded when p is even, then in v and w)
+POLY_FMA = {p: 2 * (p + 1) * ((p + 2) // 2) * (2 * p - 1) + (p + 1) * (3 * p - 1) + 4 * p - 1 for p in (1, 2, 3)}
+FORMS = {"auto": 0, "bspline": 1, "power": 2}
 FP32_LANES_PER_SM = 128
 
 
@@ -47,6 +51,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--form", default="auto", choices=sorted(FORMS),
+                    help="render form of the model: span polynomials (power) or the B-spline basis")
     ap.add_argument("--workload", default="gauss128",
                     choices=["gauss128", "noise512", "multi16", "serve48", "sweep", "variants"],
                     help="gauss128: 128^3 degree-3 render + 2^24 points (default); "
@@ -234,7 +240,9 @@ def run_ours(args, wl):
 
     ctx = mfadvr.Context(local)
     p = wl["degree"]
-    mid = ctx.load_model(wl["ctrl"], p, storage=args.storage)
+    mid = ctx.load_model(wl["ctrl"], p, storage=args.storage, render_form=FORMS[args.form])
+    rows_bytes = int(np.prod(wl["ctrl"].shape)) * 32
+    form = "power" if ctx.model_info(mid)["bytes"] > rows_bytes else "bspline"
     pts = wl["points"]
     npts = pts.shape[0]
     prm = wl["params"]
@@ -300,9 +308,16 @@ def run_ours(args, wl):
     dominant = "render" if r_mean >= e_mean else "eval_points"
     if dominant == "render":
         roof = {"kernel": "render_kernel", "bound": "alu", "achieved": render_tflops, "peak": fma_peak_tflops,
-                "unit": "TFLOP/s", "frac": render_tflops / fma_peak_tflops, "traffic": render_traffic(),
+                "unit": "TFLOP/s", "frac": render_tflops / fma_peak_tflops,
+                "traffic": render_traffic() if form == "power" else None,
                 "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 FLOP x {sm_max_mhz:.0f} MHz",
-                "per_unit": f"{C_FMA[p]} FMA per sample (sum-factorised contraction, degree {p})"}
+                "per_unit": f"{C_FMA[p]} FMA per sample (sum-factorised contraction, degree {p})",
+                "render_form": form}
+        if form == "power":
+            ex = render_samples * POLY_FMA[p] * 2 / (r_mean / 1000.0) / 1e12
+            roof["executed"] = {"fma_per_sample": POLY_FMA[p], "tflops": ex, "frac": ex / fma_peak_tflops,
+                                "note": "the power form evaluates each cell's polynomial by Horner sums: "
+                                        "an algebraic shortcut, so achieved/frac keep the algorithmic count"}
     else:
         roof = {"kernel": "eval_points_kernel", "bound": "alu", "achieved": eval_tflops, "peak": fma_peak_tflops,
                 "unit": "TFLOP/s", "frac": eval_tflops / fma_peak_tflops, "traffic": None,
@@ -325,6 +340,8 @@ def run_ours(args, wl):
                             "hbm_frac": (eval_io_bytes / (e_mean / 1000.0) / 1e9) / peaks["hbm_gbs"]
                             if "hbm_gbs" in peaks else None},
             "roofline": roof, "clocks": clk, "wall_s": wall1 - wall0}
+    line["config"]["render_form"] = (f"{form}: span polynomials, Horner sums" if form == "power" else
+                                     f"{form}: basis and sum-factorised contraction")
     line["config"]["launch"] = (f"{tuned['tile_w']}x{32 // tuned['tile_w']} ray tiles, "
                                 f"{tuned['ctas_per_sm'] or 'max'} CTAs/SM (library autotuner, untimed set-up)")
 
@@ -667,7 +684,8 @@ def run_sweep(args):
 def run_variants(args):
     """The default workload (128^3 Gaussian sum, 1024^2 frame at step 1/1024,
     2^24 points) on each model and query variant the library supports: FP32 /
-    FP16 / BF16 storage, shading off (value-only kernel), graded non-uniform
+    FP16 / BF16 storage, FP32 in both render forms (span polynomials, the
+    default here, and the B-spline basis), shading off (value-only kernel), graded non-uniform
     knots (span widths U[0.2, 1.8] normalised, all axes), rational weights
     U[0.5, 2], and the value-only, gradient-only and Hessian point queries.
     Render and query times are medians of CUDA-event timings with the L2
@@ -708,9 +726,10 @@ def run_variants(args):
         torch.cuda.synchronize(dev)
         return statistics.median(a.elapsed_time(b) for a, b in ev)
 
-    variants = [("f32", {}, 1), ("f16", {"storage": "f16"}, 1), ("bf16", {"storage": "bf16"}, 1),
-                ("f32 shading off", {}, 0), ("f32 graded knots", {"knots": knots}, 1),
-                ("f32 rational", {"weights": weights}, 1)]
+    variants = [("f32", {}, 1), ("f32 B-spline form", {"render_form": FORMS["bspline"]}, 1),
+                ("f16", {"storage": "f16"}, 1), ("bf16", {"storage": "bf16"}, 1),
+                ("f32 shading off", {}, 0), ("f32 B-spline form, shading off", {"render_form": FORMS["bspline"]}, 0),
+                ("f32 graded knots", {"knots": knots}, 1), ("f32 rational", {"weights": weights}, 1)]
     table, launches = {}, 0
     clocks = ClockSampler(local)
     clocks.start()

@@ -659,20 +659,17 @@ __device__ __forceinline__ void load_poly(const float *poly, int64_t cell, float
     for (int f = 0; f < PolyCell<P>::kPairs; ++f) v[f / (JP * (P + 1))][(f / (P + 1)) % JP][f % (P + 1)] = q[f / 4].p[f % 4];
 }
 
-// Value and local gradient (times BasisScale^3, like contract<P, Q>) of a span
-// cell's polynomial at centred coordinates (tu, tv, tw) in [-1/2, 1/2]:
-// Horner's rule in tu on the coefficient pairs (packed, two tv powers per
-// instruction), then in tv for each tw power, then in tw; each level carries
-// the derivative sums the gradient needs (for p(t) = sum A_e t^e, the
-// recurrences p <- p t + A_e and d <- d t + p give p and p').  At degree 3:
-// 40 packed and 43 scalar multiply-adds for value and gradient, 24 packed
-// and 15 scalar for the value alone.
-template <int P, int Q, typename PairAt>
+// Value and local gradient (times BasisScale^3, like contract<P, kQueryBoth>)
+// of a span cell's polynomial at centred coordinates (tu, tv, tw) in
+// [-1/2, 1/2]: Horner's rule in tu on the coefficient pairs (packed, two tv
+// powers per instruction), then in tv for each tw power, then in tw; each
+// level carries the derivative sums the gradient needs (for p(t) = sum A_e
+// t^e, the recurrences p <- p t + A_e and d <- d t + p give p and p').  At
+// degree 3: 40 packed and 43 scalar multiply-adds.
+template <int P, typename PairAt>
 __device__ __forceinline__ void contract_poly(PairAt pair, float tu, float tv, float tw, float r[4])
 {
     constexpr int JP = Block<P>::JP;
-    constexpr bool kG = (Q & kQueryGradient) != 0;
-    static_assert(Q == kQueryValue || Q == kQueryBoth, "span polynomials serve value or value+gradient queries");
     const float2 uu = make_float2(tu, tu);
     float Fv[P + 1], Fu[P + 1], Fvv[P + 1];  // per tw power: value, d/du and d/dv of the (u, v) polynomial
 #pragma unroll
@@ -683,7 +680,7 @@ __device__ __forceinline__ void contract_poly(PairAt pair, float tu, float tv, f
             float2 p = pair(c, h, P), d = p;
 #pragma unroll
             for (int a = P - 1; a >= 0; --a) {
-                if (kG && a < P - 1) d = __ffma2_rn(d, uu, p);
+                if (a < P - 1) d = __ffma2_rn(d, uu, p);
                 p = __ffma2_rn(p, uu, pair(c, h, a));
             }
             pv[2 * h] = p.x;
@@ -694,10 +691,8 @@ __device__ __forceinline__ void contract_poly(PairAt pair, float tu, float tv, f
         float q = pv[P], qv = q, qu = pu[P];
 #pragma unroll
         for (int b = P - 1; b >= 0; --b) {
-            if (kG) {
-                if (b < P - 1) qv = fmaf(qv, tv, q);
-                qu = fmaf(qu, tv, pu[b]);
-            }
+            if (b < P - 1) qv = fmaf(qv, tv, q);
+            qu = fmaf(qu, tv, pu[b]);
             q = fmaf(q, tv, pv[b]);
         }
         Fv[c] = q;
@@ -707,19 +702,15 @@ __device__ __forceinline__ void contract_poly(PairAt pair, float tu, float tv, f
     float f = Fv[P], fw = f, fv = Fvv[P], fu = Fu[P];
 #pragma unroll
     for (int c = P - 1; c >= 0; --c) {
-        if (kG) {
-            if (c < P - 1) fw = fmaf(fw, tw, f);
-            fv = fmaf(fv, tw, Fvv[c]);
-            fu = fmaf(fu, tw, Fu[c]);
-        }
+        if (c < P - 1) fw = fmaf(fw, tw, f);
+        fv = fmaf(fv, tw, Fvv[c]);
+        fu = fmaf(fu, tw, Fu[c]);
         f = fmaf(f, tw, Fv[c]);
     }
     r[0] = f;
-    if constexpr (kG) {
-        r[1] = fu;
-        r[2] = fv;
-        r[3] = fw;
-    }
+    r[1] = fu;
+    r[2] = fv;
+    r[3] = fw;
 }
 
 // Derivative orders (u, v, w) of the ten outputs of the Hessian query:

@@ -80,9 +80,11 @@ struct RenderJob {
 static_assert(sizeof(RenderJob) % 8 == 0, "RenderJob is copied in 8-byte words");
 
 // Dispatch key of the render kernels: the storage type, or kPolyForm when
-// the model's span polynomials are evaluated (the POWER render form).
+// the model's span polynomials are evaluated (the POWER render form, for
+// shaded renders: without the gradient the B-spline value-only kernel on the
+// row array is the faster one, the polynomial cells being 8x the rows' bytes).
 constexpr int kPolyForm = 16;
-inline int render_form_key(const ModelView &v) { return v.poly ? kPolyForm : v.dtype; }
+inline int render_form_key(const ModelView &v, int shading) { return v.poly && shading ? kPolyForm : v.dtype; }
 
 // Bytes of one span cell's coefficients in the POWER form (degree p <= 3):
 // (p+1) x ceil((p+1)/2) x (p+1) coefficient pairs, in whole 32-byte sectors.

@@ -299,15 +299,16 @@ std::vector<BatchGroup> pack_jobs(const RenderJob *jobs, int n, RenderJob *dst)
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     auto key = [&](int a) {
-        return std::make_tuple(jobs[a].mv.p, render_form_key(jobs[a].mv), jobs[a].rs.shading != 0,
-                               jobs[a].mv.nu != 0, jobs[a].mv.rational != 0);
+        const RenderJob &j = jobs[a];
+        return std::make_tuple(j.mv.p, render_form_key(j.mv, j.rs.shading), j.rs.shading != 0, j.mv.nu != 0,
+                               j.mv.rational != 0);
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
     std::vector<BatchGroup> groups;
     for (int k = 0; k < n; ++k) {
         RenderJob jb = jobs[order[k]];
         const int grad = jb.rs.shading != 0 ? 1 : 0, nu = jb.mv.nu != 0 ? 1 : 0, rat = jb.mv.rational != 0 ? 1 : 0;
-        const int form = render_form_key(jb.mv);
+        const int form = render_form_key(jb.mv, jb.rs.shading);
         if (groups.empty() || groups.back().p != jb.mv.p || groups.back().dtype != form ||
             groups.back().grad != grad || groups.back().nu != nu || groups.back().rat != rat)
             groups.push_back({jb.mv.p, form, grad, nu, rat, k, 0, 0});

@@ -274,7 +274,8 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
 {
     constexpr bool kCache = SpanCache<P, T, R>::kOn;
     constexpr bool kPoly = std::is_same<T, PolyF32>::value;
-    static_assert(!kPoly || (P <= 3 && !NU && !R && kCache), "span polynomials: degree <= 3, uniform, plain");
+    static_assert(!kPoly || (P <= 3 && G && !NU && !R && kCache),
+                  "span polynomials: shaded renders of uniform plain models of degree <= 3");
     const float s = ray.sf;
 
     // ---- span of sample s; positions are clamped to the lattice only when
@@ -403,8 +404,8 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
     // ---- query of sample s (composited by the next iteration) -------------
     constexpr int Q = G ? kQueryBoth : kQueryValue;
     if constexpr (kPoly) {
-        contract_poly<P, Q>([&](int k, int jp, int i) { return cache.v[k][jp][i]; }, x[0] - 0.5f, x[1] - 0.5f,
-                            x[2] - 0.5f, ray.r);
+        contract_poly<P>([&](int k, int jp, int i) { return cache.v[k][jp][i]; }, x[0] - 0.5f, x[1] - 0.5f,
+                         x[2] - 0.5f, ray.r);
     } else if constexpr (kCache) {
         contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return cache.pair(k, jp, i); }, ray.r);
     } else {
@@ -667,9 +668,8 @@ cudaError_t dispatch_degree(int dtype, bool grad, bool nu, bool rat, A... args)
     case kPolyForm:
         // span polynomials exist only for uniform-knot plain models of degree <= 3
         if constexpr (P <= 3) {
-            if (nu || rat) return cudaErrorInvalidValue;
-            return grad ? F<P, PolyF32, true, false, false>::run(args...)
-                        : F<P, PolyF32, false, false, false>::run(args...);
+            if (nu || rat || !grad) return cudaErrorInvalidValue;
+            return F<P, PolyF32, true, false, false>::run(args...);
         } else {
             return cudaErrorInvalidValue;
         }
@@ -687,8 +687,8 @@ cudaError_t dispatch_degree(int dtype, bool grad, bool nu, bool rat, A... args)
     cudaError_t launch_render_p##PP(const ModelView &mv, const RenderSetup &rs, int *counter,                 \
                                     cudaStream_t stream)                                                     \
     {                                                                                                        \
-        return dispatch_degree<PP, RenderOne>(render_form_key(mv), rs.shading != 0, mv.nu != 0, mv.rational != 0, \
-                                               &mv, &rs, counter, stream);                                    \
+        return dispatch_degree<PP, RenderOne>(render_form_key(mv, rs.shading), rs.shading != 0, mv.nu != 0,  \
+                                               mv.rational != 0, &mv, &rs, counter, stream);                 \
     }                                                                                                        \
     cudaError_t launch_render_batch_p##PP(int dtype, int grad, int nu, int rat, const RenderJob *jobs_dev,     \
                                           int njobs, int total_tiles, int ctas_per_sm, int *counter,           \
