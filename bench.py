@@ -813,8 +813,11 @@ def run_serve48(args, wl):
                 "params": dict(prm, width=r["side"], height=r["side"]), "tf_dev": tfs[r["model"]],
                 "tf_size": 256, "rgba_dev": rgba, "nsamples_dev": ns}
 
+    resident = {}  # HBM bytes of the loaded models, per storage type
+
     def served(storage):
         ids = [ctx.load_model(m["ctrl"], m["degree"], storage=storage) for m in mods]
+        resident[storage] = sum(ctx.model_info(i)["bytes"] for i in ids)
         ctx.serve_start(frame_budget_bytes=2 << 30, max_batch=args.serve_batch, max_in_flight=args.serve_flights)
         # the clock sampler starts before the warm-up: its first nvidia-smi
         # start-up on a box can hold the driver for seconds
@@ -916,7 +919,7 @@ def run_serve48(args, wl):
                                    f"step {args.serve_step:g}",
                        "frame_budget_bytes": 2 << 30, "max_batch": args.serve_batch,
                        "max_in_flight": args.serve_flights,
-                       "resident_model_bytes_f16": sum(8 * m["ncp"][0] ** 3 for m in mods),
+                       "resident_model_bytes": resident,
                        "offered_load": sum(dur) / (reqs[-1]["arrival"] - reqs[0]["arrival"])},
             "served_f16": srv16, "served_f32": srv32,
             "serial_f32": {"latency_ms_p50": 1000 * _pct(slat, 0.50), "latency_ms_p99": 1000 * _pct(slat, 0.99),
