@@ -54,12 +54,14 @@ struct CacheCP {
 // Resident CTAs per SM the compiler is asked to fit: four (16 warps, at
 // most 128 registers a thread) up to degree 3, where the 64-value cache
 // fits beside the ray state; three on general knots, whose span bounds and
-// widths take nine more registers; the degree-4 cache needs the whole
-// register file of a thread; rational models keep no cache and two
-// contractions in flight.
-template <int P, bool NU, bool R>
+// widths take nine more registers; at degree 4 three for the 16-bit cache
+// (75 registers; measured 41.6 against 49.1 ms per 512^3 frame at one) and
+// one for the FP32 cache, which needs the whole register file of a thread;
+// rational models keep two contractions in flight.
+template <int P, typename T, bool NU, bool R>
 struct MinBlocks {
-    static constexpr int value = R ? 2 : (P <= 3 ? (NU ? 3 : 4) : 1);
+    static constexpr int value =
+        R ? 2 : (P <= 3 ? (NU ? 3 : 4) : (P == 4 && sizeof(T) == 2 && !NU ? 3 : 1));
 };
 
 // State of the ray a lane is marching.
@@ -455,7 +457,7 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
 // One image
 // ---------------------------------------------------------------------------
 template <int P, typename T, bool G, bool NU, bool R>
-__global__ void __launch_bounds__(kThreads, MinBlocks<P, NU, R>::value)
+__global__ void __launch_bounds__(kThreads, MinBlocks<P, T, NU, R>::value)
     render_kernel(ModelView mv, RenderSetup rs, int *__restrict__ counter)
 {
     // transfer function as (entry, next entry - entry) pairs: one FMA per
@@ -513,7 +515,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P, NU, R>::value)
 // Many images (render jobs) of one degree and storage type
 // ---------------------------------------------------------------------------
 template <int P, typename T, bool G, bool NU, bool R>
-__global__ void __launch_bounds__(kThreads, MinBlocks<P, NU, R>::value)
+__global__ void __launch_bounds__(kThreads, MinBlocks<P, T, NU, R>::value)
     render_batch_kernel(const RenderJob *__restrict__ jobs, int njobs, int total_tiles, int *__restrict__ counter)
 {
     __shared__ RenderJob s_job[kWarps];  // the current job of each warp
