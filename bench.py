@@ -729,7 +729,9 @@ def run_variants(args):
     variants = [("f32", {}, 1), ("f32 B-spline form", {"render_form": FORMS["bspline"]}, 1),
                 ("f16", {"storage": "f16"}, 1), ("bf16", {"storage": "bf16"}, 1),
                 ("f32 shading off", {}, 0), ("f32 B-spline form, shading off", {"render_form": FORMS["bspline"]}, 0),
-                ("f32 graded knots", {"knots": knots}, 1), ("f32 rational", {"weights": weights}, 1)]
+                ("f32 graded knots", {"knots": knots}, 1),
+                ("f32 graded knots, B-spline form", {"knots": knots, "render_form": FORMS["bspline"]}, 1),
+                ("f32 rational", {"weights": weights}, 1)]
     table, launches = {}, 0
     clocks = ClockSampler(local)
     clocks.start()

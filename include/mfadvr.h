@@ -71,13 +71,14 @@ typedef enum { MFADVR_F32 = 0, MFADVR_F16 = 1, MFADVR_BF16 = 2 } mfadvr_dtype;
  * B-spline form).  Within one knot-span cell the model is a polynomial of the
  * cell's local coordinates; the POWER form stores, per cell, its monomial
  * coefficients about the cell centre (FP32, computed in FP64 from the basis
- * pieces at load) and evaluates value and gradient by nested Horner sums:
- * no basis per sample, and at degree 3 123 multiply-adds on 83 instructions
- * instead of 192 on 128 plus the basis, for (p+1)^3 floats per cell (at degree 3 and 128^3 control points:
- * 500 MB beside the 67 MB row array).  It applies to FP32 storage, uniform
- * knots, non-rational models of degree <= 3, and serves shaded renders:
- * unshaded ones (value only) run the B-spline kernel on the row array, which
- * is faster there.  Results agree with the B-spline form to FP32 rounding. */
+ * pieces at load) and evaluates value and gradient by nested Horner sums: no
+ * basis per sample, and at degree 3 123 multiply-adds on 83 instructions
+ * instead of 192 on 128 plus the basis.  The price is (p+1)^3 floats per
+ * cell: at degree 3 and 128^3 control points 500 MB beside the 67 MB row
+ * array.  It applies to FP32 storage, non-rational models of degree <= 3
+ * (uniform or general knots), and serves shaded renders; unshaded ones
+ * (value only) run the B-spline kernel on the row array, which is faster
+ * there.  Results agree with the B-spline form to FP32 rounding. */
 typedef enum {
     MFADVR_FORM_AUTO = 0,    /* POWER where it applies, fits the HBM budget and
                                 takes at most 4 GiB; the B-spline form else   */

@@ -59,12 +59,16 @@ __global__ void build_rows_kernel(const float *__restrict__ src, void *__restric
     }
 }
 
-// One thread per span cell (i, j, k) of a uniform-knot FP32 model of degree
-// P: the coefficients of the cell's polynomial about its centre (PolyCell in
+// One thread per span cell (i, j, k) of an FP32 model of degree P: the
+// coefficients of the cell's polynomial about its centre (PolyCell in
 // mfa_basis.cuh), A = (Cu x Cv x Cw) applied to the (P+1)^3 control points
 // P(i.., j.., k..) one axis at a time, in FP64, each rounded once to FP32.
+// cp0..cp2: each axis's span pieces about the span centres (FP64, m x (P+1)
+// x (P+1), the host's centred_axis_pieces).
 template <int P>
-__global__ void build_poly_kernel(const float *__restrict__ src, float2 *__restrict__ poly, int n0, int n1, int n2)
+__global__ void build_poly_kernel(const float *__restrict__ src, float2 *__restrict__ poly, int n0, int n1, int n2,
+                                  const double *__restrict__ cp0, const double *__restrict__ cp1,
+                                  const double *__restrict__ cp2)
 {
     constexpr int K = P + 1, JP = Block<P>::JP, S = PolyCell<P>::kSectors;
     const int m0 = n0 - P, m1 = n1 - P, m2 = n2 - P;
@@ -75,9 +79,12 @@ __global__ void build_poly_kernel(const float *__restrict__ src, float2 *__restr
         const int j = static_cast<int>((cell / m0) % m1);
         const int k = static_cast<int>(cell / (static_cast<int64_t>(m0) * m1));
         double cu[K][K], cv[K][K], cw[K][K];
-        centred_pieces<P>(i, m0, cu);
-        centred_pieces<P>(j, m1, cv);
-        centred_pieces<P>(k, m2, cw);
+        for (int r = 0; r < K; ++r)
+            for (int e = 0; e < K; ++e) {
+                cu[r][e] = cp0[(static_cast<int64_t>(i) * K + r) * K + e];
+                cv[r][e] = cp1[(static_cast<int64_t>(j) * K + r) * K + e];
+                cw[r][e] = cp2[(static_cast<int64_t>(k) * K + r) * K + e];
+            }
         double t[K][K][K];  // t[a][s][q] = sum_r cu[r][a] P(i+r, j+s, k+q)
         for (int q = 0; q < K; ++q)
             for (int s = 0; s < K; ++s) {
@@ -129,16 +136,23 @@ cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t
     }
 }
 
-cudaError_t launch_build_poly(const float *src, void *poly, int p, int n0, int n1, int n2, cudaStream_t stream)
+cudaError_t launch_build_poly(const float *src, void *poly, int p, int n0, int n1, int n2,
+                              const double *const pieces[3], cudaStream_t stream)
 {
     const int64_t cells = static_cast<int64_t>(n0 - p) * (n1 - p) * (n2 - p);
     if (cells <= 0) return cudaSuccess;
     const int blocks = static_cast<int>((cells + 127) / 128 < 152 * 32 ? (cells + 127) / 128 : 152 * 32);
     float2 *dst = static_cast<float2 *>(poly);
     switch (p) {
-    case 1: build_poly_kernel<1><<<blocks, 128, 0, stream>>>(src, dst, n0, n1, n2); break;
-    case 2: build_poly_kernel<2><<<blocks, 128, 0, stream>>>(src, dst, n0, n1, n2); break;
-    case 3: build_poly_kernel<3><<<blocks, 128, 0, stream>>>(src, dst, n0, n1, n2); break;
+    case 1:
+        build_poly_kernel<1><<<blocks, 128, 0, stream>>>(src, dst, n0, n1, n2, pieces[0], pieces[1], pieces[2]);
+        break;
+    case 2:
+        build_poly_kernel<2><<<blocks, 128, 0, stream>>>(src, dst, n0, n1, n2, pieces[0], pieces[1], pieces[2]);
+        break;
+    case 3:
+        build_poly_kernel<3><<<blocks, 128, 0, stream>>>(src, dst, n0, n1, n2, pieces[0], pieces[1], pieces[2]);
+        break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

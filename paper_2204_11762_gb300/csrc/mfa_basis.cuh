@@ -604,7 +604,7 @@ __device__ __forceinline__ void contract(const float Nu[P + 1], const float dNu[
 //   BasisScale^3 f = sum_{a,b,c} A[a][b][c] tu^a tv^b tw^c,
 //   A[a][b][c] = sum_{r,s,q} Cu[r][a] Cv[s][b] Cw[q][c] P(i+r, j+s, k+q),
 // where C[r][e] is the coefficient of t^e in BasisScale N_r on the span: the
-// pieces of the span's knot pattern (as in the clamped-span tables), shifted
+// span's pieces (pieces_from_knots on its knots, uniform or general), shifted
 // to the centre.  A cell stores the pairs (A[a][2h][c], A[a][2h+1][c]) in the
 // order [c][h][a], the last h padded with 0 when P is even, in whole 32-byte
 // sectors: the order of the render kernel's span cache.
@@ -618,33 +618,6 @@ struct PolyCell {
 static_assert(PolyCell<1>::kSectors * 32 == poly_cell_bytes(1) && PolyCell<2>::kSectors * 32 == poly_cell_bytes(2) &&
                   PolyCell<3>::kSectors * 32 == poly_cell_bytes(3),
               "span-polynomial cell sizes of host and device differ");
-
-// Coefficients of t^e (t = x - 1/2) of BasisScale<P> N_r on span s of an
-// axis with m uniform clamped spans, in FP64: the span's knot pattern as in
-// make_span_pieces, the pieces from pieces_from_knots, then the Taylor shift
-// x^e = sum_f binom(e, f) 2^(f-e) t^f.
-template <int P>
-__host__ __device__ constexpr void centred_pieces(int s, int m, double (&c)[P + 1][P + 1])
-{
-    const int a = s < P - 1 ? P - 1 - s : 0, b = s + P > m ? s + P - m : 0;
-    double kap[2 * P] = {};
-    for (int j = 1 - P; j <= P; ++j) {
-        const int v = j < -(P - 1 - a) ? -(P - 1 - a) : j;
-        kap[j + P - 1] = v > P - b ? P - b : v;
-    }
-    double x[P + 1][P + 1] = {};
-    pieces_from_knots<P>(kap, BasisScale<P>::value, x);
-    for (int r = 0; r <= P; ++r)
-        for (int f = 0; f <= P; ++f) {
-            double sum = 0.0, binom = 1.0, half = 1.0;  // binom(e, f), 2^(f-e) for e = f, f+1, ...
-            for (int e = f; e <= P; ++e) {
-                sum += x[r][e] * binom * half;
-                binom = binom * (e + 1) / (e + 1 - f);
-                half *= 0.5;
-            }
-            c[r][f] = sum;
-        }
-}
 
 // Loads span cell `cell` of the polynomial array into v[c][h][a] (PolyCell).
 template <int P>

@@ -113,10 +113,12 @@ constexpr size_t row_entry_bytes(int) { return 32; }
 // scaling by inv_scale and rounding to the storage type.
 cudaError_t launch_build_rows(const float *src, void *rows, int n0, int n1, int n2, int dtype, float inv_scale,
                               cudaStream_t stream);
-// Span polynomials of a uniform-knot FP32 model of degree p <= 3 from its
-// control points (src, as for launch_build_rows) into poly (m0 m1 m2 cells of
-// poly_cell_bytes(p)).
-cudaError_t launch_build_poly(const float *src, void *poly, int p, int n0, int n1, int n2, cudaStream_t stream);
+// Span polynomials of an FP32 model of degree p <= 3 from its control points
+// (src, as for launch_build_rows) into poly (m0 m1 m2 cells of
+// poly_cell_bytes(p)); pieces[a] (device, FP64) holds axis a's span pieces
+// about the span centres, m_a x (p+1) x (p+1).
+cudaError_t launch_build_poly(const float *src, void *poly, int p, int n0, int n1, int n2,
+                              const double *const pieces[3], cudaStream_t stream);
 
 // Render setup for a caller-owned FP32 lattice outside any context, and the
 // context-free error sink (mfadvr_last_error(NULL)); both in mfadvr_api.cu.

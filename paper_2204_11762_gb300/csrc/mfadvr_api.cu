@@ -393,6 +393,62 @@ int pieces_stride(int p)
     }
 }
 
+// Knot vector t_0..t_{n+p} of axis a as the kernels use it: clamped uniform
+// j/m (exact in lattice units) for uniform-knot models; for general-knot
+// models the given knots, or j/m rounded to FP32 on axes given none.
+std::vector<double> model_knots(const mfadvr_model_desc *desc, const Model &m, int a)
+{
+    const int p = m.p, n = m.n[a], mm = n - p;
+    std::vector<double> t(static_cast<size_t>(n + p + 1));
+    for (int i = 0; i < n + p + 1; ++i) {
+        const int j = i < p ? 0 : (i > n ? mm : i - p);
+        if (m.nu && desc->knots[a]) t[i] = desc->knots[a][i];
+        else if (m.nu) t[i] = static_cast<float>(static_cast<double>(j) / mm);
+        else t[i] = static_cast<double>(j) / mm;
+    }
+    return t;
+}
+
+// The span pieces of one axis about each span's centre, for the span
+// polynomials: c[(k (P+1) + r) (P+1) + f] = coefficient of t^f, t = x - 1/2,
+// of BasisScale N_r on span k (x the span's local coordinate), in FP64: the
+// pieces of pieces_from_knots, then the Taylor shift
+// x^e = sum_f binom(e, f) 2^(f-e) t^f.
+template <int P>
+std::vector<double> centred_axis_pieces(const std::vector<double> &t, int n)
+{
+    constexpr int K = P + 1;
+    std::vector<double> out(static_cast<size_t>(n - P) * K * K);
+    for (int k = 0; k < n - P; ++k) {
+        const int s = P + k;
+        const double h = t[s + 1] - t[s];
+        double kap[2 * P] = {};
+        for (int j = 1 - P; j <= P; ++j) kap[j + P - 1] = (t[s + j] - t[s]) / h;
+        double c[K][K] = {};
+        pieces_from_knots<P>(kap, basis_scale_host(P), c);
+        for (int r = 0; r < K; ++r)
+            for (int f = 0; f < K; ++f) {
+                double sum = 0.0, binom = 1.0, half = 1.0;  // binom(e, f), 2^(f-e) for e = f, f+1, ...
+                for (int e = f; e < K; ++e) {
+                    sum += c[r][e] * binom * half;
+                    binom = binom * (e + 1) / (e + 1 - f);
+                    half *= 0.5;
+                }
+                out[(static_cast<size_t>(k) * K + r) * K + f] = sum;
+            }
+    }
+    return out;
+}
+
+std::vector<double> centred_axis_pieces_p(int p, const std::vector<double> &t, int n)
+{
+    switch (p) {
+    case 1: return centred_axis_pieces<1>(t, n);
+    case 2: return centred_axis_pieces<2>(t, n);
+    default: return centred_axis_pieces<3>(t, n);
+    }
+}
+
 // Host image of a general-knot model's knot buffer: per axis the m+1
 // breakpoints t_p..t_n, the m inverse widths, the 2m+1 lookup cells (int32:
 // cell c holds the largest k with t_{p+k} <= c / 2m) and the m x stride
@@ -405,15 +461,7 @@ std::vector<float> build_knot_buffer(const mfadvr_model_desc *desc, Model *m)
     std::vector<float> buf;
     for (int a = 0; a < 3; ++a) {
         const int n = m->n[a], mm = n - p;
-        std::vector<double> t(static_cast<size_t>(n + p + 1));
-        for (int i = 0; i < n + p + 1; ++i) {
-            if (desc->knots[a]) {
-                t[i] = desc->knots[a][i];
-            } else {
-                const int j = i < p ? 0 : (i > n ? mm : i - p);
-                t[i] = static_cast<float>(static_cast<double>(j) / mm);
-            }
-        }
+        const std::vector<double> t = model_knots(desc, *m, a);
         m->brk_off[a] = buf.size();
         buf.resize(up4(buf.size() + mm + 1), 0.0f);
         for (int k = 0; k <= mm; ++k) buf[m->brk_off[a] + k] = static_cast<float>(t[p + k]);
@@ -779,13 +827,12 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
                     static_cast<unsigned long long>(ctx->budget));
     // POWER render form: span polynomials beside the row array, where the
     // model allows them (AUTO: and where they fit the budget).
-    const bool poly_ok = m.dtype == MFADVR_F32 && !m.nu && !m.rational && m.p <= 3;
+    const bool poly_ok = m.dtype == MFADVR_F32 && !m.rational && m.p <= 3;
     const uint64_t poly_b = poly_ok ? static_cast<uint64_t>(m.n[0] - m.p) * (m.n[1] - m.p) * (m.n[2] - m.p) *
                                           static_cast<uint64_t>(poly_cell_bytes(m.p))
                                     : 0;
     if (desc->render_form == MFADVR_FORM_POWER && !poly_ok)
-        return fail(ctx, MFADVR_EUNSUPPORTED,
-                    "the power render form needs FP32 storage, uniform knots, no weights and degree <= 3");
+        return fail(ctx, MFADVR_EUNSUPPORTED, "the power render form needs FP32 storage, no weights and degree <= 3");
     const bool poly_fits = !ctx->budget || ctx->used + m.bytes + poly_b <= ctx->budget;
     if (desc->render_form == MFADVR_FORM_POWER && !poly_fits)
         return fail(ctx, MFADVR_ENOMEM, "span polynomials of %llu bytes exceed the HBM budget",
@@ -836,7 +883,26 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
         if (ep == cudaSuccess) {
             m.poly_bytes = poly_b;
             m.bytes += poly_b;
-            e = launch_build_poly(static_cast<const float *>(tmp), m.d_poly, m.p, m.n[0], m.n[1], m.n[2], nullptr);
+            // per-axis span pieces about the span centres, FP64, for the build
+            std::vector<double> cp[3];
+            size_t cp_n = 0;
+            for (int a = 0; a < 3; ++a) {
+                cp[a] = centred_axis_pieces_p(m.p, model_knots(desc, m, a), m.n[a]);
+                cp_n += cp[a].size();
+            }
+            void *d_cp = nullptr;
+            e = cudaMalloc(&d_cp, cp_n * sizeof(double));
+            const double *cpd[3] = {nullptr, nullptr, nullptr};
+            for (size_t a = 0, off = 0; a < 3 && e == cudaSuccess; off += cp[a].size(), ++a) {
+                cpd[a] = static_cast<const double *>(d_cp) + off;
+                e = cudaMemcpy(const_cast<double *>(cpd[a]), cp[a].data(), cp[a].size() * sizeof(double),
+                               cudaMemcpyHostToDevice);
+            }
+            if (e == cudaSuccess)
+                e = launch_build_poly(static_cast<const float *>(tmp), m.d_poly, m.p, m.n[0], m.n[1], m.n[2], cpd,
+                                      nullptr);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (d_cp) cudaFree(d_cp);
         } else {
             cudaGetLastError();
             m.d_poly = nullptr;

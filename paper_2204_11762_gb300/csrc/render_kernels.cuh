@@ -276,8 +276,7 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
 {
     constexpr bool kCache = SpanCache<P, T, R>::kOn;
     constexpr bool kPoly = std::is_same<T, PolyF32>::value;
-    static_assert(!kPoly || (P <= 3 && G && !NU && !R && kCache),
-                  "span polynomials: shaded renders of uniform plain models of degree <= 3");
+    static_assert(!kPoly || (P <= 3 && G && !R && kCache), "span polynomials: shaded renders of plain models, p <= 3");
     const float s = ray.sf;
 
     // ---- span of sample s; positions are clamped to the lattice only when
@@ -331,7 +330,14 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
     }
     float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
     if constexpr (kPoly) {
-        // no basis: the cell's polynomial is evaluated directly below
+        // no basis: the cell's polynomial is evaluated directly below, in the
+        // span's local coordinates (general knots: from the span bounds; a
+        // rounded multiply, so that no kernel fuses it with the centring and
+        // batched and single renders agree bit for bit)
+        if constexpr (NU) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) x[a] = __fmul_rn(x[a] - ray.lo[a], ray.ih[a]);
+        }
     } else if constexpr (NU) {
         // local coordinate on the span, basis from the span's pieces
 #pragma unroll
@@ -668,10 +674,10 @@ cudaError_t dispatch_degree(int dtype, bool grad, bool nu, bool rat, A... args)
 {
     switch (dtype) {
     case kPolyForm:
-        // span polynomials exist only for uniform-knot plain models of degree <= 3
+        // span polynomials exist only for plain models of degree <= 3
         if constexpr (P <= 3) {
-            if (nu || rat || !grad) return cudaErrorInvalidValue;
-            return F<P, PolyF32, true, false, false>::run(args...);
+            if (rat || !grad) return cudaErrorInvalidValue;
+            return nu ? F<P, PolyF32, true, true, false>::run(args...) : F<P, PolyF32, true, false, false>::run(args...);
         } else {
             return cudaErrorInvalidValue;
         }

@@ -127,9 +127,10 @@ def _render(ctx, torch, mid, cam, prm, tf):
     return img.cpu().numpy(), ns.cpu().numpy()
 
 
+@pytest.mark.parametrize("form", [0, 1])  # AUTO (span polynomials for FP32 up to degree 3), B-spline
 @pytest.mark.parametrize("p,storage,shading", [(1, "f32", 1), (2, "f32", 0), (3, "f32", 1), (3, "bf16", 1),
-                                               (3, "f32", 0), (4, "f32", 1), (5, "f16", 1)])
-def test_render_general_knots(ctx, torch_cuda, orc, p, storage, shading):
+                                               (3, "f32", 0), (4, "f32", 1), (5, "f16", 1), (2, "f32", 1)])
+def test_render_general_knots(ctx, torch_cuda, orc, p, storage, shading, form):
     from paper_2204_11762_gb300 import workloads
     torch = torch_cuda
     rng = np.random.default_rng(3000 + p * 7 + shading)
@@ -140,7 +141,7 @@ def test_render_general_knots(ctx, torch_cuda, orc, p, storage, shading):
     cam = _persp((1.9, -1.2, 1.4))
     prm = {"width": 48, "height": 40, "step": 1 / 256, "max_opacity": 0.99, "ref_step": 1 / 16,
            "shading": shading}
-    mid = ctx.load_model(ctrl, p, storage=storage, knots=given)
+    mid = ctx.load_model(ctrl, p, storage=storage, knots=given, render_form=form)
     img, ns = _render(ctx, torch, mid, cam, prm, tf)
     ref = orc.render(dequantize(ctrl, storage), p, cam,
                      dict(prm, tf=tf, tf_lo=float(ctrl.min()), tf_hi=float(ctrl.max())), knot_vectors=kv)

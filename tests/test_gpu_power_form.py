@@ -1,4 +1,5 @@
-"""The POWER render form (span polynomials evaluated by Horner's rule),
+"""The POWER render form (span polynomials evaluated by Horner's rule; the
+general-knot renders of tests/test_gpu_knots.py cover it on general knots),
 through the C ABI: renders agree with the FP64 oracle as the B-spline form's
 do (pixels within 2e-3 per channel, sample counts on a branch of every tied
 decision), the polynomials take the bytes the header states, and the form is
@@ -113,13 +114,15 @@ def test_power_form_requirements(torch_cuda):
     ctrl = rng.normal(size=(10, 10, 10)).astype(np.float32)
     knots = np.concatenate([np.zeros(4), [0.3, 0.35, 0.5, 0.6, 0.8, 0.9], np.ones(4)]).astype(np.float32)
     with mfadvr.Context(0) as ctx:
-        for kw in ({"storage": "f16"}, {"storage": "bf16"}, {"knots": (knots, None, None)},
-                   {"weights": np.full_like(ctrl, 2.0)}):
+        for kw in ({"storage": "f16"}, {"storage": "bf16"}, {"weights": np.full_like(ctrl, 2.0)}):
             with pytest.raises(mfadvr.MfadvrError) as e:
                 ctx.load_model(ctrl, 3, render_form=mfadvr.FORM_POWER, **kw)
             assert e.value.status == mfadvr.EUNSUPPORTED
             mid = ctx.load_model(ctrl, 3, **kw)  # AUTO: the B-spline form
             ctx.unload_model(mid)
+        mid = ctx.load_model(ctrl, 3, knots=(knots, None, knots), render_form=mfadvr.FORM_POWER)
+        assert ctx.model_info(mid)["bytes"] > ctx.model_info(ctx.load_model(ctrl, 3, knots=(knots, None, knots),
+                                                                             render_form=mfadvr.FORM_BSPLINE))["bytes"]
         with pytest.raises(mfadvr.MfadvrError) as e:
             ctx.load_model(ctrl, 4, render_form=mfadvr.FORM_POWER)
         assert e.value.status == mfadvr.EUNSUPPORTED
