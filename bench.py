@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 # DRAM bytes (read + write) of one render_kernel<3, float> launch on the
 # 128^3 workload from one ncu capture (profiles/render_kernel_gauss128_p3_persp1024.md),
 # valid only for the kernel sources it was taken on.
-RENDER_TRAFFIC = {"sources_sha256_16": "13dd54b7becdad51", "bytes": 517646848}
+RENDER_TRAFFIC = {"sources_sha256_16": "52b3cded8aab5046", "bytes": 517920768}
 RENDER_SOURCES = ("paper_2204_11762_gb300/csrc/render_kernels.cuh", "paper_2204_11762_gb300/csrc/mfa_basis.cuh",
                   "paper_2204_11762_gb300/csrc/mfa_internal.h")
 
@@ -731,7 +731,8 @@ def run_variants(args):
                 ("f32 shading off", {}, 0), ("f32 B-spline form, shading off", {"render_form": FORMS["bspline"]}, 0),
                 ("f32 graded knots", {"knots": knots}, 1),
                 ("f32 graded knots, B-spline form", {"knots": knots, "render_form": FORMS["bspline"]}, 1),
-                ("f32 rational", {"weights": weights}, 1)]
+                ("f32 rational", {"weights": weights}, 1),
+                ("f32 rational, B-spline form", {"weights": weights, "render_form": FORMS["bspline"]}, 1)]
     table, launches = {}, 0
     clocks = ClockSampler(local)
     clocks.start()

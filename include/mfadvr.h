@@ -75,8 +75,9 @@ typedef enum { MFADVR_F32 = 0, MFADVR_F16 = 1, MFADVR_BF16 = 2 } mfadvr_dtype;
  * basis per sample, and at degree 3 123 multiply-adds on 83 instructions
  * instead of 192 on 128 plus the basis.  The price is (p+1)^3 floats per
  * cell: at degree 3 and 128^3 control points 500 MB beside the 67 MB row
- * array.  It applies to FP32 storage, non-rational models of degree <= 3
- * (uniform or general knots), and serves shaded renders; unshaded ones
+ * array (twice that for a rational model: the polynomials of w P and of
+ * w).  It applies to FP32 models of degree <= 3 (uniform or general knots,
+ * plain or rational), and serves shaded renders; unshaded ones
  * (value only) run the B-spline kernel on the row array, which is faster
  * there.  Results agree with the B-spline form to FP32 rounding. */
 typedef enum {

@@ -31,8 +31,10 @@ struct ModelView {
     const void *wrows;
     float wscale;        // storage scale of wrows (1 for FP32)
     // POWER render form: per span cell the monomial coefficients of the
-    // model about the cell centre (PolyCell in mfa_basis.cuh); null otherwise
+    // model about the cell centre (PolyCell in mfa_basis.cuh); null otherwise.
+    // A rational model's poly holds those of w P, wpoly those of w.
     const float *poly;
+    const float *wpoly;
     int nu;
     int grid[3];  // lookup cells per axis (G = 2m)
     const float *brk[3];

@@ -79,6 +79,7 @@ ModelView view_of(const Model &m)
     }
     v.rational = m.rational;
     v.poly = static_cast<const float *>(m.d_poly);
+    v.wpoly = m.d_poly && m.rational ? v.poly + m.poly_bytes / 2 / sizeof(float) : nullptr;
     v.wrows = m.d_wrows;
     v.wscale = m.wscale;
     v.nu = m.nu;
@@ -827,12 +828,12 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
                     static_cast<unsigned long long>(ctx->budget));
     // POWER render form: span polynomials beside the row array, where the
     // model allows them (AUTO: and where they fit the budget).
-    const bool poly_ok = m.dtype == MFADVR_F32 && !m.rational && m.p <= 3;
+    const bool poly_ok = m.dtype == MFADVR_F32 && m.p <= 3;
     const uint64_t poly_b = poly_ok ? static_cast<uint64_t>(m.n[0] - m.p) * (m.n[1] - m.p) * (m.n[2] - m.p) *
-                                          static_cast<uint64_t>(poly_cell_bytes(m.p))
+                                          static_cast<uint64_t>(poly_cell_bytes(m.p)) * (m.rational ? 2 : 1)
                                     : 0;
     if (desc->render_form == MFADVR_FORM_POWER && !poly_ok)
-        return fail(ctx, MFADVR_EUNSUPPORTED, "the power render form needs FP32 storage, no weights and degree <= 3");
+        return fail(ctx, MFADVR_EUNSUPPORTED, "the power render form needs FP32 storage and degree <= 3");
     const bool poly_fits = !ctx->budget || ctx->used + m.bytes + poly_b <= ctx->budget;
     if (desc->render_form == MFADVR_FORM_POWER && !poly_fits)
         return fail(ctx, MFADVR_ENOMEM, "span polynomials of %llu bytes exceed the HBM budget",
@@ -864,52 +865,56 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
     void *tmp = nullptr;
     if (m.rational) e = cudaMalloc(&m.d_wrows, rows_b);
     if (e == cudaSuccess) e = cudaMalloc(&tmp, count * sizeof(float));
-    const float *rows_src = m.rational ? wctrl.data() : desc->ctrl;
-    if (e == cudaSuccess) e = cudaMemcpy(tmp, rows_src, count * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = launch_build_rows(static_cast<const float *>(tmp), m.d_rows, m.n[0], m.n[1], m.n[2], m.dtype,
-                              1.0f / m.scale, nullptr);
-    if (e == cudaSuccess && m.rational) {
-        // the weights' row array (synchronise first: tmp is reused)
-        e = cudaDeviceSynchronize();
-        if (e == cudaSuccess) e = cudaMemcpy(tmp, desc->weights, count * sizeof(float), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess)
-            e = launch_build_rows(static_cast<const float *>(tmp), m.d_wrows, m.n[0], m.n[1], m.n[2], m.dtype,
-                                  1.0f / m.wscale, nullptr);
-    }
+    // Power form: the span polynomials, beside the row array (a rational
+    // model has two: of w P, then of w).  AUTO drops to the B-spline form
+    // when the allocation fails.
+    void *d_cp = nullptr;  // per-axis span pieces about the span centres (FP64)
+    const double *cpd[3] = {nullptr, nullptr, nullptr};
     if (e == cudaSuccess && want_poly) {
-        // AUTO drops to the B-spline form when the allocation fails
         const cudaError_t ep = cudaMalloc(&m.d_poly, poly_b);
         if (ep == cudaSuccess) {
             m.poly_bytes = poly_b;
             m.bytes += poly_b;
-            // per-axis span pieces about the span centres, FP64, for the build
             std::vector<double> cp[3];
             size_t cp_n = 0;
             for (int a = 0; a < 3; ++a) {
                 cp[a] = centred_axis_pieces_p(m.p, model_knots(desc, m, a), m.n[a]);
                 cp_n += cp[a].size();
             }
-            void *d_cp = nullptr;
             e = cudaMalloc(&d_cp, cp_n * sizeof(double));
-            const double *cpd[3] = {nullptr, nullptr, nullptr};
             for (size_t a = 0, off = 0; a < 3 && e == cudaSuccess; off += cp[a].size(), ++a) {
                 cpd[a] = static_cast<const double *>(d_cp) + off;
                 e = cudaMemcpy(const_cast<double *>(cpd[a]), cp[a].data(), cp[a].size() * sizeof(double),
                                cudaMemcpyHostToDevice);
             }
-            if (e == cudaSuccess)
-                e = launch_build_poly(static_cast<const float *>(tmp), m.d_poly, m.p, m.n[0], m.n[1], m.n[2], cpd,
-                                      nullptr);
-            if (e == cudaSuccess) e = cudaDeviceSynchronize();
-            if (d_cp) cudaFree(d_cp);
         } else {
             cudaGetLastError();
             m.d_poly = nullptr;
             if (desc->render_form == MFADVR_FORM_POWER) e = ep;
         }
     }
+    const uint64_t poly_one = m.rational ? poly_b / 2 : poly_b;  // bytes of one polynomial array
+    // rows (and polynomials) of w P or P, then of the weights
+    const float *rows_src = m.rational ? wctrl.data() : desc->ctrl;
+    if (e == cudaSuccess) e = cudaMemcpy(tmp, rows_src, count * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_build_rows(static_cast<const float *>(tmp), m.d_rows, m.n[0], m.n[1], m.n[2], m.dtype,
+                              1.0f / m.scale, nullptr);
+    if (e == cudaSuccess && m.d_poly)
+        e = launch_build_poly(static_cast<const float *>(tmp), m.d_poly, m.p, m.n[0], m.n[1], m.n[2], cpd, nullptr);
+    if (e == cudaSuccess && m.rational) {
+        // the weights' arrays (synchronise first: tmp is reused)
+        e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemcpy(tmp, desc->weights, count * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = launch_build_rows(static_cast<const float *>(tmp), m.d_wrows, m.n[0], m.n[1], m.n[2], m.dtype,
+                                  1.0f / m.wscale, nullptr);
+        if (e == cudaSuccess && m.d_poly)
+            e = launch_build_poly(static_cast<const float *>(tmp), static_cast<char *>(m.d_poly) + poly_one, m.p,
+                                  m.n[0], m.n[1], m.n[2], cpd, nullptr);
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (d_cp) cudaFree(d_cp);
     if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) {
         cudaFree(m.d_rows);

@@ -276,7 +276,7 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
 {
     constexpr bool kCache = SpanCache<P, T, R>::kOn;
     constexpr bool kPoly = std::is_same<T, PolyF32>::value;
-    static_assert(!kPoly || (P <= 3 && G && !R && kCache), "span polynomials: shaded renders of plain models, p <= 3");
+    static_assert(!kPoly || (P <= 3 && G && kCache), "span polynomials: shaded renders, degree <= 3");
     const float s = ray.sf;
 
     // ---- span of sample s; positions are clamped to the lattice only when
@@ -321,6 +321,7 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
             const int64_t cell =
                 ray.kk[0] + static_cast<int64_t>(mv.m[0]) * (ray.kk[1] + static_cast<int64_t>(mv.m[1]) * ray.kk[2]);
             load_poly<P>(mv.poly, cell, cache.v);
+            if constexpr (R) load_poly<P>(mv.wpoly, cell, cache.w);
         } else {
             ray.base = ray.kk[0] + mv.n[0] * ray.kk[1] + mv.n01 * ray.kk[2];
             ray.interior = span_interior<P>(ray.kk[0], mv.m[0]) && span_interior<P>(ray.kk[1], mv.m[1]) &&
@@ -424,7 +425,10 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
     if constexpr (R) {
         {
             float rw[4];
-            if constexpr (kCache) {
+            if constexpr (kPoly) {
+                contract_poly<P>([&](int k, int jp, int i) { return cache.w[k][jp][i]; }, x[0] - 0.5f, x[1] - 0.5f,
+                                 x[2] - 0.5f, rw);
+            } else if constexpr (kCache) {
                 contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return cache.wpair(k, jp, i); },
                                rw);
             } else {
@@ -674,10 +678,16 @@ cudaError_t dispatch_degree(int dtype, bool grad, bool nu, bool rat, A... args)
 {
     switch (dtype) {
     case kPolyForm:
-        // span polynomials exist only for plain models of degree <= 3
+        // span polynomials exist only for FP32 models of degree <= 3
         if constexpr (P <= 3) {
-            if (rat || !grad) return cudaErrorInvalidValue;
-            return nu ? F<P, PolyF32, true, true, false>::run(args...) : F<P, PolyF32, true, false, false>::run(args...);
+            if (!grad) return cudaErrorInvalidValue;
+            const int k = (nu ? 2 : 0) | (rat ? 1 : 0);
+            switch (k) {
+            case 0: return F<P, PolyF32, true, false, false>::run(args...);
+            case 1: return F<P, PolyF32, true, false, true>::run(args...);
+            case 2: return F<P, PolyF32, true, true, false>::run(args...);
+            default: return F<P, PolyF32, true, true, true>::run(args...);
+            }
         } else {
             return cudaErrorInvalidValue;
         }

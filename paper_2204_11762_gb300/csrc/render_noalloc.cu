@@ -120,6 +120,7 @@ extern "C" MFADVR_API mfadvr_status mfadvr_render_lattice_noalloc(
     mv.wrows = nullptr;
     mv.wscale = 1.0f;
     mv.poly = nullptr;  // the B-spline form: nothing beyond the caller's lattice
+    mv.wpoly = nullptr;
     for (int a = 0; a < 3; ++a) {
         mv.n[a] = n[a];
         mv.m[a] = n[a] - degree[0];

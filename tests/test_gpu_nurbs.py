@@ -95,10 +95,12 @@ def test_bad_weights_rejected(ctx, torch_cuda):
         assert e.value.status == mfadvr.EINVAL
 
 
+@pytest.mark.parametrize("form", [0, 1])  # AUTO (span polynomials for FP32 up to degree 3), B-spline
 @pytest.mark.parametrize("p,storage,shading,general", [(2, "f32", 1, False), (3, "f32", 1, False),
                                                        (3, "f32", 0, True), (3, "bf16", 1, False),
-                                                       (4, "f32", 1, True), (5, "f16", 0, False)])
-def test_render_rational(ctx, torch_cuda, orc, p, storage, shading, general):
+                                                       (4, "f32", 1, True), (5, "f16", 0, False),
+                                                       (3, "f32", 1, True), (1, "f32", 1, False)])
+def test_render_rational(ctx, torch_cuda, orc, p, storage, shading, general, form):
     from paper_2204_11762_gb300 import workloads
     torch = torch_cuda
     dev = torch.device("cuda:0")
@@ -110,7 +112,7 @@ def test_render_rational(ctx, torch_cuda, orc, p, storage, shading, general):
     tf = workloads.transfer_function(rng, 128)
     cam = {"kind": 1, "eye": (1.8, -1.3, 1.5), "center": (0.5, 0.5, 0.5), "up": (0, 0, 1), "fovy_deg": 50.0}
     prm = {"width": 48, "height": 40, "step": 1 / 256, "max_opacity": 0.99, "ref_step": 1 / 16, "shading": shading}
-    mid = ctx.load_model(ctrl, p, storage=storage, knots=kv, weights=w)
+    mid = ctx.load_model(ctrl, p, storage=storage, knots=kv, weights=w, render_form=form)
     img = torch.full((40, 48, 4), float("nan"), device=dev)
     ns = torch.full((40, 48), -1, dtype=torch.int32, device=dev)
     ctx.render(mid, cam, prm, torch.from_numpy(tf).to(dev), tf.shape[0], img, ns)

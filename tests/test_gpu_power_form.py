@@ -1,5 +1,6 @@
 """The POWER render form (span polynomials evaluated by Horner's rule; the
-general-knot renders of tests/test_gpu_knots.py cover it on general knots),
+renders of tests/test_gpu_knots.py and tests/test_gpu_nurbs.py cover it on
+general knots and rational models),
 through the C ABI: renders agree with the FP64 oracle as the B-spline form's
 do (pixels within 2e-3 per channel, sample counts on a branch of every tied
 decision), the polynomials take the bytes the header states, and the form is
@@ -114,12 +115,17 @@ def test_power_form_requirements(torch_cuda):
     ctrl = rng.normal(size=(10, 10, 10)).astype(np.float32)
     knots = np.concatenate([np.zeros(4), [0.3, 0.35, 0.5, 0.6, 0.8, 0.9], np.ones(4)]).astype(np.float32)
     with mfadvr.Context(0) as ctx:
-        for kw in ({"storage": "f16"}, {"storage": "bf16"}, {"weights": np.full_like(ctrl, 2.0)}):
+        for kw in ({"storage": "f16"}, {"storage": "bf16"}):
             with pytest.raises(mfadvr.MfadvrError) as e:
                 ctx.load_model(ctrl, 3, render_form=mfadvr.FORM_POWER, **kw)
             assert e.value.status == mfadvr.EUNSUPPORTED
             mid = ctx.load_model(ctrl, 3, **kw)  # AUTO: the B-spline form
             ctx.unload_model(mid)
+        w = np.full_like(ctrl, 2.0)
+        a = ctx.load_model(ctrl, 3, weights=w, render_form=mfadvr.FORM_POWER)
+        b = ctx.load_model(ctrl, 3, weights=w, render_form=mfadvr.FORM_BSPLINE)
+        # a rational model's polynomials: of w P and of w
+        assert ctx.model_info(a)["bytes"] - ctx.model_info(b)["bytes"] == 2 * 7 ** 3 * CELL_BYTES[3]
         mid = ctx.load_model(ctrl, 3, knots=(knots, None, knots), render_form=mfadvr.FORM_POWER)
         assert ctx.model_info(mid)["bytes"] > ctx.model_info(ctx.load_model(ctrl, 3, knots=(knots, None, knots),
                                                                              render_form=mfadvr.FORM_BSPLINE))["bytes"]
