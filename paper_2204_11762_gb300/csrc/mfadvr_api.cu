@@ -890,7 +890,14 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
         } else {
             cudaGetLastError();
             m.d_poly = nullptr;
-            if (desc->render_form == MFADVR_FORM_POWER) e = ep;
+            if (desc->render_form == MFADVR_FORM_POWER) {
+                cudaFree(m.d_rows);
+                if (m.d_knots) cudaFree(m.d_knots);
+                if (m.d_wrows) cudaFree(m.d_wrows);
+                if (tmp) cudaFree(tmp);
+                return fail(ctx, MFADVR_ENOMEM, "span polynomials: cudaMalloc(%llu): %s",
+                            static_cast<unsigned long long>(poly_b), cudaGetErrorString(ep));
+            }
         }
     }
     const uint64_t poly_one = m.rational ? poly_b / 2 : poly_b;  // bytes of one polynomial array
