@@ -58,8 +58,9 @@ def test_null_arguments_rejected_without_a_device(lib):
 
 
 def test_header_struct_layout_matches_binding():
-    """The ctypes mirrors of the public structs have the C layout (checked by
-    compiling a probe against the header)."""
+    """The ctypes mirrors of the public structs have the C layout, and the
+    binding's enum constants the header's values (checked by compiling a probe
+    against the header)."""
     import subprocess
     import tempfile
     from paper_2204_11762_gb300 import mfadvr
@@ -74,6 +75,9 @@ int main(void) {
          offsetof(mfadvr_render_params, shininess));
   printf("%zu %zu %zu %zu\n", sizeof(mfadvr_render_job), offsetof(mfadvr_render_job, params),
          offsetof(mfadvr_render_job, rgba_dev), sizeof(mfadvr_tuning));
+  printf("%zu %zu\n", offsetof(mfadvr_model_desc, weights), offsetof(mfadvr_model_desc, render_form));
+  printf("%d %d %d %d %d %d %d\n", MFADVR_FORM_AUTO, MFADVR_FORM_BSPLINE, MFADVR_FORM_POWER, MFADVR_QUERY_VALUE,
+         MFADVR_QUERY_GRADIENT, MFADVR_QUERY_BOTH, MFADVR_QUERY_HESSIAN);
   return 0;
 }
 '''
@@ -87,5 +91,8 @@ int main(void) {
     M, Cm, R, J = mfadvr.ModelDesc, mfadvr.Camera, mfadvr.RenderParams, mfadvr.RenderJob
     exp = [ctypes.sizeof(M), M.ctrl.offset, M.storage.offset, ctypes.sizeof(Cm),
            ctypes.sizeof(R), R.tf_rgba.offset, R.shininess.offset,
-           ctypes.sizeof(J), J.params.offset, J.rgba_dev.offset, ctypes.sizeof(mfadvr.Tuning)]
+           ctypes.sizeof(J), J.params.offset, J.rgba_dev.offset, ctypes.sizeof(mfadvr.Tuning),
+           M.weights.offset, M.render_form.offset,
+           mfadvr.FORM_AUTO, mfadvr.FORM_BSPLINE, mfadvr.FORM_POWER, mfadvr.QUERY_VALUE, mfadvr.QUERY_GRADIENT,
+           mfadvr.QUERY_BOTH, mfadvr.QUERY_HESSIAN]
     assert got == exp
