@@ -57,11 +57,12 @@ struct CacheCP {
 // widths take nine more registers; at degree 4 three for the 16-bit cache
 // (75 registers; measured 41.6 against 49.1 ms per 512^3 frame at one) and
 // one for the FP32 cache, which needs the whole register file of a thread;
-// rational models keep two contractions in flight.
+// at degree 5 (no cache) three (about 4% faster than one); rational models
+// keep two contractions in flight.
 template <int P, typename T, bool NU, bool R>
 struct MinBlocks {
     static constexpr int value =
-        R ? 2 : (P <= 3 ? (NU ? 3 : 4) : (P == 4 && sizeof(T) == 2 && !NU ? 3 : 1));
+        R ? 2 : (P <= 3 ? (NU ? 3 : 4) : (!NU && (P == 5 || sizeof(T) == 2) ? 3 : 1));
 };
 
 // State of the ray a lane is marching.
