@@ -39,7 +39,7 @@ UNIT = "samples/s"
 C_FMA = {p: 2 * (p + 1) ** 3 + 3 * (p + 1) ** 2 + 4 * (p + 1) for p in range(1, 6)}
 # multiply-adds the power render form executes per value+gradient sample
 # (Horner in u on packed pairs, padded when p is even, then in v and w)
-POLY_FMA = {p: 2 * (p + 1) * ((p + 2) // 2) * (2 * p - 1) + (p + 1) * (3 * p - 1) + 4 * p - 1 for p in (1, 2, 3)}
+POLY_FMA = {p: 2 * (p + 1) * ((p + 2) // 2) * (2 * p - 1) + (p + 1) * (3 * p - 1) + 4 * p - 1 for p in (1, 2, 3, 4)}
 FORMS = {"auto": 0, "bspline": 1, "power": 2}
 FP32_LANES_PER_SM = 128
 

@@ -77,7 +77,8 @@ typedef enum { MFADVR_F32 = 0, MFADVR_F16 = 1, MFADVR_BF16 = 2 } mfadvr_dtype;
  * cell: at degree 3 and 128^3 control points 500 MB beside the 67 MB row
  * array (twice that for a rational model: the polynomials of w P and of
  * w).  It applies to FP32 models of degree <= 3 (uniform or general knots,
- * plain or rational), and serves shaded renders; unshaded ones
+ * plain or rational) and to plain ones of degree 4, and serves shaded
+ * renders; unshaded ones
  * (value only) run the B-spline kernel on the row array, which is faster
  * there.  Results agree with the B-spline form to FP32 rounding. */
 typedef enum {

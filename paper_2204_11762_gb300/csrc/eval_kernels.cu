@@ -153,6 +153,9 @@ cudaError_t launch_build_poly(const float *src, void *poly, int p, int n0, int n
     case 3:
         build_poly_kernel<3><<<blocks, 128, 0, stream>>>(src, dst, n0, n1, n2, pieces[0], pieces[1], pieces[2]);
         break;
+    case 4:
+        build_poly_kernel<4><<<blocks, 128, 0, stream>>>(src, dst, n0, n1, n2, pieces[0], pieces[1], pieces[2]);
+        break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -616,7 +616,7 @@ struct PolyCell {
     static constexpr int kSectors = (kPairs + 3) / 4;
 };
 static_assert(PolyCell<1>::kSectors * 32 == poly_cell_bytes(1) && PolyCell<2>::kSectors * 32 == poly_cell_bytes(2) &&
-                  PolyCell<3>::kSectors * 32 == poly_cell_bytes(3),
+                  PolyCell<3>::kSectors * 32 == poly_cell_bytes(3) && PolyCell<4>::kSectors * 32 == poly_cell_bytes(4),
               "span-polynomial cell sizes of host and device differ");
 
 // Loads span cell `cell` of the polynomial array into v[c][h][a] (PolyCell).

@@ -88,7 +88,7 @@ static_assert(sizeof(RenderJob) % 8 == 0, "RenderJob is copied in 8-byte words")
 constexpr int kPolyForm = 16;
 inline int render_form_key(const ModelView &v, int shading) { return v.poly && shading ? kPolyForm : v.dtype; }
 
-// Bytes of one span cell's coefficients in the POWER form (degree p <= 3):
+// Bytes of one span cell's coefficients in the POWER form (degree p <= 4):
 // (p+1) x ceil((p+1)/2) x (p+1) coefficient pairs, in whole 32-byte sectors.
 constexpr int poly_cell_bytes(int p) { return ((p + 1) * ((p + 2) / 2) * (p + 1) * 8 + 31) / 32 * 32; }
 
@@ -115,7 +115,7 @@ constexpr size_t row_entry_bytes(int) { return 32; }
 // scaling by inv_scale and rounding to the storage type.
 cudaError_t launch_build_rows(const float *src, void *rows, int n0, int n1, int n2, int dtype, float inv_scale,
                               cudaStream_t stream);
-// Span polynomials of an FP32 model of degree p <= 3 from its control points
+// Span polynomials of an FP32 model of degree p <= 4 from its control points
 // (src, as for launch_build_rows) into poly (m0 m1 m2 cells of
 // poly_cell_bytes(p)); pieces[a] (device, FP64) holds axis a's span pieces
 // about the span centres, m_a x (p+1) x (p+1).

@@ -446,7 +446,8 @@ std::vector<double> centred_axis_pieces_p(int p, const std::vector<double> &t, i
     switch (p) {
     case 1: return centred_axis_pieces<1>(t, n);
     case 2: return centred_axis_pieces<2>(t, n);
-    default: return centred_axis_pieces<3>(t, n);
+    case 3: return centred_axis_pieces<3>(t, n);
+    default: return centred_axis_pieces<4>(t, n);
     }
 }
 
@@ -828,12 +829,14 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
                     static_cast<unsigned long long>(ctx->budget));
     // POWER render form: span polynomials beside the row array, where the
     // model allows them (AUTO: and where they fit the budget).
-    const bool poly_ok = m.dtype == MFADVR_F32 && m.p <= 3;
+    // degree 4: plain models only (a rational one keeps no register cache there)
+    const bool poly_ok = m.dtype == MFADVR_F32 && (m.p <= 3 || (m.p == 4 && !m.rational));
     const uint64_t poly_b = poly_ok ? static_cast<uint64_t>(m.n[0] - m.p) * (m.n[1] - m.p) * (m.n[2] - m.p) *
                                           static_cast<uint64_t>(poly_cell_bytes(m.p)) * (m.rational ? 2 : 1)
                                     : 0;
     if (desc->render_form == MFADVR_FORM_POWER && !poly_ok)
-        return fail(ctx, MFADVR_EUNSUPPORTED, "the power render form needs FP32 storage and degree <= 3");
+        return fail(ctx, MFADVR_EUNSUPPORTED,
+                    "the power render form needs FP32 storage and degree <= 3 (degree 4: without weights)");
     const bool poly_fits = !ctx->budget || ctx->used + m.bytes + poly_b <= ctx->budget;
     if (desc->render_form == MFADVR_FORM_POWER && !poly_fits)
         return fail(ctx, MFADVR_ENOMEM, "span polynomials of %llu bytes exceed the HBM budget",

@@ -277,7 +277,7 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
 {
     constexpr bool kCache = SpanCache<P, T, R>::kOn;
     constexpr bool kPoly = std::is_same<T, PolyF32>::value;
-    static_assert(!kPoly || (P <= 3 && G && kCache), "span polynomials: shaded renders, degree <= 3");
+    static_assert(!kPoly || (P <= 4 && G && kCache), "span polynomials: shaded renders, degree <= 4");
     const float s = ray.sf;
 
     // ---- span of sample s; positions are clamped to the lattice only when
@@ -679,8 +679,12 @@ cudaError_t dispatch_degree(int dtype, bool grad, bool nu, bool rat, A... args)
 {
     switch (dtype) {
     case kPolyForm:
-        // span polynomials exist only for FP32 models of degree <= 3
-        if constexpr (P <= 3) {
+        // span polynomials exist only for FP32 models of degree <= 3, and for
+        // plain ones of degree 4
+        if constexpr (P == 4) {
+            if (!grad || rat) return cudaErrorInvalidValue;
+            return nu ? F<P, PolyF32, true, true, false>::run(args...) : F<P, PolyF32, true, false, false>::run(args...);
+        } else if constexpr (P <= 3) {
             if (!grad) return cudaErrorInvalidValue;
             const int k = (nu ? 2 : 0) | (rat ? 1 : 0);
             switch (k) {

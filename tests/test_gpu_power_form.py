@@ -12,7 +12,7 @@ from _parity import assert_render_parity
 
 pytestmark = pytest.mark.gpu
 
-CELL_BYTES = {1: 32, 2: 160, 3: 256}
+CELL_BYTES = {1: 32, 2: 160, 3: 256, 4: 608}
 
 
 @pytest.fixture(scope="module")
@@ -42,7 +42,7 @@ def _render(ctx, torch, mid, cam, prm, tf):
     return d_img.cpu().numpy(), d_ns.cpu().numpy()
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
 @pytest.mark.parametrize("shading", [1, 0])
 def test_power_form_matches_oracle(ctx, torch_cuda, orc, p, shading):
     """Random lattices (every cell's polynomial differs, clamped cells at all
@@ -64,7 +64,7 @@ def test_power_form_matches_oracle(ctx, torch_cuda, orc, p, shading):
     assert np.abs(imgs[mfadvr.FORM_POWER] - imgs[mfadvr.FORM_BSPLINE]).max() < 2e-3
 
 
-@pytest.mark.parametrize("p,n", [(3, (4, 4, 4)), (3, (5, 4, 6)), (2, (3, 5, 3)), (1, (2, 2, 3))])
+@pytest.mark.parametrize("p,n", [(3, (4, 4, 4)), (3, (5, 4, 6)), (2, (3, 5, 3)), (1, (2, 2, 3)), (4, (5, 6, 5))])
 def test_power_form_single_span_axes(ctx, torch_cuda, orc, p, n):
     """Lattices with one or two spans per axis: every cell is clamped at both
     ends of some axis (the knot patterns with both ends cut)."""
@@ -80,7 +80,7 @@ def test_power_form_single_span_axes(ctx, torch_cuda, orc, p, n):
     ctx.unload_model(mid)
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_power_form_bytes_and_point_queries(ctx, torch_cuda, p):
     """The span polynomials add m0 m1 m2 cells of the stated size; point
     queries keep using the row array, bit for bit."""
@@ -129,9 +129,10 @@ def test_power_form_requirements(torch_cuda):
         mid = ctx.load_model(ctrl, 3, knots=(knots, None, knots), render_form=mfadvr.FORM_POWER)
         assert ctx.model_info(mid)["bytes"] > ctx.model_info(ctx.load_model(ctrl, 3, knots=(knots, None, knots),
                                                                              render_form=mfadvr.FORM_BSPLINE))["bytes"]
-        with pytest.raises(mfadvr.MfadvrError) as e:
-            ctx.load_model(ctrl, 4, render_form=mfadvr.FORM_POWER)
-        assert e.value.status == mfadvr.EUNSUPPORTED
+        for deg, kw in ((5, {}), (4, {"weights": w})):  # degree 5; rational degree 4
+            with pytest.raises(mfadvr.MfadvrError) as e:
+                ctx.load_model(ctrl, deg, render_form=mfadvr.FORM_POWER, **kw)
+            assert e.value.status == mfadvr.EUNSUPPORTED
         with pytest.raises(mfadvr.MfadvrError) as e:
             ctx.load_model(ctrl, 3, render_form=3)
         assert e.value.status == mfadvr.EINVAL
