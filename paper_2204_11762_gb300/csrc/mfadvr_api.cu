@@ -686,6 +686,35 @@ mfadvr_status query_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_
     return MFADVR_OK;
 }
 
+// Uploads each axis's span pieces about the span centres (FP64,
+// centred_axis_pieces) into one device buffer *buf; cpd[a] points at axis a's.
+cudaError_t upload_centred_pieces(const mfadvr_model_desc *desc, const Model &m, void **buf, const double *cpd[3])
+{
+    std::vector<double> cp[3];
+    size_t total = 0;
+    for (int a = 0; a < 3; ++a) {
+        cp[a] = centred_axis_pieces_p(m.p, model_knots(desc, m, a), m.n[a]);
+        total += cp[a].size();
+    }
+    cudaError_t e = cudaMalloc(buf, total * sizeof(double));
+    for (size_t a = 0, off = 0; a < 3 && e == cudaSuccess; off += cp[a].size(), ++a) {
+        double *dst = static_cast<double *>(*buf) + off;
+        cpd[a] = dst;
+        e = cudaMemcpy(dst, cp[a].data(), cp[a].size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
+    return e;
+}
+
+// The row array of one FP32 source lattice in device memory and, when poly is
+// given, its span polynomials.
+cudaError_t build_arrays(const Model &m, const float *src, void *rows, void *poly, float inv_scale,
+                         const double *const cpd[3])
+{
+    cudaError_t e = launch_build_rows(src, rows, m.n[0], m.n[1], m.n[2], m.dtype, inv_scale, nullptr);
+    if (e == cudaSuccess && poly) e = launch_build_poly(src, poly, m.p, m.n[0], m.n[1], m.n[2], cpd, nullptr);
+    return e;
+}
+
 }  // namespace
 
 // Largest span-polynomial array the AUTO render form builds (MFADVR_FORM_POWER
@@ -869,27 +898,17 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
     if (m.rational) e = cudaMalloc(&m.d_wrows, rows_b);
     if (e == cudaSuccess) e = cudaMalloc(&tmp, count * sizeof(float));
     // Power form: the span polynomials, beside the row array (a rational
-    // model has two: of w P, then of w).  AUTO drops to the B-spline form
-    // when the allocation fails.
-    void *d_cp = nullptr;  // per-axis span pieces about the span centres (FP64)
+    // model has two: of w P, then of w), built from each axis's span pieces
+    // about the span centres (d_cp).  AUTO drops to the B-spline form when
+    // the allocation fails.
+    void *d_cp = nullptr;
     const double *cpd[3] = {nullptr, nullptr, nullptr};
     if (e == cudaSuccess && want_poly) {
         const cudaError_t ep = cudaMalloc(&m.d_poly, poly_b);
         if (ep == cudaSuccess) {
             m.poly_bytes = poly_b;
             m.bytes += poly_b;
-            std::vector<double> cp[3];
-            size_t cp_n = 0;
-            for (int a = 0; a < 3; ++a) {
-                cp[a] = centred_axis_pieces_p(m.p, model_knots(desc, m, a), m.n[a]);
-                cp_n += cp[a].size();
-            }
-            e = cudaMalloc(&d_cp, cp_n * sizeof(double));
-            for (size_t a = 0, off = 0; a < 3 && e == cudaSuccess; off += cp[a].size(), ++a) {
-                cpd[a] = static_cast<const double *>(d_cp) + off;
-                e = cudaMemcpy(const_cast<double *>(cpd[a]), cp[a].data(), cp[a].size() * sizeof(double),
-                               cudaMemcpyHostToDevice);
-            }
+            e = upload_centred_pieces(desc, m, &d_cp, cpd);
         } else {
             cudaGetLastError();
             m.d_poly = nullptr;
@@ -903,25 +922,19 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
             }
         }
     }
+    // the arrays of w P (or P), then those of the weights: tmp holds one source
+    // lattice at a time
+    char *poly = static_cast<char *>(m.d_poly);
     const uint64_t poly_one = m.rational ? poly_b / 2 : poly_b;  // bytes of one polynomial array
-    // rows (and polynomials) of w P or P, then of the weights
     const float *rows_src = m.rational ? wctrl.data() : desc->ctrl;
     if (e == cudaSuccess) e = cudaMemcpy(tmp, rows_src, count * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = launch_build_rows(static_cast<const float *>(tmp), m.d_rows, m.n[0], m.n[1], m.n[2], m.dtype,
-                              1.0f / m.scale, nullptr);
-    if (e == cudaSuccess && m.d_poly)
-        e = launch_build_poly(static_cast<const float *>(tmp), m.d_poly, m.p, m.n[0], m.n[1], m.n[2], cpd, nullptr);
+    if (e == cudaSuccess) e = build_arrays(m, static_cast<const float *>(tmp), m.d_rows, poly, 1.0f / m.scale, cpd);
     if (e == cudaSuccess && m.rational) {
-        // the weights' arrays (synchronise first: tmp is reused)
-        e = cudaDeviceSynchronize();
+        e = cudaDeviceSynchronize();  // tmp is reused
         if (e == cudaSuccess) e = cudaMemcpy(tmp, desc->weights, count * sizeof(float), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
-            e = launch_build_rows(static_cast<const float *>(tmp), m.d_wrows, m.n[0], m.n[1], m.n[2], m.dtype,
-                                  1.0f / m.wscale, nullptr);
-        if (e == cudaSuccess && m.d_poly)
-            e = launch_build_poly(static_cast<const float *>(tmp), static_cast<char *>(m.d_poly) + poly_one, m.p,
-                                  m.n[0], m.n[1], m.n[2], cpd, nullptr);
+            e = build_arrays(m, static_cast<const float *>(tmp), m.d_wrows, poly ? poly + poly_one : nullptr,
+                             1.0f / m.wscale, cpd);
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (d_cp) cudaFree(d_cp);
