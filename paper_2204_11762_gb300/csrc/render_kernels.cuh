@@ -51,18 +51,25 @@ struct CacheCP {
     static constexpr bool value = R ? P <= 3 : P <= 4;
 };
 
+// Storage tag of the POWER render form: the lane caches its span cell's
+// polynomial coefficients (FP32 pairs, PolyCell in mfa_basis.cuh) and
+// evaluates them by Horner's rule; no basis per sample.
+struct PolyF32 {};
+
 // Resident CTAs per SM the compiler is asked to fit: four (16 warps, at
 // most 128 registers a thread) up to degree 3, where the 64-value cache
-// fits beside the ray state; three on general knots, whose span bounds and
-// widths take nine more registers; at degree 4 three for the 16-bit cache
-// (75 registers; measured 41.6 against 49.1 ms per 512^3 frame at one) and
-// one for the FP32 cache, which needs the whole register file of a thread;
-// at degree 5 (no cache) three (about 4% faster than one); rational models
-// keep two contractions in flight.
+// fits beside the ray state; three in the B-spline form on general knots,
+// whose span bounds and widths take nine more registers (the power form,
+// with no basis, fits four there too: 4.82 -> 4.21 ms on graded knots); at
+// degree 4 three for the 16-bit cache (75 registers; measured 41.6 against
+// 49.1 ms per 512^3 frame at one) and one for the FP32 cache, which needs the
+// whole register file of a thread; at degree 5 (no cache) three (about 4%
+// faster than one); rational models keep two contractions in flight.
 template <int P, typename T, bool NU, bool R>
 struct MinBlocks {
+    static constexpr bool kPoly = std::is_same<T, PolyF32>::value;
     static constexpr int value =
-        R ? 2 : (P <= 3 ? (NU ? 3 : 4) : (!NU && (P == 5 || sizeof(T) == 2) ? 3 : 1));
+        R ? 2 : (P <= 3 ? (NU && !kPoly ? 3 : 4) : (!NU && (P == 5 || sizeof(T) == 2) ? 3 : 1));
 };
 
 // State of the ray a lane is marching.
@@ -78,11 +85,6 @@ struct LaneRay {
     float Cr, Cg, Cb, A;         // premultiplied colour and opacity so far
     float r[4];                  // query of sample sf - 1, not yet composited
 };
-
-// Storage tag of the POWER render form: the lane caches its span cell's
-// polynomial coefficients (FP32 pairs, PolyCell in mfa_basis.cuh) and
-// evaluates them by Horner's rule; no basis per sample.
-struct PolyF32 {};
 
 // Cached span block: FP32 pairs for FP32 storage; for 16-bit storage the
 // stored pairs themselves (one 32-bit register each, half the registers),
