@@ -58,9 +58,10 @@ struct PolyF32 {};
 
 // Resident CTAs per SM the compiler is asked to fit: four (16 warps, at
 // most 128 registers a thread) up to degree 3, where the 64-value cache
-// fits beside the ray state; three in the B-spline form on general knots,
-// whose span bounds and widths take nine more registers (the power form,
-// with no basis, fits four there too: 4.82 -> 4.21 ms on graded knots); at
+// fits beside the ray state; three for an FP32 B-spline block on general
+// knots, whose span bounds and widths take nine more registers (the power
+// form, with no basis, fits four there: 4.82 -> 4.21 ms on graded knots, and
+// so does the 16-bit block, 32 registers: 5.95 -> 5.42 ms in BF16); at
 // degree 4 three for the 16-bit cache (75 registers; measured 41.6 against
 // 49.1 ms per 512^3 frame at one) and one for the FP32 cache, which needs the
 // whole register file of a thread; at degree 5 (no cache) three (about 4%
@@ -69,7 +70,7 @@ template <int P, typename T, bool NU, bool R>
 struct MinBlocks {
     static constexpr bool kPoly = std::is_same<T, PolyF32>::value;
     static constexpr int value =
-        R ? 2 : (P <= 3 ? (NU && !kPoly ? 3 : 4) : (!NU && (P == 5 || sizeof(T) == 2) ? 3 : 1));
+        R ? 2 : (P <= 3 ? (NU && !kPoly && sizeof(T) == 4 ? 3 : 4) : (!NU && (P == 5 || sizeof(T) == 2) ? 3 : 1));
 };
 
 // State of the ray a lane is marching.
