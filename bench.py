@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 # DRAM bytes (read + write) of one render_kernel<3, float> launch on the
 # 128^3 workload from one ncu capture (profiles/render_kernel_gauss128_p3_persp1024.md),
 # valid only for the kernel sources it was taken on.
-RENDER_TRAFFIC = {"sources_sha256_16": "21e3c9abe7e19f5e", "bytes": 517825792}
+RENDER_TRAFFIC = {"sources_sha256_16": "af74aa39e5094c0c", "bytes": 518120960}
 RENDER_SOURCES = ("paper_2204_11762_gb300/csrc/render_kernels.cuh", "paper_2204_11762_gb300/csrc/mfa_basis.cuh",
                   "paper_2204_11762_gb300/csrc/mfa_internal.h")
 
