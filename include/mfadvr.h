@@ -24,7 +24,9 @@
  *    returns.
  *  - Streams: "stream" is a cudaStream_t passed as void* (NULL = the legacy
  *    default stream).  mfadvr_eval_points and mfadvr_render only enqueue work
- *    on it and return; the *_host variants and mfadvr_load_model synchronise.
+ *    on it and return, as does mfadvr_query_points_host_async (page-locked
+ *    host buffers); the other *_host variants and mfadvr_load_model
+ *    synchronise.
  *  - Threads: a context is used by one host thread at a time (or under an
  *    external lock).
  *  - Degrees: 1..MFADVR_MAX_DEGREE and equal on the three axes (the kernels
