@@ -9,11 +9,22 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mfa_internal.h"
 #include "mfadvr.h"
 
 namespace mfadvr {
 namespace api {
+
+// A named NVTX range over a scope: each entry point and each serving batch
+// shows up by name on a profiler's timeline (no cost without a tool attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 struct Model {
     void *d_rows = nullptr;   // row layout, see mfa_basis.cuh

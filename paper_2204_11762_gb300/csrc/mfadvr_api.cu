@@ -771,6 +771,7 @@ mfadvr_status mfadvr_destroy(mfadvr_ctx *ctx)
 
 mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, int32_t *model_id)
 {
+    TraceRange trace("mfadvr_load_model");
     if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
     if (!desc || !model_id) return fail(ctx, MFADVR_EINVAL, "desc and model_id must not be NULL");
     if (!desc->ctrl) return fail(ctx, MFADVR_EINVAL, "desc->ctrl must not be NULL");
@@ -955,6 +956,7 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
 
 mfadvr_status mfadvr_unload_model(mfadvr_ctx *ctx, int32_t model_id)
 {
+    TraceRange trace("mfadvr_unload_model");
     if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
     Model *m = nullptr;
     if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
@@ -985,24 +987,28 @@ mfadvr_status mfadvr_model_info(mfadvr_ctx *ctx, int32_t model_id, float *pmin, 
 mfadvr_status mfadvr_eval_points(mfadvr_ctx *ctx, int32_t model_id, const float *params_dev, int64_t n,
                                  float *out_dev, int32_t *spans_dev, void *stream)
 {
+    TraceRange trace("mfadvr_eval_points");
     return query_device(ctx, model_id, params_dev, n, MFADVR_QUERY_BOTH, out_dev, spans_dev, stream);
 }
 
 mfadvr_status mfadvr_eval_points_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_host, int64_t n,
                                       float *out_host, int32_t *spans_host, void *stream)
 {
+    TraceRange trace("mfadvr_eval_points_host");
     return query_host(ctx, model_id, params_host, n, MFADVR_QUERY_BOTH, out_host, spans_host, stream);
 }
 
 mfadvr_status mfadvr_query_points(mfadvr_ctx *ctx, int32_t model_id, const float *params_dev, int64_t n,
                                   int32_t query, float *out_dev, int32_t *spans_dev, void *stream)
 {
+    TraceRange trace("mfadvr_query_points");
     return query_device(ctx, model_id, params_dev, n, query, out_dev, spans_dev, stream);
 }
 
 mfadvr_status mfadvr_query_points_host(mfadvr_ctx *ctx, int32_t model_id, const float *params_host, int64_t n,
                                        int32_t query, float *out_host, int32_t *spans_host, void *stream)
 {
+    TraceRange trace("mfadvr_query_points_host");
     return query_host(ctx, model_id, params_host, n, query, out_host, spans_host, stream);
 }
 
@@ -1010,12 +1016,14 @@ mfadvr_status mfadvr_query_points_host_async(mfadvr_ctx *ctx, int32_t model_id, 
                                              int32_t query, float *out_host, int32_t *spans_host, int32_t max_ctas,
                                              void *stream)
 {
+    TraceRange trace("mfadvr_query_points_host_async");
     return query_host_async(ctx, model_id, params_host, n, query, out_host, spans_host, max_ctas, stream);
 }
 
 mfadvr_status mfadvr_render(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_camera *camera,
                             const mfadvr_render_params *params, float *rgba_dev, int32_t *nsamples_dev, void *stream)
 {
+    TraceRange trace("mfadvr_render");
     if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
     Model *m = nullptr;
     if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
@@ -1045,6 +1053,7 @@ mfadvr_status mfadvr_render_host(mfadvr_ctx *ctx, int32_t model_id, const mfadvr
                                  const mfadvr_render_params *params, float *rgba_host, int32_t *nsamples_host,
                                  void *stream)
 {
+    TraceRange trace("mfadvr_render_host");
     if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
     Model *m = nullptr;
     if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
@@ -1085,6 +1094,7 @@ mfadvr_status mfadvr_render_host(mfadvr_ctx *ctx, int32_t model_id, const mfadvr
 
 mfadvr_status mfadvr_render_batch(mfadvr_ctx *ctx, int32_t njobs, const mfadvr_render_job *jobs, void *stream)
 {
+    TraceRange trace("mfadvr_render_batch");
     if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
     if (njobs < 1 || njobs > MFADVR_MAX_BATCH || !jobs)
         return fail(ctx, MFADVR_EINVAL, "njobs must be in 1..%d and jobs not NULL", MFADVR_MAX_BATCH);
@@ -1126,6 +1136,7 @@ mfadvr_status mfadvr_autotune(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_ca
                               const mfadvr_render_params *params, float *rgba_dev, int32_t *nsamples_dev, void *stream,
                               mfadvr_tuning *best)
 {
+    TraceRange trace("mfadvr_autotune");
     if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
     Model *m = nullptr;
     if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;

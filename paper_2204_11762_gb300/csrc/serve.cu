@@ -96,6 +96,7 @@ struct Server {
     // through the graph of its group signature.  Called without the lock.
     cudaError_t launch(const std::vector<Request> &batch, int k, unsigned slot, cudaEvent_t ev, int *ngroups)
     {
+        TraceRange trace("mfadvr_serve_batch");
         cudaError_t e = cudaSuccess;
         RenderJob *hj = h_jobs + static_cast<size_t>(slot) * MFADVR_MAX_BATCH;
         RenderJob *dj = d_jobs + static_cast<size_t>(slot) * MFADVR_MAX_BATCH;
