@@ -21,21 +21,26 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mfa_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# A prebuilt library to load instead (the mutation tests point this at copies
+# of the oracle with planted mistakes, to show that the pins catch them).
+_LIB_OVERRIDE = os.environ.get("MFADVR_ORACLE_LIB")
 _lock = threading.Lock()
 _lib = None
 
 
+GCC_FLAGS = ["-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off"]
+
+
 def build(force: bool = False) -> str:
     """Compile ``liboracle.so`` next to its source (gcc, -O2, pthreads)."""
+    if _LIB_OVERRIDE:
+        return _LIB_OVERRIDE
     with _lock:
         stale = (not os.path.exists(_LIB_PATH)
                  or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
         if force or stale:
             tmp = _LIB_PATH + f".tmp{os.getpid()}"
-            subprocess.check_call(
-                ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
-                 "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC,
-                 "-lm", "-lpthread"])
+            subprocess.check_call(["gcc", *GCC_FLAGS, "-o", tmp, _SRC, "-lm", "-lpthread"])
             os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -66,8 +71,7 @@ class RenderParams(ctypes.Structure):
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(_LIB_PATH)
+        L = ctypes.CDLL(build())
         P = ctypes.POINTER
         L.orc_make_knots.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]
         L.orc_find_span.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_double), ctypes.c_double]

@@ -371,6 +371,57 @@ def test_shading_closed_form_linear_field(orc, grad):
     np.testing.assert_allclose(res["rgba"][..., 3], A, atol=1e-12)
 
 
+@pytest.mark.parametrize("grad", [(1.0, -2.0, 0.5), (0.3, 0.4, -0.2)])
+def test_shading_closed_form_world_box(orc, grad):
+    """The same linear field on a world box of extents (2, 0.5, 1): the world
+    gradient is the parameter gradient divided by the extents per axis, so
+    n = (g0/2, g1/0.5, g2/1) normalised, and with the view along +z every
+    sample has c (ka + kd |n_z|) + ks |n_z|^s."""
+    from paper_2204_11762_gb300.workloads import field_lattice
+    g = np.array(grad)
+    lin = lambda X, Y, Z: g[0] * X + g[1] * Y + g[2] * Z
+    ctrl = field_lattice(lin, (5, 5, 5), 2, lo=0.0, hi=1.0)
+    col = np.array([float(np.float32(c)) for c in (0.8, 0.5, 0.3)])
+    a = float(np.float32(0.03))
+    tf = _const_tf(tuple(col) + (a,))
+    ka, kd, ks, sh = 0.1, 0.7, 0.2, 10.0
+    box = ((0.0, 0.0, 0.0), (2.0, 0.5, 1.0))
+    cam = {"kind": 0, "eye": (1.0, 0.25, -1.0), "center": (1.0, 0.25, 0.5), "up": (0.0, 1.0, 0.0),
+           "ortho_height": 0.4}
+    res = orc.render(ctrl, 2, cam, {"width": 4, "height": 4, "step": 1 / 32, "max_opacity": 1.0, "tf": tf,
+                                    "shading": 1, "ka": ka, "kd": kd, "ks": ks, "shininess": sh},
+                     box_min=box[0], box_max=box[1])
+    gw = g / np.array([2.0, 0.5, 1.0])
+    ndl = abs(gw[2]) / np.linalg.norm(gw)
+    rgb = np.clip(col * (ka + kd * ndl) + ks * ndl ** sh, 0, 1)
+    A = 1 - (1 - a) ** 32
+    np.testing.assert_allclose(res["rgba"][..., :3], np.broadcast_to(rgb * A, (4, 4, 3)), atol=1e-12)
+
+
+def test_perspective_rows_and_fov_closed_form(orc):
+    """One image column from an eye at (1.5, 0.5, 0.7) looking along -x (up
+    +z, vertical FOV 40 deg): row y's ray is (-1, 0, s_y) normalised with
+    s_y = (1 - 2 (y + 1/2)/H) tan(20 deg), row 0 at the top.  It enters the
+    box through the face x = 1 and leaves through the top face z = 1 after
+    x-travel 0.3/s_y - 0.5 when that is below 1 (upward rays), else through
+    the face x = 0; the chord is that x-travel times sqrt(1 + s_y^2), and the
+    ray takes floor(chord/step) samples."""
+    ctrl = np.full((4, 4, 4), 0.5)
+    tf = _const_tf((1, 1, 1, 0.0))
+    H, step = 8, 1 / 200
+    cam = {"kind": 1, "eye": (1.5, 0.5, 0.7), "center": (0.5, 0.5, 0.7), "up": (0, 0, 1), "fovy_deg": 40.0}
+    res = orc.render(ctrl, 3, cam, {"width": 1, "height": H, "step": step, "max_opacity": 1.0, "tf": tf,
+                                    "shading": 0})
+    for y in range(H):
+        s = (1 - 2 * (y + 0.5) / H) * math.tan(math.radians(20.0))
+        h = min(1.0, 0.3 / s - 0.5) if s > 0 else 1.0
+        chord = h * math.sqrt(1 + s * s)
+        r = chord / step
+        assert abs(r - round(r)) > 1e-6  # no tied count in this set-up
+        assert res["nsamples"][y, 0] == math.floor(r), (y, res["nsamples"][y, 0], r)
+    assert res["nsamples"][0, 0] < res["nsamples"][H - 1, 0]  # the top row leaves through the top
+
+
 def test_depth_ramp_brute_force_product(orc):
     """Field f = w (exact for p = 1), TF ramp in opacity and red: along +z the
     k-th sample sits at w_k = (k + 1/2) step, so the pixel is the explicit
