@@ -51,6 +51,34 @@ MUTANTS = {
     "rows_bottom_up": ("double sy = (1.0 - 2.0 * (y + 0.5) / H) * th;",
                        "double sy = (2.0 * (y + 0.5) / H - 1.0) * th;"),
     "slab_enter_not_advanced": ("if (ta > a0) { a0 = ta; b0 = ea; }", "if (ta < a0) { a0 = ta; b0 = ea; }"),
+    "recurrence_right_denominator": ("val += (t[i + q + 1] - u) / (t[i + q + 1] - t[i + 1]) * B[q - 1][r];",
+                                     "val += (t[i + q + 1] - u) / (t[i + q] - t[i + 1]) * B[q - 1][r];"),
+    "lattice_index_transposed": (
+        "return m->ctrl[(size_t)i + (size_t)m->n[0] * ((size_t)j + (size_t)m->n[1] * (size_t)k)];",
+        "return m->ctrl[(size_t)j + (size_t)m->n[1] * ((size_t)i + (size_t)m->n[0] * (size_t)k)];"),
+    "rational_numerator_unweighted": ("const double w = weight_at(m, i, j, k), wP = w * ctrl_at(m, i, j, k);",
+                                      "const double w = weight_at(m, i, j, k), wP = ctrl_at(m, i, j, k);"),
+    "knot_right_end_unchecked": ("if (t[i] != 0.0 || t[n + i] != 1.0) return -1;", "if (t[i] != 0.0) return -1;"),
+    "zero_weight_accepted": ("if (!(m->weights[i] > 0.0) || !isfinite(m->weights[i])) return -1;",
+                             "if (!(m->weights[i] >= 0.0) || !isfinite(m->weights[i])) return -1;"),
+    "camera_right_flipped": ("cross3(cam->up, J.fwd, J.right);", "cross3(J.fwd, cam->up, J.right);"),
+    "ortho_aspect_dropped": ("double sx = ((x + 0.5) / W - 0.5) * cam->ortho_height * aspect;",
+                             "double sx = ((x + 0.5) / W - 0.5) * cam->ortho_height;"),
+    "ortho_rows_bottom_up": ("double sy = (0.5 - (y + 0.5) / H) * cam->ortho_height;",
+                             "double sy = ((y + 0.5) / H - 0.5) * cam->ortho_height;"),
+    "perspective_direction_unnormalised": ("d[a] /= l;", "(void)l;"),
+    "parallel_ray_high_side_kept": ("if (o[a] < m->box_min[a] || o[a] > m->box_max[a]) return 0;",
+                                    "if (o[a] < m->box_min[a]) return 0;"),
+    "sample_count_rounded_up": ("long N = (long)floor(r);", "long N = (long)ceil(r);"),
+    "tf_range_offset_dropped": ("clamp01((v - J->lo) / (J->hi - J->lo))", "clamp01(v / (J->hi - J->lo))"),
+    "tf_nearest_entry": ("double fr = x - i;", "double fr = floor(x - i + 0.5);"),
+    "opacity_accumulates_alpha": ("A += w;", "A += alpha;"),
+    "termination_not_strict": ("if (stop < 0 && A > rp->max_opacity) {", "if (stop < 0 && A >= rp->max_opacity) {"),
+    "shading_one_sided": ("double ndl = fabs(-(g[0] * d[0] + g[1] * d[1] + g[2] * d[2]) / gn);",
+                          "double ndl = fmax(0.0, -(g[0] * d[0] + g[1] * d[1] + g[2] * d[2]) / gn);"),
+    "flat_field_diffuse": ("for (int c = 0; c < 3; ++c) rgba[c] *= rp->ka;",
+                           "for (int c = 0; c < 3; ++c) rgba[c] *= rp->kd;"),
+    "flat_threshold_strict": ("if (gn <= J->gthresh) {", "if (gn < J->gthresh) {"),
 }
 
 

@@ -465,6 +465,64 @@ def test_perspective_centre_ray_chord(orc):
     assert res["nsamples"][0, 0] == 0
 
 
+def test_orthographic_footprint_closed_form(orc):
+    """Orthographic view along +z of the field f = X + 2Y (exact for p = 2),
+    image 8 x 4, view height 0.7: pixel (x, y) looks down the line
+    X = 1/2 + ((x + 1/2)/8 - 1/2) 0.7 (8/4), Y = 1/2 + (1/2 - (y + 1/2)/4) 0.7,
+    row 0 at the top.  A two-entry TF ramps red over [-1, 3] with a constant
+    opacity, so a hit pixel is ((f + 1)/4 A, 0, 0, A) with A = 1 - (1 - a)^32;
+    the columns x = 0 and x = 7 pass beside the box (X < 0 and X > 1) and stay
+    empty."""
+    from paper_2204_11762_gb300.workloads import field_lattice
+    ctrl = field_lattice(lambda X, Y, Z: X + 2.0 * Y, (5, 5, 5), 2, lo=0.0, hi=1.0)
+    a = _f32(0.05)
+    tf = np.array([[0, 0, 0, a], [1, 0, 0, a]], dtype=np.float32)
+    W, H, h = 8, 4, 0.7
+    cam = {"kind": 0, "eye": (0.5, 0.5, -1.0), "center": (0.5, 0.5, 0.5), "up": (0.0, 1.0, 0.0),
+           "ortho_height": h}
+    res = orc.render(ctrl, 2, cam, {"width": W, "height": H, "step": 1 / 32, "max_opacity": 1.0, "tf": tf,
+                                    "tf_lo": -1.0, "tf_hi": 3.0, "shading": 0})
+    A = 1 - (1 - a) ** 32
+    for y in range(H):
+        for x in range(W):
+            X = 0.5 + ((x + 0.5) / W - 0.5) * h * (W / H)
+            Y = 0.5 + (0.5 - (y + 0.5) / H) * h
+            if not 0.0 < X < 1.0:
+                assert res["nsamples"][y, x] == 0 and (res["rgba"][y, x] == 0).all(), (x, y)
+                continue
+            assert res["nsamples"][y, x] == 32
+            np.testing.assert_allclose(res["rgba"][y, x], [(X + 2 * Y + 1) / 4 * A, 0, 0, A], atol=1e-12)
+
+
+@pytest.mark.parametrize("ert,n_exp", [(0.75, 3), (0.7, 2), (0.875, 4)])
+def test_termination_is_strictly_above_o_max(orc, ert, n_exp):
+    """Sample opacity 1/2: the cumulative opacity after k samples is
+    1 - 2^-k exactly (0.5, 0.75, 0.875, ...), and the march stops at the first
+    k with A > O_max, so an O_max met exactly takes one sample more."""
+    ctrl = np.full((4, 4, 4), 0.5)
+    tf = _const_tf((1.0, 1.0, 1.0, 0.5))
+    res = orc.render(ctrl, 2, _ortho(), {"width": 3, "height": 3, "step": 1 / 16, "max_opacity": ert,
+                                         "tf": tf, "shading": 0})
+    A = 1 - 0.5 ** n_exp
+    assert (res["nsamples"] == n_exp).all()
+    np.testing.assert_array_equal(res["rgba"], np.full(res["rgba"].shape, A))
+
+
+def test_flat_field_takes_the_ambient_term_only(orc):
+    """Zero field: every gradient is exactly zero, so a shaded sample keeps
+    only the ambient part, c ka, and the pixel is c ka A."""
+    ctrl = np.zeros((5, 5, 5))
+    col = np.array([_f32(c) for c in (0.8, 0.5, 0.3)])
+    a = _f32(0.04)
+    tf = _const_tf(tuple(col) + (a,))
+    ka, kd, ks = 0.25, 0.6, 0.3
+    res = orc.render(ctrl, 2, _ortho(), {"width": 3, "height": 3, "step": 1 / 32, "max_opacity": 1.0, "tf": tf,
+                                         "shading": 1, "ka": ka, "kd": kd, "ks": ks, "shininess": 8.0})
+    A = 1 - (1 - a) ** 32
+    np.testing.assert_allclose(res["rgba"][..., :3], np.broadcast_to(col * ka * A, (3, 3, 3)), atol=1e-12)
+    np.testing.assert_allclose(res["rgba"][..., 3], A, atol=1e-12)
+
+
 @pytest.mark.parametrize("p,n,shading", [(1, 4, 0), (2, 5, 1), (3, 6, 1)])
 def test_render_span_mode_equals_brute_mode(orc, p, n, shading):
     rng = np.random.default_rng(53 + p)
