@@ -243,3 +243,43 @@ def test_full_size_value_noise_sampled_rows(ctx, torch_cuda, orc, storage):
     rows = np.arange(0, wl["params"]["height"], 216)
     assert_render_parity(img, ns, ref, rows=rows)
     assert np.isfinite(img).all()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("form", [0, 1])  # AUTO (span polynomials for FP32), B-spline
+def test_zero_field_shades_ambient_only(ctx, torch_cuda, orc, storage, form):
+    """All control points zero: every gradient is exactly zero, so each
+    shaded sample keeps only the ambient term of the first TF entry (the
+    lattice's value range is one point)."""
+    from paper_2204_11762_gb300 import workloads
+    rng = np.random.default_rng(811)
+    ctrl = np.zeros((6, 7, 8), dtype=np.float32)
+    tf = workloads.transfer_function(rng, 32)
+    cam = _persp((1.9, 1.4, 1.7))
+    prm = {"width": 24, "height": 20, "step": 1 / 64, "max_opacity": 0.99, "shading": 1, "ka": 0.3}
+    mid = ctx.load_model(ctrl, 3, storage=storage, render_form=form)
+    img, ns = _render(ctx, torch_cuda, mid, cam, prm, tf)
+    ref = orc.render(ctrl.astype(np.float64), 3, cam, dict(prm, tf=tf))
+    assert_render_parity(img, ns, ref)
+    hit = ref["nsamples"] > 0
+    assert hit.any() and (~hit).any()
+    np.testing.assert_allclose(img[hit][:, :3] / img[hit][:, 3:4], np.broadcast_to(tf[0, :3] * 0.3, (hit.sum(), 3)),
+                               rtol=1e-4)
+    ctx.unload_model(mid)
+
+
+def test_every_ray_misses_the_box(ctx, torch_cuda, orc):
+    """A camera looking away from the box: every pixel is written empty
+    (zero RGBA, zero samples) over the NaN-filled output."""
+    from paper_2204_11762_gb300 import workloads
+    rng = np.random.default_rng(812)
+    ctrl = rng.uniform(0, 1, size=(5, 5, 5)).astype(np.float32)
+    tf = workloads.transfer_function(rng, 16)
+    cam = {"kind": 1, "eye": (3.0, 0.5, 0.5), "center": (4.0, 0.5, 0.5), "up": (0, 0, 1), "fovy_deg": 40.0}
+    prm = {"width": 33, "height": 17, "step": 1 / 64, "max_opacity": 0.99, "shading": 1}
+    mid = ctx.load_model(ctrl, 2)
+    img, ns = _render(ctx, torch_cuda, mid, cam, prm, tf)
+    ref = orc.render(ctrl.astype(np.float64), 2, cam, dict(prm, tf=tf))
+    assert (ref["nsamples"] == 0).all()
+    assert (img == 0).all() and (ns == 0).all()
+    ctx.unload_model(mid)
