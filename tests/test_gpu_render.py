@@ -56,7 +56,7 @@ def test_small_marschner_lobb_workload(ctx, torch_cuda, orc):
 
 @pytest.mark.parametrize("form", [0, 1])  # AUTO (span polynomials up to degree 3), B-spline
 @pytest.mark.parametrize("p,n,W,H,shading", [(1, 4, 4, 4, 0), (2, 5, 8, 8, 1), (3, 6, 8, 8, 1), (3, 4, 5, 7, 0),
-                                             (4, 7, 9, 6, 1), (5, 8, 6, 9, 1)])
+                                             (4, 7, 9, 6, 1), (5, 8, 6, 9, 1), (3, 5, 1, 1, 1), (2, 4, 1, 3, 0)])
 def test_tiny_images(ctx, torch_cuda, orc, p, n, W, H, shading, form):
     from paper_2204_11762_gb300 import workloads
     rng = np.random.default_rng(200 + p * 3 + n)
