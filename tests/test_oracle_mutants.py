@@ -79,20 +79,53 @@ MUTANTS = {
     "flat_field_diffuse": ("for (int c = 0; c < 3; ++c) rgba[c] *= rp->ka;",
                            "for (int c = 0; c < 3; ++c) rgba[c] *= rp->kd;"),
     "flat_threshold_strict": ("if (gn <= J->gthresh) {", "if (gn < J->gthresh) {"),
+    "point_span_output_shifted": ("if (s3) s3[d] = s[d];", "if (s3) s3[d] = s[d] - 1;"),
+    "point_clamp_dropped": ("for (int d = 0; d < 3; ++d) q[d] = clamp01((double)j->uvw[3 * i + d]);",
+                            "for (int d = 0; d < 3; ++d) q[d] = (double)j->uvw[3 * i + d];"),
+    "point_chunks_skip_first": ("jobs[t].begin = npts * t / nthreads;",
+                                "jobs[t].begin = npts * t / nthreads + (t > 0);"),
+    "render_rows_dealt_inverted": ("if ((rows_done++ % J->nthreads) != ra->tid) continue;",
+                                   "if ((rows_done++ % J->nthreads) == ra->tid) continue;"),
+    "render_row_step_ignored": ("for (int y = 0; y < H; y += J->row_step) {", "for (int y = 0; y < H; y += 1) {"),
+    "sample_count_tie_never_flagged": ("if (rn >= 1.0 && fabs(r - rn) < window) {",
+                                       "if (rn >= 1.0 && fabs(r - rn) < 0.0) {"),
+    "termination_tie_low_edge_dropped": ("if (lo < 0 && A > rp->max_opacity - ORC_TIE_OPACITY) lo = k + 1;",
+                                         "if (lo < 0 && A > rp->max_opacity) lo = k + 1;"),
+    "termination_tie_high_edge_dropped": ("if (A > rp->max_opacity + ORC_TIE_OPACITY) { hi = k + 1; break; }",
+                                          "if (A > rp->max_opacity) { hi = k + 1; break; }"),
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_planted_mistake(name, tmp_path):
+def _run_mutant(name, src, workdir):
+    """Compile one mutant and run the pins against it: (exit code, output)."""
     import oracle
     old, new = MUTANTS[name]
-    src = open(SRC).read()
-    assert src.count(old) == 1, f"{name}: the text to mutate must occur exactly once"
-    mutant_c = tmp_path / "mutant.c"
-    mutant_c.write_text(src.replace(old, new))
-    lib = tmp_path / "libmutant.so"
-    subprocess.check_call(["gcc", *oracle.GCC_FLAGS, "-o", str(lib), str(mutant_c), "-lm", "-lpthread"])
-    env = dict(os.environ, MFADVR_ORACLE_LIB=str(lib))
+    if src.count(old) != 1:
+        return None, f"the text to mutate occurs {src.count(old)} times"
+    mutant_c = os.path.join(workdir, f"{name}.c")
+    with open(mutant_c, "w") as fh:
+        fh.write(src.replace(old, new))
+    lib = os.path.join(workdir, f"lib{name}.so")
+    subprocess.check_call(["gcc", *oracle.GCC_FLAGS, "-o", lib, mutant_c, "-lm", "-lpthread"])
+    env = dict(os.environ, MFADVR_ORACLE_LIB=lib)
     r = subprocess.run([sys.executable, "-m", "pytest", *PIN_FILES, "-x", "-q", "-p", "no:cacheprovider",
                         "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0, f"no pin caught the planted mistake '{name}':\n{r.stdout[-2000:]}"
+    return r.returncode, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def mutant_results(tmp_path_factory):
+    """Every mutant's pin run, several at a time (each is its own process)."""
+    from concurrent.futures import ThreadPoolExecutor
+    src = open(SRC).read()
+    workdir = str(tmp_path_factory.mktemp("mutants"))
+    names = sorted(MUTANTS)
+    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        return dict(zip(names, ex.map(lambda n: _run_mutant(n, src, workdir), names)))
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, mutant_results):
+    rc, out = mutant_results[name]
+    assert rc is not None, f"{name}: {out}"
+    assert rc != 0, f"no pin caught the planted mistake '{name}':\n{out}"

@@ -138,6 +138,29 @@ def test_span_is_exact_floor(orc, n, p):
         assert orc.find_span(n, p, u) == _span_exact(u, n, p), (u, n, p)
 
 
+def test_point_query_spans_are_exact_floor(orc):
+    """The spans a point query reports, per axis, equal p + floor(u m) in
+    exact arithmetic on the clamped FP32 coordinate; points outside [0, 1]
+    take the end spans.  Several threads share the points."""
+    rng = np.random.default_rng(6)
+    p, n = 3, (9, 8, 13)
+    ctrl = rng.normal(size=(n[2], n[1], n[0]))
+    cols = []
+    for d in range(3):
+        m = n[d] - p
+        us = list(rng.uniform(-0.1, 1.1, 300))
+        for j in range(m + 1):
+            k32 = np.float32(j / m)
+            us += [float(k32), float(np.nextafter(k32, np.float32(2))), float(np.nextafter(k32, np.float32(-1)))]
+        cols.append(us)
+    npts = max(len(c) for c in cols)  # shorter axes padded with more random points
+    uvw = np.stack([np.asarray(c + list(rng.uniform(0, 1, npts - len(c))), dtype=np.float32) for c in cols], axis=1)
+    _, spans = orc.eval_points(ctrl, p, uvw, threads=3)
+    for d in range(3):
+        want = [_span_exact(min(max(float(u), 0.0), 1.0), n[d], p) for u in uvw[:, d]]
+        np.testing.assert_array_equal(spans[:, d], want)
+
+
 # --------------------------------------------------------------------------
 # Tensor-product queries
 # --------------------------------------------------------------------------
@@ -506,6 +529,23 @@ def test_termination_is_strictly_above_o_max(orc, ert, n_exp):
     A = 1 - 0.5 ** n_exp
     assert (res["nsamples"] == n_exp).all()
     np.testing.assert_array_equal(res["rgba"], np.full(res["rgba"].shape, A))
+
+
+@pytest.mark.parametrize("ert,ns,lo,hi", [(0.99225, 8, 7, 8), (0.992, 7, 7, 8)])
+def test_termination_tie_bracket_closed_form(orc, ert, ns, lo, hi):
+    """Sample opacity 1/2, so A_k = 1 - 2^-k exactly (A_6 = 0.984375,
+    A_7 = 0.9921875, A_8 = 0.99609375).  The exact march stops at the first
+    k with A_k > O_max; the bracket an FP32 march may stop in runs from the
+    first k with A_k > O_max - 2e-4 to the first with A_k > O_max + 2e-4.
+    O_max = 0.99225 puts A_7 just below the threshold (stop 8, bracket 7-8);
+    O_max = 0.992 puts it just above (stop 7, bracket 7-8)."""
+    ctrl = np.full((4, 4, 4), 0.5)
+    tf = _const_tf((1.0, 1.0, 1.0, 0.5))
+    res = orc.render(ctrl, 2, _ortho(), {"width": 2, "height": 2, "step": 1 / 16, "max_opacity": ert,
+                                         "tf": tf, "shading": 0})
+    assert (res["nsamples"] == ns).all()
+    assert (res["ns_lo"] == lo).all() and (res["ns_hi"] == hi).all()
+    np.testing.assert_array_equal(res["rgba"], np.full(res["rgba"].shape, 1 - 0.5 ** ns))
 
 
 def test_flat_field_takes_the_ambient_term_only(orc):
