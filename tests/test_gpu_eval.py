@@ -355,3 +355,20 @@ def test_async_host_query_beside_a_render(ctx, torch_cuda):
         np.testing.assert_array_equal(h_out.numpy(), ref_out)
         np.testing.assert_array_equal(h_img.numpy(), ref_img)
     ctx.unload_model(mid)
+
+
+def test_readme_python_example_runs(torch_cuda):
+    """The usage example in README.md runs as written and gives finite
+    queries and a non-empty image."""
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    text = open(os.path.join(root, "README.md")).read()
+    blocks = re.findall(r"```python\n(.*?)```", text, flags=re.S)
+    assert len(blocks) == 1
+    scope = {}
+    exec(compile(blocks[0], "README.md", "exec"), scope)
+    torch_cuda.cuda.synchronize()
+    out, img = scope["out"], scope["img"]
+    assert torch_cuda.isfinite(out).all() and torch_cuda.isfinite(img).all()
+    assert (img[..., 3] > 0).any()
