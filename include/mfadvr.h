@@ -95,7 +95,7 @@ typedef enum {
  * world box that maps onto the parameter box [0,1]^3. */
 typedef struct {
     int32_t degree[3];     /* p_d, 1..MFADVR_MAX_DEGREE, equal on all axes     */
-    int32_t ncp[3];        /* n_d >= p_d + 1, n_d <= 2^24                      */
+    int32_t ncp[3];        /* n_d >= p_d + 1, n_d <= 2^24, n0 n1 n2 < 2^31    */
     float box_min[3];      /* world box; box_max > box_min on every axis       */
     float box_max[3];
     const float *ctrl;     /* HOST, n0*n1*n2 finite FP32 values (u fastest)    */
@@ -135,8 +135,10 @@ typedef struct {
  * k = 0..N-1, N = floor((t_exit - t_enter)/step), [t_enter, t_exit] the part
  * of the ray inside the world box (t_enter >= 0). */
 typedef struct {
-    int32_t width, height;  /* > 0                                            */
-    float step;             /* constant sample distance, world units, > 0      */
+    int32_t width, height;  /* 1..65536 each, width * height <= 2^30          */
+    float step;             /* constant sample distance, world units, > 0, and
+                               at most 2^24 samples along the world box's
+                               diagonal (diagonal / step <= 2^24)              */
     float max_opacity;      /* O_max: stop after a sample makes A > O_max      */
     float ref_step;         /* opacity correction 1-(1-a)^(step/ref); <=0: off */
     const float *tf_rgba;   /* tf_size RGBA entries (DEVICE for mfadvr_render,
