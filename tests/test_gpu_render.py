@@ -209,6 +209,9 @@ def test_render_invalid_arguments(ctx, torch_cuda):
                      ({"kind": 1, "eye": (2, 2, 2), "fovy_deg": 180.0}, good),
                      ({"kind": 1, "eye": (2, 2, 2)}, dict(good, step=0.0)),
                      ({"kind": 1, "eye": (2, 2, 2)}, dict(good, width=0)),
+                     # refused on the host before any launch, so the 4 x 4 output is never written
+                     ({"kind": 1, "eye": (2, 2, 2)}, dict(good, width=65537)),
+                     ({"kind": 1, "eye": (2, 2, 2)}, dict(good, width=40000, height=40000)),
                      ({"kind": 1, "eye": (2, 2, 2)}, dict(good, shading=2))]:
         with pytest.raises(mfadvr.MfadvrError) as e:
             ctx.render(mid, cam, prm, tf, 4, img)
