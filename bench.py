@@ -27,10 +27,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes (read + write) of one render_kernel<3, float> launch on the
-# 128^3 workload from one ncu capture (profiles/render_kernel_gauss128_p3_persp1024.md),
-# valid only for the kernel sources it was taken on.
-RENDER_TRAFFIC = {"sources_sha256_16": "af74aa39e5094c0c", "bytes": 518120960}
+# DRAM bytes (read + write) of one render_kernel<3, PolyF32> launch (the power
+# form) on the 128^3 workload from one ncu capture
+# (profiles/render_kernel_gauss128_p3_persp1024.md), valid only for the kernel
+# sources it was taken on.
+RENDER_TRAFFIC = {"sources_sha256_16": "3ef3c511a20fb90a", "bytes": 517680896}
 RENDER_SOURCES = ("paper_2204_11762_gb300/csrc/render_kernels.cuh", "paper_2204_11762_gb300/csrc/mfa_basis.cuh",
                   "paper_2204_11762_gb300/csrc/mfa_internal.h")
 

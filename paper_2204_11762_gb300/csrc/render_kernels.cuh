@@ -187,6 +187,7 @@ __device__ __forceinline__ bool start_ray(const RenderSetup &rs, int px, int py,
         ray.kf[a] = -2.0f;  // forces a span lookup at the first sample
         ray.lo[a] = 2.0f;   // (general knots: an empty span)
         ray.hi[a] = -1.0f;
+        ray.kk[a] = 0;
     }
     ray.sf = 0.f;
     ray.Cr = ray.Cg = ray.Cb = ray.A = 0.f;
@@ -302,13 +303,27 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
     }
     if (moved) {
         if constexpr (NU) {
+            // Only the axes whose span no longer holds x are resolved.  A
+            // march leaves a span into its neighbour on that side, which two
+            // exact compares confirm (breakpoints strictly increase, so the
+            // span holding x is unique); anything else (a new ray, a skipped
+            // narrow span) takes the grid search.
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 x[a] = clamp01f(x[a]);
-                const int k = span_search(mv.brk[a], mv.cell[a], mv.grid[a], x[a]);
+                if (x[a] >= ray.lo[a] && x[a] < ray.hi[a]) continue;
+                const int last = mv.m[a] - 1;
+                int k = ray.kk[a] + (x[a] >= ray.hi[a] ? 1 : -1);
+                k = min(max(k, 0), last);
+                float lo = __ldg(mv.brk[a] + k), hi = __ldg(mv.brk[a] + k + 1);
+                if (!(ray.lo[a] <= ray.hi[a] && lo <= x[a] && (x[a] < hi || k == last))) {
+                    k = span_search(mv.brk[a], mv.cell[a], mv.grid[a], x[a]);
+                    lo = __ldg(mv.brk[a] + k);
+                    hi = __ldg(mv.brk[a] + k + 1);
+                }
                 ray.kk[a] = k;
-                ray.lo[a] = __ldg(mv.brk[a] + k);
-                ray.hi[a] = __ldg(mv.brk[a] + k + 1);
+                ray.lo[a] = lo;
+                ray.hi[a] = hi;
                 ray.ih[a] = __ldg(mv.ih[a] + k);
             }
         } else {
