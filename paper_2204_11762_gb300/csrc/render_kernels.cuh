@@ -230,20 +230,6 @@ __device__ __forceinline__ float lg2_approx(float x)
     return y;
 }
 
-// One iteration of the lane's ray, software-pipelined over two samples:
-// the span bookkeeping (with a cache reload when the span changed), basis
-// and contraction of sample sf, and the applyTFs, shading and compositing
-// of sample sf - 1, whose query the previous iteration left in ray.r.  The
-// two halves are independent, so the compiler interleaves the contraction's
-// FMAs with the serial TF / shading / compositing chain.  Early termination
-// is decided on the composited sample; the query of sample sf is then
-// dropped, as is the one past the last sample.  G: the gradient is queried
-// (shading on); without it the value-only contraction runs.  NU: general
-// knots, the ray walked in parameter units, the span found by binary search
-// on a span change and the basis taken from the span's pieces.  R: rational
-// model, the value f = A / W and its gradient (grad A - f grad W) / W from the
-// contractions of w P and of w.  Returns true when the ray is finished
-// (pixel written).
 // Loads the span block whose first row entry is `base` into the lane's cache
 // (and, for a rational model, the weights' block).
 template <int P, typename T, bool R>
@@ -275,6 +261,21 @@ __device__ __forceinline__ void reload_block(const ModelView &mv, int base, Span
     }
 }
 
+// One iteration of the lane's ray, software-pipelined over two samples:
+// the span bookkeeping (with a cache reload when the span changed), basis
+// and contraction of sample sf, and the applyTFs, shading and compositing
+// of sample sf - 1, whose query the previous iteration left in ray.r.  The
+// two halves are independent, so the compiler interleaves the contraction's
+// FMAs with the serial TF / shading / compositing chain.  Early termination
+// is decided on the composited sample; the query of sample sf is then
+// dropped, as is the one past the last sample.  G: the gradient is queried
+// (shading on); without it the value-only contraction runs.  NU: general
+// knots, the ray walked in parameter units; on a span change the axes that
+// left their span take the neighbouring span when two compares confirm it,
+// else a search of the span grid; the basis comes from the span's pieces.
+// R: rational model, the value f = A / W and its gradient
+// (grad A - f grad W) / W from the contractions of w P and of w.  Returns
+// true when the ray is finished (pixel written).
 template <int P, typename T, bool G, bool NU, bool R, typename Tf>
 __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSetup &rs, const Tf &tf, LaneRay &ray,
                                             SpanCache<P, T, R> &cache)
