@@ -109,6 +109,28 @@ def whole_job_value(units_per_rank_step: int, steps: int, max_ms: float, world: 
     return world * units_per_rank_step * steps / (max_ms / 1000.0)
 
 
+def measure_fma_peak(torch, dev, stream, iters=4096, reps=3):
+    """FP32 multiply-add throughput of this GPU from the library's probe
+    (mfadvr_probe_fma): best of `reps` launches, scalar and packed, timed with
+    CUDA events on `stream`.  Returns TFLOP/s (2 FLOP per multiply-add) per
+    form and the best."""
+    from paper_2204_11762_gb300 import mfadvr
+    sink = torch.zeros(1, dtype=torch.float32, device=dev)
+    out = {}
+    for packed in (False, True):
+        best = 0.0
+        for _ in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fmas = mfadvr.probe_fma(sink, iters, packed=packed, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            best = max(best, fmas * 2 / (e0.elapsed_time(e1) / 1000.0) / 1e12)
+        out["packed" if packed else "scalar"] = best
+    out["best"] = max(out.values())
+    return out
+
+
 def _measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -290,6 +312,7 @@ def run_ours(args, wl):
     render_ms = [e[0].elapsed_time(e[1]) for e in ev]
     eval_ms = [e[1].elapsed_time(e[2]) for e in ev]
     total_ms = sum(render_ms) + sum(eval_ms)
+    fma_probe = measure_fma_peak(torch, dev, stream)  # after the timed region, same stream and clocks
     assert int(d_ns.sum(dtype=torch.int64).item()) == render_samples, "sample count changed between steps"
 
     total_ms = max_over_ranks(total_ms, dev)
@@ -315,6 +338,11 @@ def run_ours(args, wl):
                 "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 FLOP x {sm_max_mhz:.0f} MHz",
                 "per_unit": f"{C_FMA[p]} FMA per sample (sum-factorised contraction, degree {p})",
                 "render_form": form}
+        roof["measured_peak"] = {"tflops": fma_probe["best"], "frac": render_tflops / fma_probe["best"],
+                                 "scalar_tflops": fma_probe["scalar"], "packed_tflops": fma_probe["packed"],
+                                 "source": "measured on this GPU in this run: mfadvr_probe_fma (8 independent "
+                                           "FMA chains per thread, full occupancy), best of 3 launches per form, "
+                                           "CUDA events on the bench stream right after the timed region"}
         if form == "power":
             ex = render_samples * POLY_FMA[p] * 2 / (r_mean / 1000.0) / 1e12
             roof["executed"] = {"fma_per_sample": POLY_FMA[p], "tflops": ex, "frac": ex / fma_peak_tflops,

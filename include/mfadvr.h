@@ -408,15 +408,39 @@ MFADVR_API mfadvr_status mfadvr_serve_trace(mfadvr_ctx *ctx, mfadvr_serve_trace_
  * corrupt each other's images.  Serialise them.
  * Set-up: the first call on a device, with that device current, looks up
  * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture on that device.  The work runs on the current
- * device and is asynchronous on `stream`.  Errors are read with
- * mfadvr_last_error(NULL). */
+ * before any stream capture on that device.  A cudaDeviceReset gives the
+ * device a new context, and the next call looks the address up again, so
+ * make a call outside any capture after a reset too.  The work runs on the
+ * current device and is asynchronous on `stream`; every buffer must be
+ * memory of that device (or managed memory), else MFADVR_EINVAL.  Errors
+ * are read with mfadvr_last_error(NULL). */
 #define MFADVR_NOALLOC_MAX_POINTS (1 << 19)
 MFADVR_API mfadvr_status mfadvr_render_lattice_noalloc(const float *ctrl_dev, const int32_t degree[3],
                                                        const int32_t ncp[3], const float box_min[3],
                                                        const float box_max[3], const mfadvr_camera *camera,
                                                        const mfadvr_render_params *params, float *rgba_dev,
                                                        int32_t *nsamples_dev, void *stream);
+
+/* FP32 multiply-add throughput probe.  The paper has no counterpart: this is
+ * a measurement.  The render and point-query kernels run on the FP32 FMA
+ * pipe, and a benchmark divides their multiply-adds per second by this
+ * call's, beside the peak derived from unit counts and clocks.
+ * Enqueues one kernel on `stream` (asynchronous) on the current device: one
+ * block of 256 threads per resident slot on every SM, each thread running
+ * eight independent multiply-add chains for `iters` loop iterations of 64
+ * chain steps, as scalar FMAs (packed = 0) or packed fma.rn.f32x2 pairs
+ * (packed = 1).  Time it with events on the same stream.
+ *  packed:    0 or 1.
+ *  iters:     1..2^24 loop iterations per thread.
+ *  sink_dev:  DEVICE, at least one float of the current device; written only
+ *             in a case that does not arise (it keeps the chains live).
+ *  fma_count: HOST, set to the multiply-adds the launch executes (2 FLOP
+ *             each).
+ * Errors (before any launch): EINVAL for NULL pointers, iters or packed out of
+ * range, or a sink that is not memory of the current device; ECUDA if the
+ * launch fails.  Read the message with mfadvr_last_error(NULL). */
+MFADVR_API mfadvr_status mfadvr_probe_fma(int32_t packed, int32_t iters, float *sink_dev, void *stream,
+                                          double *fma_count);
 
 /* Static text for a status code. */
 MFADVR_API const char *mfadvr_status_string(mfadvr_status status);

@@ -798,9 +798,12 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
         if (!why.empty()) return fail(ctx, MFADVR_EINVAL, "knots[%d]: %s", a, why.c_str());
     }
 
-    const uint64_t count = static_cast<uint64_t>(desc->ncp[0]) * desc->ncp[1] * desc->ncp[2];
-    if (count >= (uint64_t(1) << 31))
+    // n0 n1 <= 2^48 cannot wrap; the third side is checked by division so
+    // that no wrapped product of three sides passes the limit.
+    const uint64_t ncp01 = static_cast<uint64_t>(desc->ncp[0]) * static_cast<uint64_t>(desc->ncp[1]);
+    if (ncp01 > ((uint64_t(1) << 31) - 1) / static_cast<uint64_t>(desc->ncp[2]))
         return fail(ctx, MFADVR_EUNSUPPORTED, "lattices of 2^31 or more control points are not supported");
+    const uint64_t count = ncp01 * static_cast<uint64_t>(desc->ncp[2]);
     float pmin = INFINITY, pmax = -INFINITY, pabs = 0.0f;
     for (uint64_t i = 0; i < count; ++i) {
         const float v = desc->ctrl[i];

@@ -33,8 +33,10 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void *g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // context id the address was looked up in
 
-bool device_pointer(const void *p)
+// Device memory of device `dev` (managed memory is reachable from any device).
+bool device_pointer(const void *p, int dev)
 {
     if (!p) return false;
     cudaPointerAttributes attr;
@@ -42,7 +44,37 @@ bool device_pointer(const void *p)
         cudaGetLastError();
         return false;
     }
-    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+    return (attr.type == cudaMemoryTypeDevice && attr.device == dev) || attr.type == cudaMemoryTypeManaged;
+}
+
+// Unique id of the calling thread's current CUDA context, 0 if none or if the
+// driver entry points cannot be found.  A cudaDeviceReset destroys the
+// primary context; the next one gets a new id, so a cached symbol address is
+// looked up again instead of being used stale.
+unsigned long long current_context_id()
+{
+    using GetCurrent = int (*)(void **);
+    using GetId = int (*)(void *, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &f, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPoint("cuCtxGetId", &f, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    void *c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != 0 || !c || get_id(c, &id) != 0) return 0;
+    return id;
 }
 
 mfadvr_status err(mfadvr_status st, const char *msg) { return mfadvr::fail_noctx(st, msg); }
@@ -65,11 +97,13 @@ extern "C" MFADVR_API mfadvr_status mfadvr_render_lattice_noalloc(
             return err(MFADVR_EINVAL, "box_max must exceed box_min on every axis");
         n[a] = ncp[a];
     }
-    const unsigned long long points = static_cast<unsigned long long>(n[0]) * n[1] * n[2];
-    if (points > MFADVR_NOALLOC_MAX_POINTS) {
-        char msg[160];
-        snprintf(msg, sizeof msg, "lattice of %llu control points exceeds the allocation-free scratch (at most %d)",
-                 points, MFADVR_NOALLOC_MAX_POINTS);
+    // n0 n1 <= 2^48 cannot wrap in 64 bits; the third factor is checked by
+    // division, so that no product of three sides wraps past the limit.
+    const unsigned long long n01 = static_cast<unsigned long long>(n[0]) * static_cast<unsigned long long>(n[1]);
+    if (n01 > static_cast<unsigned long long>(MFADVR_NOALLOC_MAX_POINTS) / static_cast<unsigned long long>(n[2])) {
+        char msg[200];
+        snprintf(msg, sizeof msg, "lattice of %d x %d x %d control points exceeds the allocation-free scratch "
+                 "(at most %d)", n[0], n[1], n[2], MFADVR_NOALLOC_MAX_POINTS);
         return err(MFADVR_ENOMEM, msg);
     }
     if (std::isnan(params->tf_lo) || std::isnan(params->tf_hi))
@@ -86,16 +120,18 @@ extern "C" MFADVR_API mfadvr_status mfadvr_render_lattice_noalloc(
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return err(MFADVR_ECUDA, "no usable current device");
-    if (!device_pointer(ctrl_dev) || !device_pointer(params->tf_rgba) || !device_pointer(rgba_dev) ||
-        (nsamples_dev && !device_pointer(nsamples_dev)))
-        return err(MFADVR_EINVAL, "ctrl, tf_rgba, rgba and nsamples must be device pointers");
+    if (!device_pointer(ctrl_dev, dev) || !device_pointer(params->tf_rgba, dev) || !device_pointer(rgba_dev, dev) ||
+        (nsamples_dev && !device_pointer(nsamples_dev, dev)))
+        return err(MFADVR_EINVAL, "ctrl, tf_rgba, rgba and nsamples must be memory of the current device");
 
-    // Set-up, once per device and with that device current: the device
-    // address of the scratch array (its host-side name is only a stand-in).
+    // Set-up, once per device (and again after a cudaDeviceReset replaced
+    // its context), with that device current: the device address of the
+    // scratch array (its host-side name is only a stand-in).
     void *scratch = nullptr;
     {
         std::lock_guard<std::mutex> g(g_setup_mu);
-        if (!g_scratch_ptr[dev]) {
+        const unsigned long long ctx_id = current_context_id();
+        if (!g_scratch_ptr[dev] || ctx_id != g_scratch_ctx[dev]) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) {
@@ -103,6 +139,7 @@ extern "C" MFADVR_API mfadvr_status mfadvr_render_lattice_noalloc(
                 return err(MFADVR_ECUDA, "cudaGetSymbolAddress of the allocation-free scratch failed");
             }
             g_scratch_ptr[dev] = p;
+            g_scratch_ctx[dev] = current_context_id();  // the lookup made the context current if none was
         }
         scratch = g_scratch_ptr[dev];
     }

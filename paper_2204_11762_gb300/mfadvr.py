@@ -34,7 +34,7 @@ EXPORTS = ("mfadvr_create", "mfadvr_destroy", "mfadvr_load_model", "mfadvr_unloa
            "mfadvr_status_string", "mfadvr_last_error", "mfadvr_render_lattice_noalloc", "mfadvr_render_batch",
            "mfadvr_autotune", "mfadvr_tuning_save", "mfadvr_tuning_load", "mfadvr_serve_start", "mfadvr_serve_stop",
            "mfadvr_submit", "mfadvr_wait", "mfadvr_serve_stats", "mfadvr_serve_trace", "mfadvr_query_points",
-           "mfadvr_query_points_host", "mfadvr_query_points_host_async")
+           "mfadvr_query_points_host", "mfadvr_query_points_host_async", "mfadvr_probe_fma")
 MAX_BATCH = 256
 NOALLOC_MAX_POINTS = 1 << 19
 
@@ -140,6 +140,8 @@ def load_library(build_if_missing: bool = True):
     L.mfadvr_render_lattice_noalloc.argtypes = [vp, P(i3), P(i3), P(f3), P(f3), P(Camera), P(RenderParams),
                                                 vp, vp, vp]
     L.mfadvr_render_lattice_noalloc.restype = i32
+    L.mfadvr_probe_fma.argtypes = [i32, i32, vp, vp, P(ctypes.c_double)]
+    L.mfadvr_probe_fma.restype = i32
     L.mfadvr_status_string.argtypes = [i32]
     L.mfadvr_status_string.restype = ctypes.c_char_p
     L.mfadvr_last_error.argtypes = [vp]
@@ -220,6 +222,17 @@ def render_lattice_noalloc(ctrl_dev, degree: int, ncp, camera: dict, params: dic
                                          ctypes.byref(prm), _ptr(rgba_dev), _ptr(nsamples_dev), _stream(stream))
     if st != OK:
         raise MfadvrError(st, L.mfadvr_last_error(None).decode())
+
+
+def probe_fma(sink_dev, iters: int, packed: bool = True, stream=None) -> float:
+    """mfadvr_probe_fma: enqueue the FP32 multiply-add throughput probe on
+    `stream` (current device); returns the multiply-adds the launch runs."""
+    L = load_library()
+    n = ctypes.c_double(0.0)
+    st = L.mfadvr_probe_fma(int(bool(packed)), int(iters), _ptr(sink_dev), _stream(stream), ctypes.byref(n))
+    if st != OK:
+        raise MfadvrError(st, L.mfadvr_last_error(None).decode())
+    return n.value
 
 
 class Context:

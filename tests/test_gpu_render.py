@@ -229,6 +229,26 @@ def test_render_invalid_arguments(ctx, torch_cuda):
     ctx.unload_model(mid)
 
 
+def test_load_model_rejects_sides_whose_product_wraps(ctx, torch_cuda):
+    """Sides of 2^24 x 2^24 x 2^16 control points multiply to 2^64, 0 in 64-bit
+    arithmetic; load_model must refuse them before reading the lattice."""
+    import ctypes
+
+    from paper_2204_11762_gb300 import mfadvr
+    tiny = np.zeros(8, dtype=np.float32)
+    d = mfadvr.ModelDesc()
+    d.degree[:] = [3, 3, 3]
+    d.ncp[:] = [1 << 24, 1 << 24, 1 << 16]
+    d.box_min[:] = [0.0, 0.0, 0.0]
+    d.box_max[:] = [1.0, 1.0, 1.0]
+    d.ctrl = tiny.ctypes.data
+    d.storage = 0
+    mid = ctypes.c_int32(-1)
+    st = ctx._L.mfadvr_load_model(ctx._h, ctypes.byref(d), ctypes.byref(mid))
+    assert st == mfadvr.EUNSUPPORTED
+    assert mid.value == -1
+
+
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 def test_full_size_value_noise_sampled_rows(ctx, torch_cuda, orc, storage):
     """Degree 4, 512^3 value-noise model, 3840x2160 perspective frame at step

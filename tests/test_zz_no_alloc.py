@@ -73,3 +73,21 @@ def test_noalloc_rejects_oversize_lattice(torch_cuda):
         mfadvr.render_lattice_noalloc(d_ctrl, 3, n, {"kind": 1, "eye": (2, 2, 2)}, prm, d_tf, 4, img)
     assert e.value.status == mfadvr.ENOMEM
     assert "exceeds the allocation-free scratch" in str(e.value)
+
+
+def test_noalloc_rejects_sides_whose_product_wraps(torch_cuda):
+    """Sides of 2^24 x 2^24 x 2^16 control points multiply to 2^64, which is 0
+    in 64-bit arithmetic; the call must refuse them before any launch
+    rather than let a wrapped count pass the size limit."""
+    from paper_2204_11762_gb300 import mfadvr
+    torch = torch_cuda
+    dev = torch.device("cuda:0")
+    n = (1 << 24, 1 << 24, 1 << 16)
+    d_ctrl = torch.zeros(64, device=dev)
+    d_tf = torch.ones((4, 4), device=dev)
+    img = torch.empty((8, 8, 4), device=dev)
+    prm = {"width": 8, "height": 8, "step": 0.05, "tf_lo": 0.0, "tf_hi": 1.0}
+    with pytest.raises(mfadvr.MfadvrError) as e:
+        mfadvr.render_lattice_noalloc(d_ctrl, 3, n, {"kind": 1, "eye": (2, 2, 2)}, prm, d_tf, 4, img)
+    assert e.value.status == mfadvr.ENOMEM
+    torch.cuda.synchronize()
