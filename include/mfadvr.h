@@ -79,7 +79,9 @@ typedef enum { MFADVR_F32 = 0, MFADVR_F16 = 1, MFADVR_BF16 = 2 } mfadvr_dtype;
  * cell: at degree 3 and 128^3 control points 500 MB beside the 67 MB row
  * array (twice that for a rational model: the polynomials of w P and of
  * w).  It applies to FP32 models of degree <= 3 (uniform or general knots,
- * plain or rational) and to plain ones of degree 4, and serves shaded
+ * plain or rational) and to plain ones of degree 4, with fewer than 2^22
+ * spans per axis (a sample is placed by its FP32 offset from the span's
+ * centre, index + 1/2, exact below that), and serves shaded
  * renders; unshaded ones
  * (value only) run the B-spline kernel on the row array, which is faster
  * there.  Results agree with the B-spline form to FP32 rounding. */

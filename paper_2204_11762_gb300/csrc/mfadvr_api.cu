@@ -863,13 +863,17 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
     // POWER render form: span polynomials beside the row array, where the
     // model allows them (AUTO: and where they fit the budget).
     // degree 4: plain models only (a rational one keeps no register cache there)
-    const bool poly_ok = m.dtype == MFADVR_F32 && (m.p <= 3 || (m.p == 4 && !m.rational));
+    // The kernels place a sample by its offset from the span's centre, index
+    // + 1/2, exact in FP32 below 2^22 spans per axis.
+    const bool poly_ok = m.dtype == MFADVR_F32 && (m.p <= 3 || (m.p == 4 && !m.rational)) &&
+                         m.n[0] - m.p < (1 << 22) && m.n[1] - m.p < (1 << 22) && m.n[2] - m.p < (1 << 22);
     const uint64_t poly_b = poly_ok ? static_cast<uint64_t>(m.n[0] - m.p) * (m.n[1] - m.p) * (m.n[2] - m.p) *
                                           static_cast<uint64_t>(poly_cell_bytes(m.p)) * (m.rational ? 2 : 1)
                                     : 0;
     if (desc->render_form == MFADVR_FORM_POWER && !poly_ok)
         return fail(ctx, MFADVR_EUNSUPPORTED,
-                    "the power render form needs FP32 storage and degree <= 3 (degree 4: without weights)");
+                    "the power render form needs FP32 storage, degree <= 3 (degree 4: without weights) and "
+                    "fewer than 2^22 spans per axis");
     const bool poly_fits = !ctx->budget || ctx->used + m.bytes + poly_b <= ctx->budget;
     if (desc->render_form == MFADVR_FORM_POWER && !poly_fits)
         return fail(ctx, MFADVR_ENOMEM, "span polynomials of %llu bytes exceed the HBM budget",
