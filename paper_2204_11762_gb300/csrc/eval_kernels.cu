@@ -70,7 +70,7 @@ __global__ void build_poly_kernel(const float *__restrict__ src, float2 *__restr
                                   const double *__restrict__ cp0, const double *__restrict__ cp1,
                                   const double *__restrict__ cp2)
 {
-    constexpr int K = P + 1, JP = Block<P>::JP, S = PolyCell<P>::kSectors;
+    constexpr int K = P + 1, S = PolyCell<P>::kSectors;
     const int m0 = n0 - P, m1 = n1 - P, m2 = n2 - P;
     const int64_t cells = static_cast<int64_t>(m0) * m1 * m2;
     for (int64_t cell = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; cell < cells;
@@ -105,13 +105,13 @@ __global__ void build_poly_kernel(const float *__restrict__ src, float2 *__restr
                 }
         float2 *out = poly + cell * (4 * S);
         for (int f = 0; f < 4 * S; ++f) {
-            const int c = f / (JP * K), h = (f / K) % JP, a = f % K;
+            const int g = f / (K * K), b = (f / K) % K, a = f % K;
             float2 pr = make_float2(0.0f, 0.0f);
             if (f < PolyCell<P>::kPairs) {
-                double lo = 0.0, hi = 0.0;  // A[a][2h][c], A[a][2h+1][c]
+                double lo = 0.0, hi = 0.0;  // A[a][b][2g], A[a][b][2g+1]
                 for (int q = 0; q < K; ++q) {
-                    lo += cw[q][c] * w[a][2 * h][q];
-                    if (2 * h + 1 < K) hi += cw[q][c] * w[a][2 * h + 1][q];
+                    lo += cw[q][2 * g] * w[a][b][q];
+                    if (2 * g + 1 < K) hi += cw[q][2 * g + 1] * w[a][b][q];
                 }
                 pr = make_float2(static_cast<float>(lo), static_cast<float>(hi));
             }

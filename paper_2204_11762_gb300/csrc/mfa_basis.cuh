@@ -605,9 +605,11 @@ __device__ __forceinline__ void contract(const float Nu[P + 1], const float dNu[
 //   A[a][b][c] = sum_{r,s,q} Cu[r][a] Cv[s][b] Cw[q][c] P(i+r, j+s, k+q),
 // where C[r][e] is the coefficient of t^e in BasisScale N_r on the span: the
 // span's pieces (pieces_from_knots on its knots, uniform or general), shifted
-// to the centre.  A cell stores the pairs (A[a][2h][c], A[a][2h+1][c]) in the
-// order [c][h][a], the last h padded with 0 when P is even, in whole 32-byte
-// sectors: the order of the render kernel's span cache.
+// to the centre.  A cell stores the pairs (A[a][b][2g], A[a][b][2g+1]) (two
+// tw powers) in the order [g][b][a], the last g padded with 0 when P is even,
+// in whole 32-byte sectors: the order of the render kernel's span cache,
+// whose flat pair index is (g (P+1) + b) (P+1) + a.  Pairing along tw lets
+// both the tu and the tv Horner levels run on packed FMAs.
 // ---------------------------------------------------------------------------
 template <int P>
 struct PolyCell {
@@ -619,7 +621,8 @@ static_assert(PolyCell<1>::kSectors * 32 == poly_cell_bytes(1) && PolyCell<2>::k
                   PolyCell<3>::kSectors * 32 == poly_cell_bytes(3) && PolyCell<4>::kSectors * 32 == poly_cell_bytes(4),
               "span-polynomial cell sizes of host and device differ");
 
-// Loads span cell `cell` of the polynomial array into v[c][h][a] (PolyCell).
+// Loads span cell `cell` of the polynomial array into the lane's cache, pair
+// f of the cell to flat element f of v (PolyCell).
 template <int P>
 __device__ __forceinline__ void load_poly(const float *poly, int64_t cell, float2 (&v)[P + 1][Block<P>::JP][P + 1])
 {
@@ -634,43 +637,45 @@ __device__ __forceinline__ void load_poly(const float *poly, int64_t cell, float
 
 // Value and local gradient (times BasisScale^3, like contract<P, kQueryBoth>)
 // of a span cell's polynomial at centred coordinates (tu, tv, tw) in
-// [-1/2, 1/2]: Horner's rule in tu on the coefficient pairs (packed, two tv
-// powers per instruction), then in tv for each tw power, then in tw; each
+// [-1/2, 1/2]: per pair of tw powers, Horner's rule in tu on the coefficient
+// pairs, then in tv, both on packed FMAs; then, per tw power, in tw.  Each
 // level carries the derivative sums the gradient needs (for p(t) = sum A_e
-// t^e, the recurrences p <- p t + A_e and d <- d t + p give p and p').  At
-// degree 3: 40 packed and 43 scalar multiply-adds.
+// t^e, the recurrences p <- p t + A_e and d <- d t + p give p and p').
+// pair(f) is the cache's flat pair f = (g (P+1) + b) (P+1) + a.  At degree 3:
+// 56 packed and 11 scalar multiply-adds.
 template <int P, typename PairAt>
 __device__ __forceinline__ void contract_poly(PairAt pair, float tu, float tv, float tw, float r[4])
 {
-    constexpr int JP = Block<P>::JP;
-    const float2 uu = make_float2(tu, tu);
-    float Fv[P + 1], Fu[P + 1], Fvv[P + 1];  // per tw power: value, d/du and d/dv of the (u, v) polynomial
+    constexpr int K = P + 1, CP = Block<P>::JP;
+    const float2 uu = make_float2(tu, tu), vv = make_float2(tv, tv);
+    float Fv[2 * CP], Fu[2 * CP], Fvv[2 * CP];  // per tw power: value, d/du and d/dv of the (u, v) polynomial
 #pragma unroll
-    for (int c = 0; c <= P; ++c) {
-        float pv[2 * JP], pu[2 * JP];
+    for (int g = 0; g < CP; ++g) {
+        float2 pv[K], pu[K];
 #pragma unroll
-        for (int h = 0; h < JP; ++h) {
-            float2 p = pair(c, h, P), d = p;
+        for (int b = 0; b < K; ++b) {
+            float2 p = pair((g * K + b) * K + P), d = p;
 #pragma unroll
             for (int a = P - 1; a >= 0; --a) {
                 if (a < P - 1) d = __ffma2_rn(d, uu, p);
-                p = __ffma2_rn(p, uu, pair(c, h, a));
+                p = __ffma2_rn(p, uu, pair((g * K + b) * K + a));
             }
-            pv[2 * h] = p.x;
-            pv[2 * h + 1] = p.y;
-            pu[2 * h] = d.x;
-            pu[2 * h + 1] = d.y;
+            pv[b] = p;
+            pu[b] = d;
         }
-        float q = pv[P], qv = q, qu = pu[P];
+        float2 q = pv[P], qv = q, qu = pu[P];
 #pragma unroll
         for (int b = P - 1; b >= 0; --b) {
-            if (b < P - 1) qv = fmaf(qv, tv, q);
-            qu = fmaf(qu, tv, pu[b]);
-            q = fmaf(q, tv, pv[b]);
+            if (b < P - 1) qv = __ffma2_rn(qv, vv, q);
+            qu = __ffma2_rn(qu, vv, pu[b]);
+            q = __ffma2_rn(q, vv, pv[b]);
         }
-        Fv[c] = q;
-        Fvv[c] = qv;
-        Fu[c] = qu;
+        Fv[2 * g] = q.x;
+        Fv[2 * g + 1] = q.y;
+        Fvv[2 * g] = qv.x;
+        Fvv[2 * g + 1] = qv.y;
+        Fu[2 * g] = qu.x;
+        Fu[2 * g + 1] = qu.y;
     }
     float f = Fv[P], fw = f, fv = Fvv[P], fu = Fu[P];
 #pragma unroll

@@ -474,9 +474,9 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
     // ---- query of sample s (composited by the next iteration) -------------
     constexpr int Q = G ? kQueryBoth : kQueryValue;
     if constexpr (kCentred) {
-        contract_poly<P>([&](int k, int jp, int i) { return cache.v[k][jp][i]; }, x[0], x[1], x[2], ray.r);
+        contract_poly<P>([&](int f) { return (&cache.v[0][0][0])[f]; }, x[0], x[1], x[2], ray.r);
     } else if constexpr (kPoly) {
-        contract_poly<P>([&](int k, int jp, int i) { return cache.v[k][jp][i]; }, x[0] - 0.5f, x[1] - 0.5f,
+        contract_poly<P>([&](int f) { return (&cache.v[0][0][0])[f]; }, x[0] - 0.5f, x[1] - 0.5f,
                          x[2] - 0.5f, ray.r);
     } else if constexpr (kCache) {
         contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return cache.pair(k, jp, i); }, ray.r);
@@ -489,9 +489,9 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
         {
             float rw[4];
             if constexpr (kCentred) {
-                contract_poly<P>([&](int k, int jp, int i) { return cache.w[k][jp][i]; }, x[0], x[1], x[2], rw);
+                contract_poly<P>([&](int f) { return (&cache.w[0][0][0])[f]; }, x[0], x[1], x[2], rw);
             } else if constexpr (kPoly) {
-                contract_poly<P>([&](int k, int jp, int i) { return cache.w[k][jp][i]; }, x[0] - 0.5f, x[1] - 0.5f,
+                contract_poly<P>([&](int f) { return (&cache.w[0][0][0])[f]; }, x[0] - 0.5f, x[1] - 0.5f,
                                  x[2] - 0.5f, rw);
             } else if constexpr (kCache) {
                 contract<P, Q>(Nu, dNu, Nv, dNv, Nw, dNw, [&](int k, int jp, int i) { return cache.wpair(k, jp, i); },
@@ -611,8 +611,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P, T, NU, R>::value)
     SpanCache<P, T, R> cache;
 
     for (;;) {
+        // as in render_kernel: rays are handed out only to a wholly idle warp
         const unsigned need = __ballot_sync(kFull, idle);
-        if (need) {
+        if (need == kFull) {
             if (pool_next >= pool_end && held < 0 && !exhausted) {
                 int t = 0;
                 if (lane == 0) t = atomicAdd(counter, 1);
