@@ -57,7 +57,7 @@ struct RenderSetup {
     int correct_opacity;                // 1 when step != ref_step
     const float4 *tf;                   // device table, tf_size >= 2 entries
     int tf_size;
-    // table coordinate of a contraction result r: clamp(r*tf_a + tf_b, 0, tf_size-1)
+    // table coordinate of a contraction result r: clamp(r*tf_a + tf_b, 0, 1) (tf_size-1)
     // (folds the storage scale, the basis scale and [lo, hi] into one FMA)
     float tf_a, tf_b;
     int shading;

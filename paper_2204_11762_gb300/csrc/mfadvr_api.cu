@@ -217,8 +217,8 @@ mfadvr_status make_setup(mfadvr_ctx *ctx, const Model &m, const mfadvr_camera *c
     const double hi = std::isnan(rp->tf_hi) ? m.pmax : rp->tf_hi;
     const double last = rp->tf_size > 1 ? rp->tf_size - 1 : 1;
     const double inv_range = hi > lo ? 1.0 / (hi - lo) : 0.0;
-    rs->tf_a = static_cast<float>((m.rational ? 1.0 : static_cast<double>(m.scale) / bs3) * inv_range * last);
-    rs->tf_b = static_cast<float>(-lo * inv_range * last);
+    rs->tf_a = static_cast<float>((m.rational ? 1.0 : static_cast<double>(m.scale) / bs3) * inv_range);
+    rs->tf_b = static_cast<float>(-lo * inv_range);
     rs->shading = rp->shading;
     rs->ka = rp->ka;
     rs->kd = rp->kd;
@@ -1172,7 +1172,9 @@ mfadvr_status mfadvr_autotune(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_ca
             rs.tile_w_log2 = ilog2_u64(static_cast<uint64_t>(tw));
             rs.ctas_per_sm = c;
             float ms_best = INFINITY;
-            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+            // the fastest of 7 launches after a warm-up one: neighbouring
+            // shapes differ by about 1-2%, which 3 launches did not resolve
+            for (int rep = 0; rep < 8 && e == cudaSuccess; ++rep) {
                 int *counter = nullptr;
                 if (mfadvr_status st = next_counter(ctx, &counter)) {
                     cudaEventDestroy(e0);

@@ -428,7 +428,7 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
     // -infinity (2^23 + floor(xt) exactly, for 0 <= xt < 2^23), whose bits
     // hold the integer; the subtraction of 2^23 is exact.  No conversion
     // instructions on the serial TF chain.
-    const float xt = fminf(fmaxf(fmaf(r[0], rs.tf_a, rs.tf_b), 0.0f), static_cast<float>(rs.tf_size - 1));
+    const float xt = __saturatef(fmaf(r[0], rs.tf_a, rs.tf_b)) * static_cast<float>(rs.tf_size - 1);
     const float it23 = fminf(__fadd_rd(xt, 8388608.0f), 8388608.0f + static_cast<float>(rs.tf_size - 2));
     const int it = __float_as_int(it23) - 0x4B000000;
     const float fr = xt - (it23 - 8388608.0f);
@@ -437,7 +437,7 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
     float cr = fmaf(fr, td.x, ta.x);
     float cg = fmaf(fr, td.y, ta.y);
     float cb = fmaf(fr, td.z, ta.z);
-    float alpha = clamp01f(fmaf(fr, td.w, ta.w));
+    float alpha = __saturatef(fmaf(fr, td.w, ta.w));
     const float corrected = 1.0f - ex2_approx(lg2_approx(1.0f - alpha) * rs.opacity_ratio);
     alpha = rs.correct_opacity ? corrected : alpha;
     alpha = s > 0.0f ? alpha : 0.0f;  // no sample before the first
@@ -448,19 +448,17 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
         const float gy = r[2] * rs.grad_scale[1];
         const float gz = r[3] * rs.grad_scale[2];
         const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-        const float ndl =
-            fminf(fabsf(fmaf(gx, ray.dir[0], fmaf(gy, ray.dir[1], gz * ray.dir[2]))) * rsqrtf(g2), 1.0f);
+        const float ndl = __saturatef(fabsf(fmaf(gx, ray.dir[0], fmaf(gy, ray.dir[1], gz * ray.dir[2]))) * rsqrtf(g2));
         // a flat gradient (|g| at or below the threshold) shades ambient-only,
         // unclamped: c ka; otherwise c (ka + kd ndl) + ks ndl^shininess,
         // clamped to [0, 1]
         const bool flat = g2 <= rs.gthresh2;
-        const float spec = flat ? 0.0f : rs.ks * __powf(ndl, rs.shininess);
-        const float diff = flat ? rs.ka : fmaf(rs.kd, ndl, rs.ka);
-        const float lo = flat ? -INFINITY : 0.0f, hi = flat ? INFINITY : 1.0f;
+        const float spec = rs.ks * __powf(ndl, rs.shininess);
+        const float diff = fmaf(rs.kd, ndl, rs.ka);
         if constexpr (G) {  // the gradient is queried exactly when shading is on
-            cr = fminf(fmaxf(fmaf(cr, diff, spec), lo), hi);
-            cg = fminf(fmaxf(fmaf(cg, diff, spec), lo), hi);
-            cb = fminf(fmaxf(fmaf(cb, diff, spec), lo), hi);
+            cr = flat ? cr * rs.ka : __saturatef(fmaf(cr, diff, spec));
+            cg = flat ? cg * rs.ka : __saturatef(fmaf(cg, diff, spec));
+            cb = flat ? cb * rs.ka : __saturatef(fmaf(cb, diff, spec));
         }
     }
 
