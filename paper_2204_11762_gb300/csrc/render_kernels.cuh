@@ -280,7 +280,11 @@ __device__ __forceinline__ void reload_block(const ModelView &mv, int base, Span
 // R: rational model, the value f = A / W and its gradient
 // (grad A - f grad W) / W from the contractions of w P and of w.  Returns
 // true when the ray is finished (pixel written).
-template <int P, typename T, bool G, bool NU, bool R, typename Tf>
+// Which sample of its ray an iteration may be at: any (a sample s = 0 has no
+// predecessor to composite), the first (contract only), or a later one.
+enum StepMode { kStepAny = 0, kStepFirst = 1, kStepLater = 2 };
+
+template <int P, typename T, bool G, bool NU, bool R, int MODE, typename Tf>
 __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSetup &rs, const Tf &tf, LaneRay &ray,
                                             SpanCache<P, T, R> &cache)
 {
@@ -422,52 +426,54 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
     }
 
     // ---- applyTFs on sample s - 1: linear interpolation in the table -------
-    const float r[4] = {ray.r[0], ray.r[1], ray.r[2], ray.r[3]};
-    // Table coordinate xt in [0, N-1]; entry floor(xt), capped at N-2, and
-    // the fraction past it.  The floor comes from one add rounded toward
-    // -infinity (2^23 + floor(xt) exactly, for 0 <= xt < 2^23), whose bits
-    // hold the integer; the subtraction of 2^23 is exact.  No conversion
-    // instructions on the serial TF chain.
-    const float xt = __saturatef(fmaf(r[0], rs.tf_a, rs.tf_b)) * static_cast<float>(rs.tf_size - 1);
-    const float it23 = fminf(__fadd_rd(xt, 8388608.0f), 8388608.0f + static_cast<float>(rs.tf_size - 2));
-    const int it = __float_as_int(it23) - 0x4B000000;
-    const float fr = xt - (it23 - 8388608.0f);
-    float4 ta, td;
-    tf.at(it, ta, td);
-    float cr = fmaf(fr, td.x, ta.x);
-    float cg = fmaf(fr, td.y, ta.y);
-    float cb = fmaf(fr, td.z, ta.z);
-    float alpha = __saturatef(fmaf(fr, td.w, ta.w));
-    const float corrected = 1.0f - ex2_approx(lg2_approx(1.0f - alpha) * rs.opacity_ratio);
-    alpha = rs.correct_opacity ? corrected : alpha;
-    alpha = s > 0.0f ? alpha : 0.0f;  // no sample before the first
+    if constexpr (MODE != kStepFirst) {
+        const float r[4] = {ray.r[0], ray.r[1], ray.r[2], ray.r[3]};
+        // Table coordinate xt in [0, N-1]; entry floor(xt), capped at N-2, and
+        // the fraction past it.  The floor comes from one add rounded toward
+        // -infinity (2^23 + floor(xt) exactly, for 0 <= xt < 2^23), whose bits
+        // hold the integer; the subtraction of 2^23 is exact.  No conversion
+        // instructions on the serial TF chain.
+        const float xt = __saturatef(fmaf(r[0], rs.tf_a, rs.tf_b)) * static_cast<float>(rs.tf_size - 1);
+        const float it23 = fminf(__fadd_rd(xt, 8388608.0f), 8388608.0f + static_cast<float>(rs.tf_size - 2));
+        const int it = __float_as_int(it23) - 0x4B000000;
+        const float fr = xt - (it23 - 8388608.0f);
+        float4 ta, td;
+        tf.at(it, ta, td);
+        float cr = fmaf(fr, td.x, ta.x);
+        float cg = fmaf(fr, td.y, ta.y);
+        float cb = fmaf(fr, td.z, ta.z);
+        float alpha = __saturatef(fmaf(fr, td.w, ta.w));
+        const float corrected = 1.0f - ex2_approx(lg2_approx(1.0f - alpha) * rs.opacity_ratio);
+        alpha = rs.correct_opacity ? corrected : alpha;
+        if constexpr (MODE == kStepAny) alpha = s > 0.0f ? alpha : 0.0f;  // no sample before the first
 
-    // ---- shading: Blinn-Phong, headlight L = V = -d, two-sided -------------
-    {
-        const float gx = r[1] * rs.grad_scale[0];
-        const float gy = r[2] * rs.grad_scale[1];
-        const float gz = r[3] * rs.grad_scale[2];
-        const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-        const float ndl = __saturatef(fabsf(fmaf(gx, ray.dir[0], fmaf(gy, ray.dir[1], gz * ray.dir[2]))) * rsqrtf(g2));
-        // a flat gradient (|g| at or below the threshold) shades ambient-only,
-        // unclamped: c ka; otherwise c (ka + kd ndl) + ks ndl^shininess,
-        // clamped to [0, 1]
-        const bool flat = g2 <= rs.gthresh2;
-        const float spec = rs.ks * __powf(ndl, rs.shininess);
-        const float diff = fmaf(rs.kd, ndl, rs.ka);
-        if constexpr (G) {  // the gradient is queried exactly when shading is on
-            cr = flat ? cr * rs.ka : __saturatef(fmaf(cr, diff, spec));
-            cg = flat ? cg * rs.ka : __saturatef(fmaf(cg, diff, spec));
-            cb = flat ? cb * rs.ka : __saturatef(fmaf(cb, diff, spec));
+        // ---- shading: Blinn-Phong, headlight L = V = -d, two-sided -------------
+        {
+            const float gx = r[1] * rs.grad_scale[0];
+            const float gy = r[2] * rs.grad_scale[1];
+            const float gz = r[3] * rs.grad_scale[2];
+            const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+            const float ndl = __saturatef(fabsf(fmaf(gx, ray.dir[0], fmaf(gy, ray.dir[1], gz * ray.dir[2]))) * rsqrtf(g2));
+            // a flat gradient (|g| at or below the threshold) shades ambient-only,
+            // unclamped: c ka; otherwise c (ka + kd ndl) + ks ndl^shininess,
+            // clamped to [0, 1]
+            const bool flat = g2 <= rs.gthresh2;
+            const float spec = rs.ks * __powf(ndl, rs.shininess);
+            const float diff = fmaf(rs.kd, ndl, rs.ka);
+            if constexpr (G) {  // the gradient is queried exactly when shading is on
+                cr = flat ? cr * rs.ka : __saturatef(fmaf(cr, diff, spec));
+                cg = flat ? cg * rs.ka : __saturatef(fmaf(cg, diff, spec));
+                cb = flat ? cb * rs.ka : __saturatef(fmaf(cb, diff, spec));
+            }
         }
-    }
 
-    // ---- front-to-back compositing of sample s - 1 -------------------------
-    const float wgt = (1.0f - ray.A) * alpha;
-    ray.Cr = fmaf(wgt, cr, ray.Cr);
-    ray.Cg = fmaf(wgt, cg, ray.Cg);
-    ray.Cb = fmaf(wgt, cb, ray.Cb);
-    ray.A += wgt;
+        // ---- front-to-back compositing of sample s - 1 -------------------------
+        const float wgt = (1.0f - ray.A) * alpha;
+        ray.Cr = fmaf(wgt, cr, ray.Cr);
+        ray.Cg = fmaf(wgt, cg, ray.Cg);
+        ray.Cb = fmaf(wgt, cb, ray.Cb);
+        ray.A += wgt;
+    }
 
     // ---- query of sample s (composited by the next iteration) -------------
     constexpr int Q = G ? kQueryBoth : kQueryValue;
@@ -518,7 +524,8 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
     ray.sf = s + 1.0f;
 
     // ---- early ray termination / end of the ray: s samples composited ------
-    if (s > 0.0f && (ray.A > rs.max_opacity || s >= ray.nsf)) {
+    if constexpr (MODE == kStepFirst) return false;  // a ray has at least one sample
+    if ((MODE == kStepLater || s > 0.0f) && (ray.A > rs.max_opacity || s >= ray.nsf)) {
         rs.out[ray.pix] = make_float4(ray.Cr, ray.Cg, ray.Cb, ray.A);
         if (rs.nsamples) rs.nsamples[ray.pix] = static_cast<int>(s);
         return true;
@@ -546,45 +553,32 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P, T, NU, R>::value)
     const TfShared tf{s_tf};
 
     const int lane = threadIdx.x & 31;
-    const unsigned lane_lt = (1u << lane) - 1u;
     const int tw_log2 = rs.tile_w_log2;
     const int tiles_x = (rs.width + (1 << tw_log2) - 1) >> tw_log2;
     const int tiles_y = (rs.height + (32 >> tw_log2) - 1) >> (5 - tw_log2);
     const int total = tiles_x * tiles_y * 32;  // ray slots, some outside the image
 
-    int pool_next = 0, pool_end = 0;
-    bool exhausted = false;
-    bool idle = true;
     LaneRay ray;
     SpanCache<P, T, R> cache;
 
     for (;;) {
-        // ---- hand rays to idle lanes ----------------------------------------
-        // A warp takes its next tile only when all its lanes are idle:
-        // lanes that march neighbouring rays from the same start change
-        // cells together, so a warp's iteration touches half as many
-        // distinct cells and a quarter of its iterations change none.
-        const unsigned need = __ballot_sync(kFull, idle);
-        if (need == kFull) {
-            if (pool_next >= pool_end && !exhausted) {
-                int b = 0;
-                if (lane == 0) b = atomicAdd(counter, 32);
-                b = __shfl_sync(kFull, b, 0);
-                if (b >= total) exhausted = true;
-                else { pool_next = b; pool_end = b + 32; }
-            }
-            const int avail = pool_end - pool_next;
-            const int rank = __popc(need & lane_lt);
-            if (idle && rank < avail) {
-                int px, py;
-                slot_pixel(pool_next + rank, tiles_x, tw_log2, px, py);
-                if (px < rs.width && py < rs.height) idle = !start_ray(rs, px, py, ray);
-            }
-            pool_next += min(avail, __popc(need));
-            if (exhausted && __all_sync(kFull, idle)) break;
+        // ---- a wholly idle warp takes its next tile ------------------------
+        // Lanes that march neighbouring rays from the same start change cells
+        // together, so a warp's iteration touches half as many distinct cells
+        // and a quarter of its iterations change none.  The first sample of
+        // every ray is then contracted in one step of its own, and later
+        // iterations carry no test for a missing predecessor.
+        int b = 0;
+        if (lane == 0) b = atomicAdd(counter, 32);
+        b = __shfl_sync(kFull, b, 0);
+        if (b >= total) break;
+        int px, py;
+        slot_pixel(b + lane, tiles_x, tw_log2, px, py);
+        bool active = px < rs.width && py < rs.height && start_ray(rs, px, py, ray);
+        if (active) sample_step<P, T, G, NU, R, kStepFirst>(mv, rs, tf, ray, cache);
+        while (__any_sync(kFull, active)) {
+            if (active && sample_step<P, T, G, NU, R, kStepLater>(mv, rs, tf, ray, cache)) active = false;
         }
-        if (idle) continue;
-        if (sample_step<P, T, G, NU, R>(mv, rs, tf, ray, cache)) idle = true;
     }
 }
 
@@ -649,7 +643,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P, T, NU, R>::value)
         }
         if (idle) continue;
         const TfGlobal tf{J.rs.tf};
-        if (sample_step<P, T, G, NU, R>(J.mv, J.rs, tf, ray, cache)) idle = true;
+        if (sample_step<P, T, G, NU, R, kStepAny>(J.mv, J.rs, tf, ray, cache)) idle = true;
     }
 }
 
