@@ -264,6 +264,32 @@ MFADVR_API mfadvr_status mfadvr_render(mfadvr_ctx *ctx, int32_t model_id, const 
                             const mfadvr_render_params *params, float *rgba_dev, int32_t *nsamples_dev,
                             void *stream);
 
+/* mfadvr_render with a record of the knot spans (a test and inspection
+ * facility): the same kernel, instantiated with a trace, also writes for each
+ * ray's first max_samples samples the FP32 position the kernel walks and the
+ * knot-span index it evaluates the model on (queryValueMFA / queryGradientMFA
+ * inside Algorithm 1, Sec. 3.1), so that the spans can be checked exactly
+ * against a span search on those positions.
+ *  rgba_dev, nsamples_dev: as for mfadvr_render.
+ *  max_samples:  samples recorded per ray, >= 1; width*height*max_samples
+ *                at most 2^24.
+ *  pos_dev:      DEVICE, height x width x max_samples x 3 FP32: sample k of
+ *                the ray of pixel (x, y) at [(y width + x) max_samples + k]:
+ *                its position in lattice units on uniform knots (the
+ *                parameter u times the span count m, unclamped), in parameter
+ *                units on general knots.  Entries past the ray's last
+ *                contracted sample are not written.
+ *  span_dev:     DEVICE, same layout, int32: the knot-span index s in
+ *                [p, n-1] per axis (the span of the position clamped to the
+ *                parameter box).
+ * Only shaded renders of plain FP32 models (either render form, uniform or
+ * general knots) are traced: EUNSUPPORTED otherwise.  Asynchronous on
+ * stream. */
+MFADVR_API mfadvr_status mfadvr_render_trace(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_camera *camera,
+                                             const mfadvr_render_params *params, float *rgba_dev,
+                                             int32_t *nsamples_dev, int32_t max_samples, float *pos_dev,
+                                             int32_t *span_dev, void *stream);
+
 /* As mfadvr_render with HOST buffers (params->tf_rgba is then a host
  * pointer): copies the table in, renders, copies the image (and sample
  * counts, if requested) back and synchronises the stream.  Page-locked

@@ -102,6 +102,16 @@ cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t
 // the launcher zeroes it on `stream` first.  The value-only kernel runs when
 // rs.shading is 0 (no gradient is needed).
 cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream);
+// The same render recording, for each ray's first max_samples samples, the
+// FP32 position the kernel walks and the knot spans it contracts with
+// (mfadvr_render_trace).  FP32 models, shading on, plain (not rational).
+struct TraceOn {
+    float *pos;      // H x W x max_samples x 3: lattice units (uniform knots) or parameter units
+    int32_t *span;   // H x W x max_samples x 3: knot-span index, p..n-1
+    int max_samples;
+};
+cudaError_t launch_render_trace(const ModelView &mv, const RenderSetup &rs, int *counter, const TraceOn &tr,
+                                cudaStream_t stream);
 // Batched render of njobs jobs of degree p and storage dtype, all with
 // shading on (grad = 1) or all off (grad = 0), all on general knots (nu = 1)
 // or all on uniform ones, all rational (rat = 1) or none (jobs_dev in device

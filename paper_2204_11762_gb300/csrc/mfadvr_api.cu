@@ -1056,6 +1056,41 @@ mfadvr_status mfadvr_render(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_came
     return MFADVR_OK;
 }
 
+mfadvr_status mfadvr_render_trace(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_camera *camera,
+                                  const mfadvr_render_params *params, float *rgba_dev, int32_t *nsamples_dev,
+                                  int32_t max_samples, float *pos_dev, int32_t *span_dev, void *stream)
+{
+    TraceRange trace("mfadvr_render_trace");
+    if (!ctx) return fail(nullptr, MFADVR_EINVAL, "ctx must not be NULL");
+    Model *m = nullptr;
+    if (mfadvr_status st = find_model(ctx, model_id, &m)) return st;
+    RenderSetup rs;
+    if (mfadvr_status st = make_setup(ctx, *m, camera, params, &rs)) return st;
+    apply_tuning(ctx, *m, &rs);
+    if (m->dtype != MFADVR_F32 || m->rational || params->shading == 0)
+        return fail(ctx, MFADVR_EUNSUPPORTED, "the render trace covers shaded renders of plain FP32 models");
+    if (max_samples < 1 || static_cast<int64_t>(params->width) * params->height * max_samples > (int64_t(1) << 24))
+        return fail(ctx, MFADVR_EINVAL, "max_samples must be >= 1 and width*height*max_samples <= 2^24");
+    if (!rgba_dev || reinterpret_cast<uintptr_t>(rgba_dev) % 16 != 0 || !pos_dev || !span_dev ||
+        reinterpret_cast<uintptr_t>(pos_dev) % 4 != 0 || reinterpret_cast<uintptr_t>(span_dev) % 4 != 0 ||
+        reinterpret_cast<uintptr_t>(nsamples_dev) % 4 != 0)
+        return fail(ctx, MFADVR_EINVAL, "rgba (16-byte aligned), pos and span must be set; pos, span, nsamples 4-byte aligned");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "cudaSetDevice");
+    if (!is_device_ptr(rgba_dev) || !is_device_ptr(params->tf_rgba) || !is_device_ptr(pos_dev) ||
+        !is_device_ptr(span_dev) || (nsamples_dev && !is_device_ptr(nsamples_dev)))
+        return fail(ctx, MFADVR_EINVAL, "rgba, tf_rgba, pos, span and nsamples must be device pointers");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (mfadvr_status st = stage_tf(ctx, params->tf_rgba, params->tf_size, false, &rs, s)) return st;
+    rs.out = reinterpret_cast<float4 *>(rgba_dev);
+    rs.nsamples = nsamples_dev;
+    int *counter = nullptr;
+    if (mfadvr_status st = next_counter(ctx, &counter)) return st;
+    cudaError_t e = launch_render_trace(view_of(*m), rs, counter, TraceOn{pos_dev, span_dev, max_samples}, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "render trace launch");
+    return MFADVR_OK;
+}
+
 mfadvr_status mfadvr_render_host(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_camera *camera,
                                  const mfadvr_render_params *params, float *rgba_host, int32_t *nsamples_host,
                                  void *stream)

@@ -280,13 +280,19 @@ __device__ __forceinline__ void reload_block(const ModelView &mv, int base, Span
 // R: rational model, the value f = A / W and its gradient
 // (grad A - f grad W) / W from the contractions of w P and of w.  Returns
 // true when the ray is finished (pixel written).
+// Render-path trace (a test facility): for each ray's first max_samples
+// samples, the FP32 position the kernel walks (lattice units on uniform
+// knots, parameter units on general knots) and the knot spans it contracts
+// with, as written by TraceOn; TraceOff compiles to nothing.
+struct TraceOff {};  // TraceOn: mfa_internal.h
+
 // Which sample of its ray an iteration may be at: any (a sample s = 0 has no
 // predecessor to composite), the first (contract only), or a later one.
 enum StepMode { kStepAny = 0, kStepFirst = 1, kStepLater = 2 };
 
-template <int P, typename T, bool G, bool NU, bool R, int MODE, typename Tf>
+template <int P, typename T, bool G, bool NU, bool R, int MODE, typename Tf, typename Tr = TraceOff>
 __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSetup &rs, const Tf &tf, LaneRay &ray,
-                                            SpanCache<P, T, R> &cache)
+                                            SpanCache<P, T, R> &cache, const Tr &tr = Tr{})
 {
     constexpr bool kCache = SpanCache<P, T, R>::kOn;
     constexpr bool kPoly = std::is_same<T, PolyF32>::value;
@@ -381,6 +387,17 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
             ray.interior = span_interior<P>(ray.kk[0], mv.m[0]) && span_interior<P>(ray.kk[1], mv.m[1]) &&
                            span_interior<P>(ray.kk[2], mv.m[2]);
             if constexpr (kCache) reload_block<P, T, R>(mv, ray.base, cache);
+        }
+    }
+    if constexpr (std::is_same<Tr, TraceOn>::value) {
+        const int k = static_cast<int>(s);
+        if (k < tr.max_samples) {
+            const int64_t at = (static_cast<int64_t>(ray.pix) * tr.max_samples + k) * 3;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                tr.pos[at + a] = fmaf(s, ray.dX[a], ray.X0[a]);
+                tr.span[at + a] = ray.kk[a] + P;
+            }
         }
     }
     float Nu[P + 1], dNu[P + 1], Nv[P + 1], dNv[P + 1], Nw[P + 1], dNw[P + 1];
@@ -536,9 +553,9 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
 // ---------------------------------------------------------------------------
 // One image
 // ---------------------------------------------------------------------------
-template <int P, typename T, bool G, bool NU, bool R>
+template <int P, typename T, bool G, bool NU, bool R, typename Tr = TraceOff>
 __global__ void __launch_bounds__(kThreads, MinBlocks<P, T, NU, R>::value)
-    render_kernel(ModelView mv, RenderSetup rs, int *__restrict__ counter)
+    render_kernel(ModelView mv, RenderSetup rs, int *__restrict__ counter, Tr tr)
 {
     // transfer function as (entry, next entry - entry) pairs: one FMA per
     // channel interpolates
@@ -575,9 +592,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P, T, NU, R>::value)
         int px, py;
         slot_pixel(b + lane, tiles_x, tw_log2, px, py);
         bool active = px < rs.width && py < rs.height && start_ray(rs, px, py, ray);
-        if (active) sample_step<P, T, G, NU, R, kStepFirst>(mv, rs, tf, ray, cache);
+        if (active) sample_step<P, T, G, NU, R, kStepFirst>(mv, rs, tf, ray, cache, tr);
         while (__any_sync(kFull, active)) {
-            if (active && sample_step<P, T, G, NU, R, kStepLater>(mv, rs, tf, ray, cache)) active = false;
+            if (active && sample_step<P, T, G, NU, R, kStepLater>(mv, rs, tf, ray, cache, tr)) active = false;
         }
     }
 }
@@ -655,17 +672,18 @@ int sm_count()
     return sms;
 }
 
-template <int P, typename T, bool G, bool NU, bool R>
-cudaError_t launch_render_t(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream)
+template <int P, typename T, bool G, bool NU, bool R, typename Tr = TraceOff>
+cudaError_t launch_render_t(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream,
+                            Tr tr = Tr{})
 {
     const size_t smem = 2 * sizeof(float4) * static_cast<size_t>(rs.tf_size);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(render_kernel<P, T, G, NU, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(render_kernel<P, T, G, NU, R, Tr>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem));
         if (e != cudaSuccess) return e;
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<P, T, G, NU, R>, kThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<P, T, G, NU, R, Tr>, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (rs.ctas_per_sm > 0 && rs.ctas_per_sm < per_sm) per_sm = rs.ctas_per_sm;
@@ -677,7 +695,7 @@ cudaError_t launch_render_t(const ModelView &mv, const RenderSetup &rs, int *cou
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
     if (e != cudaSuccess) return e;
-    render_kernel<P, T, G, NU, R><<<static_cast<int>(blocks), kThreads, smem, stream>>>(mv, rs, counter);
+    render_kernel<P, T, G, NU, R, Tr><<<static_cast<int>(blocks), kThreads, smem, stream>>>(mv, rs, counter, tr);
     return cudaGetLastError();
 }
 
@@ -705,6 +723,18 @@ struct RenderOne {
     static cudaError_t run(const ModelView *mv, const RenderSetup *rs, int *counter, cudaStream_t s)
     {
         return launch_render_t<P, T, G, NU, R>(*mv, *rs, counter, s);
+    }
+};
+// The traced render: FP32 models (either render form, uniform or general
+// knots, plain), shading on; other kinds are not compiled for it.
+template <int P, typename T, bool G, bool NU, bool R>
+struct RenderTrace {
+    static cudaError_t run(const ModelView *mv, const RenderSetup *rs, int *counter, TraceOn tr, cudaStream_t s)
+    {
+        if constexpr (G && !R && (std::is_same<T, PolyF32>::value || std::is_same<T, float>::value))
+            return launch_render_t<P, T, G, NU, R, TraceOn>(*mv, *rs, counter, s, tr);
+        else
+            return cudaErrorNotSupported;
     }
 };
 template <int P, typename T, bool G, bool NU, bool R>
@@ -774,6 +804,12 @@ cudaError_t dispatch_degree(int dtype, bool grad, bool nu, bool rat, A... args)
         return dispatch_degree<PP, RenderOne>(render_form_key(mv, rs.shading), rs.shading != 0, mv.nu != 0,  \
                                                mv.rational != 0, &mv, &rs, counter, stream);                 \
     }                                                                                                        \
+    cudaError_t launch_render_trace_p##PP(const ModelView &mv, const RenderSetup &rs, int *counter,           \
+                                          const TraceOn &tr, cudaStream_t stream)                             \
+    {                                                                                                        \
+        return dispatch_degree<PP, RenderTrace>(render_form_key(mv, rs.shading), rs.shading != 0, mv.nu != 0, \
+                                                 mv.rational != 0, &mv, &rs, counter, tr, stream);           \
+    }                                                                                                        \
     cudaError_t launch_render_batch_p##PP(int dtype, int grad, int nu, int rat, const RenderJob *jobs_dev,     \
                                           int njobs, int total_tiles, int ctas_per_sm, int *counter,           \
                                           cudaStream_t stream)                                               \
@@ -787,6 +823,11 @@ cudaError_t launch_render_p2(const ModelView &, const RenderSetup &, int *, cuda
 cudaError_t launch_render_p3(const ModelView &, const RenderSetup &, int *, cudaStream_t);
 cudaError_t launch_render_p4(const ModelView &, const RenderSetup &, int *, cudaStream_t);
 cudaError_t launch_render_p5(const ModelView &, const RenderSetup &, int *, cudaStream_t);
+cudaError_t launch_render_trace_p1(const ModelView &, const RenderSetup &, int *, const TraceOn &, cudaStream_t);
+cudaError_t launch_render_trace_p2(const ModelView &, const RenderSetup &, int *, const TraceOn &, cudaStream_t);
+cudaError_t launch_render_trace_p3(const ModelView &, const RenderSetup &, int *, const TraceOn &, cudaStream_t);
+cudaError_t launch_render_trace_p4(const ModelView &, const RenderSetup &, int *, const TraceOn &, cudaStream_t);
+cudaError_t launch_render_trace_p5(const ModelView &, const RenderSetup &, int *, const TraceOn &, cudaStream_t);
 cudaError_t launch_render_batch_p1(int, int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);
 cudaError_t launch_render_batch_p2(int, int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);
 cudaError_t launch_render_batch_p3(int, int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);

@@ -34,7 +34,8 @@ EXPORTS = ("mfadvr_create", "mfadvr_destroy", "mfadvr_load_model", "mfadvr_unloa
            "mfadvr_status_string", "mfadvr_last_error", "mfadvr_render_lattice_noalloc", "mfadvr_render_batch",
            "mfadvr_autotune", "mfadvr_tuning_save", "mfadvr_tuning_load", "mfadvr_serve_start", "mfadvr_serve_stop",
            "mfadvr_submit", "mfadvr_wait", "mfadvr_serve_stats", "mfadvr_serve_trace", "mfadvr_query_points",
-           "mfadvr_query_points_host", "mfadvr_query_points_host_async", "mfadvr_probe_fma")
+           "mfadvr_query_points_host", "mfadvr_query_points_host_async", "mfadvr_probe_fma",
+           "mfadvr_render_trace")
 MAX_BATCH = 256
 NOALLOC_MAX_POINTS = 1 << 19
 
@@ -114,6 +115,7 @@ def load_library(build_if_missing: bool = True):
         "mfadvr_query_points_host_async": [vp, i32, vp, i64, i32, vp, vp, i32, vp],
         "mfadvr_render": [vp, i32, P(Camera), P(RenderParams), vp, vp, vp],
         "mfadvr_render_host": [vp, i32, P(Camera), P(RenderParams), vp, vp, vp],
+        "mfadvr_render_trace": [vp, i32, P(Camera), P(RenderParams), vp, vp, i32, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -365,6 +367,17 @@ class Context:
         prm = make_params(params, _ptr(tf_dev), tf_size)
         self._check(self._L.mfadvr_render(self._h, int(model_id), ctypes.byref(cam), ctypes.byref(prm),
                                           _ptr(rgba_dev), _ptr(nsamples_dev), _stream(stream)))
+
+    def render_trace(self, model_id, camera: dict, params: dict, tf_dev, tf_size, rgba_dev, nsamples_dev,
+                     max_samples: int, pos_dev, span_dev, stream=None):
+        """mfadvr_render_trace: render and record each ray's first max_samples
+        sample positions (H x W x max_samples x 3 float32) and knot spans
+        (same shape, int32) in the caller's device buffers."""
+        cam = make_camera(camera)
+        prm = make_params(params, _ptr(tf_dev), tf_size)
+        self._check(self._L.mfadvr_render_trace(self._h, int(model_id), ctypes.byref(cam), ctypes.byref(prm),
+                                                _ptr(rgba_dev), _ptr(nsamples_dev), int(max_samples),
+                                                _ptr(pos_dev), _ptr(span_dev), _stream(stream)))
 
     def render_host(self, model_id, camera: dict, params: dict, tf, rgba=None, nsamples=None, stream=None):
         tf = np.ascontiguousarray(tf, dtype=np.float32).reshape(-1, 4)

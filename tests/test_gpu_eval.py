@@ -357,17 +357,12 @@ def test_async_host_query_beside_a_render(ctx, torch_cuda):
     ctx.unload_model(mid)
 
 
-def test_readme_python_example_runs(torch_cuda):
-    """The usage example in README.md runs as written and gives finite
-    queries and a non-empty image."""
+def test_usage_example_runs(torch_cuda):
+    """The usage example (tests/example_usage.py, which README.md quotes)
+    runs as written and gives finite queries and a non-empty image."""
     import os
-    import re
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    text = open(os.path.join(root, "README.md")).read()
-    blocks = re.findall(r"```python\n(.*?)```", text, flags=re.S)
-    assert len(blocks) == 1
-    scope = {}
-    exec(compile(blocks[0], "README.md", "exec"), scope)
+    import runpy
+    scope = runpy.run_path(os.path.join(os.path.dirname(os.path.abspath(__file__)), "example_usage.py"))
     torch_cuda.cuda.synchronize()
     out, img = scope["out"], scope["img"]
     assert torch_cuda.isfinite(out).all() and torch_cuda.isfinite(img).all()
