@@ -66,6 +66,8 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 16-bit storage comparison")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default workload: skip the ml32, noise512 and serving-slice legs of the line")
     ap.add_argument("--serve-step", type=float, default=1.0 / 512, help="serve48: sample step")
     ap.add_argument("--serve-batch", type=int, default=32, help="serve48: requests per scheduling step")
     ap.add_argument("--serve-flights", type=int, default=3, help="serve48: batches in flight")
@@ -453,6 +455,18 @@ def run_ours(args, wl):
                                 "render_samples_per_s": rs / tr, "eval_points_per_s": (1 << 22) / te}
 
     ctx.close()
+    del d_pts, d_out, d_img, d_ns
+    torch.cuda.empty_cache()
+
+    # ---- the other named configurations, bounded, rank 0 at N = 1 --------
+    if not args.no_configs and world == 1:
+        t0 = time.perf_counter()
+        configs = {"ml32": leg_ml32(torch, dev, local, flush, stream)}
+        configs["noise512"] = leg_noise512(torch, dev, local, flush, stream)
+        torch.cuda.empty_cache()
+        configs["serve_slice"] = leg_serve_slice(torch, dev, local, args)
+        configs["wall_s"] = time.perf_counter() - t0
+        line["configs"] = configs
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -898,26 +912,22 @@ def _pct(xs, q):
     return xs[min(len(xs) - 1, int(q * len(xs)))]
 
 
-def run_serve48(args, wl):
-    """Real-time replay of a Poisson request stream (2000 requests at 200/s,
-    48 resident models of degree 3-4, images 256^2..2048^2) through the
-    serving loop, with FP16 models (and FP32, to separate batching from
-    storage), against serial plain-FP32 rendering of the same stream
-    (queueing simulated from the measured render times)."""
-    import torch
+def serve_legs(ctx, torch, dev, local, mods, reqs, prm, args, err_requests=0):
+    """One request stream through three renderers, each replayed in real time
+    (every request submitted at its arrival time): the serving loop with FP16
+    models, the serving loop with FP32 models, and serial plain-FP32 rendering
+    (one request at a time, synchronously, in arrival order: a request waits
+    for all earlier ones).  Latency = completion - arrival.  err_requests > 0:
+    the FP16-served images of that many of the stream's 256^2 requests are
+    compared with the FP64 oracle of the FP32 lattice (every 2nd row)."""
+    import numpy as np
 
-    from paper_2204_11762_gb300 import mfadvr
-
-    mods, reqs, prm = wl
-    prm = dict(prm, step=args.serve_step)
-    rank, world, local = _dist()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    ctx = mfadvr.Context(local)
+    import oracle
     tfs = [torch.from_numpy(m["tf"]).to(dev) for m in mods]
     pool = 8
     bufs = {side: [(torch.empty((side, side, 4), device=dev), torch.empty((side, side), dtype=torch.int32, device=dev))
                    for _ in range(pool)] for side in sorted({r["side"] for r in reqs})}
+    check = [i for i, r in enumerate(reqs) if r["side"] == 256][:err_requests]
 
     def job(r, ids, rgba, ns):
         return {"model_id": ids[r["model"]], "camera": r["camera"],
@@ -925,6 +935,7 @@ def run_serve48(args, wl):
                 "tf_size": 256, "rgba_dev": rgba, "nsamples_dev": ns}
 
     resident = {}  # HBM bytes of the loaded models, per storage type
+    kept = {}      # host copies of the checked requests' images
 
     def served(storage):
         ids = [ctx.load_model(m["ctrl"], m["degree"], storage=storage) for m in mods]
@@ -938,7 +949,7 @@ def run_serve48(args, wl):
             r = dict(reqs[0], model=k, side=256)
             ctx.wait(ctx.submit(job(r, ids, *bufs[256][k % pool])))
         warm = []  # and an unmeasured burst of the stream's first requests (every size and buffer)
-        for i, r in enumerate(reqs[:300]):
+        for i, r in enumerate(reqs[:min(300, len(reqs))]):
             warm.append(ctx.submit(job(r, ids, *bufs[r["side"]][i % pool])))
             if len(warm) >= pool:
                 ctx.wait(warm.pop(0))
@@ -951,6 +962,13 @@ def run_serve48(args, wl):
         owner = {side: [None] * pool for side in bufs}
         used = {side: 0 for side in bufs}
         submit_t, lat = {}, {}
+
+        def retire(i, side, slot):
+            lat[i] = ctx.wait(submit_t[i][1]) / 1e6 + (submit_t[i][0] - reqs[i]["arrival"])
+            if storage == "f16" and i in check:
+                kept[i] = bufs[side][slot][0].cpu().numpy()
+            return bufs[side][slot][1].sum(dtype=torch.int64)
+
         t0 = time.perf_counter()
         for i, r in enumerate(reqs):
             target = t0 + r["arrival"]
@@ -966,15 +984,13 @@ def run_serve48(args, wl):
             prev = owner[side][slot]
             rgba, ns = bufs[side][slot]
             if prev is not None:  # the buffer's previous request must be done
-                lat[prev] = ctx.wait(submit_t[prev][1]) / 1e6 + (submit_t[prev][0] - reqs[prev]["arrival"])
-                samples += ns.sum(dtype=torch.int64)
+                samples += retire(prev, side, slot)
             submit_t[i] = (time.perf_counter() - t0, ctx.submit(job(r, ids, rgba, ns)))
             owner[side][slot] = i
         for side in bufs:
             for slot, prev in enumerate(owner[side]):
                 if prev is not None and prev not in lat:
-                    lat[prev] = ctx.wait(submit_t[prev][1]) / 1e6 + (submit_t[prev][0] - reqs[prev]["arrival"])
-                    samples += bufs[side][slot][1].sum(dtype=torch.int64)
+                    samples += retire(prev, side, slot)
         clk = clocks.stop()
         stats = ctx.serve_stats()
         ctx.serve_stop()
@@ -984,62 +1000,224 @@ def run_serve48(args, wl):
         n = int(samples.item())
         lats = [lat[i] for i in range(len(reqs))]
         makespan = max(reqs[i]["arrival"] + lats[i] for i in range(len(reqs))) - reqs[0]["arrival"]
-        per_s = {}
-        for r, l in zip(reqs, lats):
-            per_s.setdefault(int(r["arrival"]), []).append(l)
         client_wait = max(submit_t[i][0] - reqs[i]["arrival"] for i in range(len(reqs)))
-        return {"latency_ms_p99_by_arrival_second": [round(1000 * _pct(per_s[k], 0.99), 1) for k in sorted(per_s)],
-                "client_submit_delay_ms_max": 1000 * client_wait,
-                "latency_ms_p50": 1000 * _pct(lats, 0.50), "latency_ms_p99": 1000 * _pct(lats, 0.99),
+        return {"latency_ms_p50": 1000 * _pct(lats, 0.50), "latency_ms_p99": 1000 * _pct(lats, 0.99),
                 "latency_ms_max": 1000 * max(lats), "samples": n, "makespan_s": makespan,
-                "samples_per_s": n / makespan, "frames_per_s": len(reqs) / makespan, "clocks": clk, **stats}
+                "samples_per_s": n / makespan, "frames_per_s": len(reqs) / makespan,
+                "client_submit_delay_ms_max": 1000 * client_wait, "clocks": clk, **stats}
 
     srv16 = served("f16")
     srv32 = served("f32")
 
-    # serial plain FP32: each request rendered alone, in arrival order
+    # serial plain FP32, replayed in real time: one request at a time,
+    # synchronously, each started at its arrival or when the previous one is
+    # done, whichever is later
     ids32 = [ctx.load_model(m["ctrl"], m["degree"]) for m in mods]
     stream = torch.cuda.current_stream(dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in reqs]
-    acc = torch.zeros((), dtype=torch.int64, device=dev)
     for k in range(len(mods)):  # warm-up
         j = job(dict(reqs[0], model=k, side=256), ids32, *bufs[256][0])
-        ctx.render(j["model_id"], j["camera"], j["params"], j["tf_dev"], 256, j["rgba_dev"], j["nsamples_dev"])
-    for (a, b), r in zip(ev, reqs):
+        ctx.render(j["model_id"], j["camera"], j["params"], j["tf_dev"], 256, j["rgba_dev"], j["nsamples_dev"],
+                   stream=stream)
+    torch.cuda.synchronize(dev)
+    acc = torch.zeros((), dtype=torch.int64, device=dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    slat, busy = [], 0.0
+    t0 = time.perf_counter()
+    for r in reqs:
+        while time.perf_counter() - t0 < r["arrival"]:
+            pass
         rgba, ns = bufs[r["side"]][0]
         j = job(r, ids32, rgba, ns)
-        a.record(stream)
+        ts = time.perf_counter()
         ctx.render(j["model_id"], j["camera"], j["params"], j["tf_dev"], 256, rgba, ns, stream=stream)
-        b.record(stream)
         acc += ns.sum(dtype=torch.int64)
-    torch.cuda.synchronize(dev)
-    dur = [a.elapsed_time(b) / 1000.0 for a, b in ev]
+        stream.synchronize()
+        te = time.perf_counter()
+        busy += te - ts
+        slat.append(te - t0 - r["arrival"])
+    clk = clocks.stop()
     serial_samples = int(acc.item())
-    done, slat = 0.0, []
-    for r, d in zip(reqs, dur):
-        done = max(done, r["arrival"]) + d
-        slat.append(done - r["arrival"])
-    serial_makespan = done - reqs[0]["arrival"]
+    serial_makespan = max(r["arrival"] + l for r, l in zip(reqs, slat)) - reqs[0]["arrival"]
+    for m in ids32:
+        ctx.unload_model(m)
+    serial = {"latency_ms_p50": 1000 * _pct(slat, 0.50), "latency_ms_p99": 1000 * _pct(slat, 0.99),
+              "latency_ms_max": 1000 * max(slat), "samples": serial_samples, "busy_s": busy,
+              "makespan_s": serial_makespan, "samples_per_s": serial_samples / serial_makespan,
+              "frames_per_s": len(reqs) / serial_makespan, "clocks": clk,
+              "replay": "real time, synchronous, one request at a time"}
+    span = reqs[-1]["arrival"] - reqs[0]["arrival"]
+    out = {"served_f16": srv16, "served_f32": srv32, "serial_f32": serial, "resident_model_bytes": resident,
+           "offered_load_serial_f32": busy / span if span > 0 else None,
+           "f16_vs_serial_f32_samples_per_s": srv16["samples_per_s"] / serial["samples_per_s"]}
+    if check:
+        oracle.build()
+        worst, rms = 0.0, []
+        for i in check:
+            r = reqs[i]
+            m = mods[r["model"]]
+            ref = oracle.render(m["ctrl"], m["degree"], r["camera"],
+                                dict(prm, width=256, height=256, tf=m["tf"]), row_step=2)
+            rows = np.arange(0, 256, 2)
+            e = np.minimum(np.abs(kept[i] - ref["rgba"]).max(-1), np.abs(kept[i] - ref["rgba_alt"]).max(-1))[rows]
+            worst = max(worst, float(e.max()))
+            rms.append(float(np.sqrt(np.mean(e * e))))
+        out["f16_pixel_error_vs_oracle"] = {"max": worst, "rms": float(np.mean(rms)), "requests": len(check),
+                                            "rows": "every 2nd row of each 256^2 image",
+                                            "reference": "FP64 oracle of the FP32 lattice"}
+    return out
+
+
+def _fp32_peak(torch, dev, clk):
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = (clk or {}).get("sm_max_mhz") or _measured_peaks().get("sm_max_mhz") or 2070.0
+    return props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+
+
+def _timed_frames(ctx, torch, dev, local, mid, wl, prm, d_tf, d_img, d_ns, flush, stream, frames, warm):
+    """Autotuned launch shape (untimed), `warm` untimed frames, then `frames`
+    frames timed with CUDA events, the L2 flushed before each.  Returns
+    (ms list, composited samples per frame, clocks)."""
+    ctx.autotune(mid, wl["camera"], prm, d_tf, wl["tf"].shape[0], d_img, d_ns, stream=stream)
+    for _ in range(warm):
+        flush.zero_()
+        ctx.render(mid, wl["camera"], prm, d_tf, wl["tf"].shape[0], d_img, d_ns, stream=stream)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(frames)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        ctx.render(mid, wl["camera"], prm, d_tf, wl["tf"].shape[0], d_img, d_ns, stream=stream)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    return [a.elapsed_time(b) for a, b in ev], int(d_ns.sum(dtype=torch.int64).item()), clk
+
+
+def leg_ml32(torch, dev, local, flush, stream, frames=20):
+    """The small case: 32^3 degree-3 Marschner-Lobb model at 128x128
+    orthographic, step 1/256: frame time and the largest pixel error against
+    the oracle's full frame."""
+    import numpy as np
+
+    import oracle
+    from paper_2204_11762_gb300 import mfadvr, workloads
+    wl = workloads.small_ml_workload()
+    prm = wl["params"]
+    W, H = prm["width"], prm["height"]
+    ctx = mfadvr.Context(local)
+    d_tf = torch.from_numpy(wl["tf"]).to(dev)
+    d_img = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    d_ns = torch.empty((H, W), dtype=torch.int32, device=dev)
+    mid = ctx.load_model(wl["ctrl"], wl["degree"])
+    ms, samples, clk = _timed_frames(ctx, torch, dev, local, mid, wl, prm, d_tf, d_img, d_ns, flush, stream,
+                                     frames, 3)
+    img = d_img.cpu().numpy()
     ctx.close()
+    oracle.build()
+    t0 = time.perf_counter()
+    ref = oracle.render(wl["ctrl"], wl["degree"], wl["camera"], dict(prm, tf=wl["tf"]))
+    t_oracle = time.perf_counter() - t0
+    err = np.minimum(np.abs(img - ref["rgba"]).max(-1), np.abs(img - ref["rgba_alt"]).max(-1))
+    r_ms = statistics.mean(ms)
+    return {"workload": "ml32_p3: 128x128 orthographic, 32^3 Marschner-Lobb (Eq. 2) + N(0, 0.01), step 1/256, "
+                        "TF 256, shading",
+            "frames": frames, "render_ms": r_ms, "samples_per_frame": samples,
+            "samples_per_s": samples / (r_ms / 1000.0), "frames_per_s": 1000.0 / r_ms,
+            "max_pixel_err_vs_oracle": float(err.max()), "tolerance": 2e-3,
+            "oracle_full_frame_s": t_oracle, "oracle_cores": os.cpu_count() or 1, "clocks": clk}
+
+
+def leg_noise512(torch, dev, local, flush, stream, frames=3):
+    """The large single model: 512^3 degree-4 value noise at 3840x2160, step
+    1/2048, TF 1024, in FP32 and in BF16 storage: frame times, the roofline
+    fraction, and the pixel error against the oracle of the FP32 lattice on
+    every 540th row."""
+    import numpy as np
+
+    import oracle
+    from paper_2204_11762_gb300 import mfadvr, workloads
+    wl = workloads.value_noise_workload(512)
+    p, prm = wl["degree"], wl["params"]
+    W, H = prm["width"], prm["height"]
+    ctx = mfadvr.Context(local)
+    d_tf = torch.from_numpy(wl["tf"]).to(dev)
+    d_img = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    d_ns = torch.empty((H, W), dtype=torch.int32, device=dev)
+    out, imgs = {}, {}
+    for st in ("f32", "bf16"):
+        mid = ctx.load_model(wl["ctrl"], p, storage=st)
+        ms, samples, clk = _timed_frames(ctx, torch, dev, local, mid, wl, prm, d_tf, d_img, d_ns, flush, stream,
+                                         frames, 2)
+        imgs[st] = d_img.cpu().numpy()
+        ctx.unload_model(mid)
+        r_ms = statistics.mean(ms)
+        tflops = samples * C_FMA[p] * 2 / (r_ms / 1000.0) / 1e12
+        peak = _fp32_peak(torch, dev, clk)
+        out[st] = {"render_ms": r_ms, "samples_per_frame": samples, "samples_per_s": samples / (r_ms / 1000.0),
+                   "tflops": tflops, "frac": tflops / peak, "clocks": clk}
+    ctx.close()
+    oracle.build()
+    rows = np.arange(0, H, 540)
+    ref = oracle.render(wl["ctrl"], p, wl["camera"], dict(prm, tf=wl["tf"]), row_step=540)
+    for st in out:
+        e = np.minimum(np.abs(imgs[st] - ref["rgba"]).max(-1), np.abs(imgs[st] - ref["rgba_alt"]).max(-1))[rows]
+        out[st]["pixel_err_vs_oracle"] = {"max": float(e.max()), "rms": float(np.sqrt(np.mean(e * e)))}
+    out["bf16"]["vs_f32"] = out["f32"]["render_ms"] / out["bf16"]["render_ms"]
+    return {"workload": "noise512_p4: 3840x2160 perspective, 512^3 value noise, step 1/2048, TF 1024, shading",
+            "frames": frames, "per_unit": f"{C_FMA[p]} FMA per sample", "error_rows": "every 540th row",
+            **out}
+
+
+def leg_serve_slice(torch, dev, local, args, models=8, requests=200):
+    """A bounded slice of the serving workload: the stream's first `models`
+    models (degree 3-4, lattices 96^3..384^3) and `requests` Poisson requests
+    at 200/s, replayed in real time through the serving loop with FP16 and
+    with FP32 models and through serial plain-FP32 rendering."""
+    from paper_2204_11762_gb300 import mfadvr, workloads
+    mods, reqs, prm = workloads.serving_workload(models=models, requests=requests)
+    prm = dict(prm, step=args.serve_step)
+    ctx = mfadvr.Context(local)
+    legs = serve_legs(ctx, torch, dev, local, mods, reqs, prm, args, err_requests=4)
+    ctx.close()
+    return {"workload": f"serve slice: {requests} requests, Poisson 200/s, {models} resident models "
+                        f"(degree 3-4, lattices {min(m['ncp'][0] for m in mods)}^3.."
+                        f"{max(m['ncp'][0] for m in mods)}^3), images {{256,512,1024,2048}}^2, "
+                        f"step {args.serve_step:g}",
+            "frame_budget_bytes": 2 << 30, "max_batch": args.serve_batch, "max_in_flight": args.serve_flights,
+            **legs}
+
+
+def run_serve48(args, wl):
+    """Real-time replay of a Poisson request stream (2000 requests at 200/s,
+    48 resident models of degree 3-4, images 256^2..2048^2) through the
+    serving loop with FP16 models and with FP32 models, against serial
+    plain-FP32 rendering of the same stream, also replayed in real time."""
+    import torch
+
+    from paper_2204_11762_gb300 import mfadvr
+
+    mods, reqs, prm = wl
+    prm = dict(prm, step=args.serve_step)
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = mfadvr.Context(local)
+    legs = serve_legs(ctx, torch, dev, local, mods, reqs, prm, args, err_requests=8)
+    ctx.close()
+    srv16 = legs["served_f16"]
     line = {"metric": METRIC, "value": srv16["samples_per_s"], "unit": UNIT, "n_gpus": world,
             "steps": len(reqs), "warmup": len(mods), "ms_per_step": 1000 * srv16["makespan_s"] / len(reqs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (storage f16)",
             "data": "synthetic",
-            "config": {"workload": f"serve48: 2000 requests, Poisson 200/s, 48 resident models (degree 3-4, "
-                                   f"lattices 96^3..384^3, FP16), images {{256,512,1024,2048}}^2, "
+            "config": {"workload": f"serve48: {len(reqs)} requests, Poisson 200/s, {len(mods)} resident models "
+                                   f"(degree 3-4, lattices 96^3..384^3, FP16), images {{256,512,1024,2048}}^2, "
                                    f"step {args.serve_step:g}",
                        "frame_budget_bytes": 2 << 30, "max_batch": args.serve_batch,
-                       "max_in_flight": args.serve_flights,
-                       "resident_model_bytes": resident,
-                       "offered_load": sum(dur) / (reqs[-1]["arrival"] - reqs[0]["arrival"])},
-            "served_f16": srv16, "served_f32": srv32,
-            "serial_f32": {"latency_ms_p50": 1000 * _pct(slat, 0.50), "latency_ms_p99": 1000 * _pct(slat, 0.99),
-                           "latency_ms_max": 1000 * max(slat), "samples": serial_samples,
-                           "gpu_busy_s": sum(dur), "makespan_s": serial_makespan,
-                           "samples_per_s": serial_samples / serial_makespan,
-                           "busy_samples_per_s": serial_samples / sum(dur),
-                           "frames_per_s": len(reqs) / serial_makespan},
-            "gpu_launches": srv16["launches"]}
+                       "max_in_flight": args.serve_flights},
+            **legs, "gpu_launches": srv16["launches"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

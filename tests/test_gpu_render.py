@@ -6,7 +6,7 @@ two branches."""
 import numpy as np
 import pytest
 
-from _parity import assert_render_parity, dequantize
+from _parity import assert_render_parity, assert_ties_rare, dequantize
 
 pytestmark = pytest.mark.gpu
 
@@ -191,6 +191,8 @@ def test_full_size_gaussian_workload_sampled_rows(ctx, torch_cuda, orc):
     ref = orc.render(wl["ctrl"], wl["degree"], wl["camera"], dict(wl["params"], tf=wl["tf"]), row_step=64)
     rows = np.arange(0, wl["params"]["height"], 64)
     assert_render_parity(img, ns, ref, rows=rows)
+    st = assert_ties_rare(img, ns, ref, rows)  # 0 of 5437 hit pixels measured
+    print(f"gauss128 tie use: {st}")
     assert np.isfinite(img).all()
     assert (img[..., 3] <= 1.0 + 1e-6).all() and (img >= -1e-6).all()
     ctx.unload_model(mid)
@@ -265,6 +267,15 @@ def test_full_size_value_noise_sampled_rows(ctx, torch_cuda, orc, storage):
     ref = orc.render(deq, wl["degree"], wl["camera"], prm, row_step=216)
     rows = np.arange(0, wl["params"]["height"], 216)
     assert_render_parity(img, ns, ref, rows=rows)
+    # Near O_max a sample at step 1/2048 (opacity reference 1/16) adds about
+    # (1 - 0.99) alpha / 128 ~ 2e-5 of opacity, while FP32 rounding over the
+    # ray's ~3500 samples moves the cumulative opacity by up to ~2e-4: the
+    # strict A > O_max test can then fall a few samples from the exact FP64
+    # stop on a small share of the rays (0.4% measured), each inside the
+    # oracle's tie range and within the pixel tolerance.
+    st = assert_ties_rare(img, ns, ref, rows, limit=1e-2)
+    assert st["max_samples_off"] <= 2  # 1 measured
+    print(f"noise512 {storage} tie use: {st}")
     assert np.isfinite(img).all()
 
 
