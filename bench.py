@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 # form) on the 128^3 workload from one ncu capture
 # (profiles/render_kernel_gauss128_p3_persp1024.md), valid only for the kernel
 # sources it was taken on.
-RENDER_TRAFFIC = {"sources_sha256_16": "9f68dee08cb1cc48", "bytes": 517292544}
+RENDER_TRAFFIC = {"sources_sha256_16": "157c2fc88db5fc61", "bytes": 539675136}
 RENDER_SOURCES = ("paper_2204_11762_gb300/csrc/render_kernels.cuh", "paper_2204_11762_gb300/csrc/mfa_basis.cuh",
                   "paper_2204_11762_gb300/csrc/mfa_internal.h")
 
@@ -66,6 +66,8 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 16-bit storage comparison")
+    ap.add_argument("--image", type=int, default=0,
+                    help="default workload: square frame of this side instead of 1024 (profiling small cases)")
     ap.add_argument("--no-configs", action="store_true",
                     help="default workload: skip the ml32, noise512 and serving-slice legs of the line")
     ap.add_argument("--serve-step", type=float, default=1.0 / 512, help="serve48: sample step")
@@ -234,10 +236,11 @@ def run_reference(args, wl):
 
 
 def _config(wl, args):
-    return {"workload": "gauss20_128cube_p3: 1024x1024 perspective render (60 deg, step 1/1024, O_max 0.99, "
+    return {"workload": f"gauss20_128cube_p3: {wl['params']['width']}x{wl['params']['height']} perspective render (60 deg, step 1/1024, O_max 0.99, "
                         "TF 256, opacity ref 1/16, shading) + eval_points on 2^24 uniform points",
             "model": f"MFA degree {wl['degree']}, 128^3 control points, clamped uniform knots",
-            "storage": args.storage, "image": "1024x1024", "eval_points": 1 << 24,
+            "storage": args.storage, "image": f"{wl['params']['width']}x{wl['params']['height']}",
+            "eval_points": 1 << 24,
             "l2": "flushed between steps (256 MiB write outside the timed events)",
             "parallelism": f"replicas x{args.gpus} (independent frames per GPU)"}
 
@@ -1268,6 +1271,8 @@ def main():
         run_sweep(args)
         return
     wl = workloads.gaussian_sum_workload()
+    if args.image:
+        wl["params"] = dict(wl["params"], width=args.image, height=args.image)
     if args.impl == "reference":
         run_reference(args, wl)
     else:
