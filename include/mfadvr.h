@@ -64,8 +64,10 @@ typedef int32_t mfadvr_status;
 #define MFADVR_MAX_DEGREE 5
 #define MFADVR_MAX_TF_SIZE 4096
 
-/* Storage type of the control points.  F16 and BF16 store P / s with the
- * per-model scale s = max|P| (s = 1 when all P are 0); evaluation converts to
+/* Storage type of the control points.  F16 and BF16 store P / s with a
+ * per-model scale s (s = 1 when all P are 0): for BF16 s = max|P|; for F16
+ * the power of two that puts max|P| / s in [2^14, 2^15), so that values down
+ * to about 2^-29 max|P| are normal FP16 numbers.  Evaluation converts to
  * FP32, accumulates in FP32 and multiplies the result by s. */
 typedef enum { MFADVR_F32 = 0, MFADVR_F16 = 1, MFADVR_BF16 = 2 } mfadvr_dtype;
 
@@ -113,7 +115,7 @@ typedef struct {
                               model (NURBS, Sec. 2.3), f = sum w P N N N /
                               sum w N N N.  The library stores w P and w in
                               the storage type (16-bit: each with its own
-                              max-abs scale); two contractions per query
+                              scale, as for P); two contractions per query
                               make it about half the plain model's speed */
     int32_t render_form;   /* mfadvr_render_form; 0 (AUTO) when zeroed      */
 } mfadvr_model_desc;

@@ -769,6 +769,22 @@ mfadvr_status mfadvr_destroy(mfadvr_ctx *ctx)
     return MFADVR_OK;
 }
 
+// Scale s of a 16-bit array whose largest magnitude is amax; the array holds
+// P / s.  BF16 (FP32's exponent range): s = amax.  FP16: a power of two that
+// puts amax in [2^14, 2^15), the top binade FP16 holds, so that values down
+// to about 2^-29 amax stay normal numbers (with s = amax, everything below
+// 6.1e-5 amax was subnormal: the near-flat regions of a field lost their
+// precision, and their shading normals with it); multiplying by 1/s is then
+// exact.  FP32 storage, or an all-zero array: 1.
+static float storage_scale(int storage, float amax)
+{
+    if (storage == MFADVR_F32 || !(amax > 0.0f)) return 1.0f;
+    if (storage == MFADVR_BF16) return amax;
+    int e = 0;
+    std::frexp(amax, &e);  // amax = f 2^e, f in [0.5, 1)
+    return std::ldexp(1.0f, e - 15);
+}
+
 mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, int32_t *model_id)
 {
     TraceRange trace("mfadvr_load_model");
@@ -845,8 +861,8 @@ mfadvr_status mfadvr_load_model(mfadvr_ctx *ctx, const mfadvr_model_desc *desc, 
     m.pmin = pmin;
     m.pmax = pmax;
     m.pabs = pabs;
-    m.scale = (desc->storage == MFADVR_F32 || qabs == 0.0f) ? 1.0f : qabs;
-    m.wscale = (desc->storage == MFADVR_F32 || !m.rational) ? 1.0f : wmax;
+    m.scale = storage_scale(desc->storage, qabs);
+    m.wscale = m.rational ? storage_scale(desc->storage, wmax) : 1.0f;
     const uint64_t rows_b = count * row_entry_bytes(m.dtype);
     m.bytes = rows_b * (m.rational ? 2 : 1);
     std::vector<float> knot_buf;

@@ -13,16 +13,26 @@ GRAD_RTOL = 1e-4
 PIXEL_ATOL = 2e-3
 
 
+def storage_scale(amax: float, storage: str) -> float:
+    """The library's per-model scale of a 16-bit array with largest
+    magnitude amax: BF16 amax; FP16 the power of two putting amax in
+    [2^14, 2^15); 1 for an all-zero array."""
+    if not amax > 0:
+        return 1.0
+    if storage == "bf16":
+        return float(np.float32(amax))
+    _, e = np.frexp(np.float32(amax))
+    return float(np.ldexp(np.float32(1.0), int(e) - 15))
+
+
 def dequantize(ctrl: np.ndarray, storage: str) -> np.ndarray:
     """The lattice a 16-bit model actually holds: P/s rounded to the storage
-    type (s = max|P| in FP32, P * (1/s) in FP32, round to nearest even),
-    times s, in float64."""
+    type (s = storage_scale(max|P|), P * (1/s) in FP32, round to nearest
+    even), times s, in float64."""
     ctrl = np.asarray(ctrl, dtype=np.float32)
     if storage == "f32":
         return ctrl.astype(np.float64)
-    s = np.float32(np.abs(ctrl).max())
-    if s == 0:
-        s = np.float32(1.0)
+    s = np.float32(storage_scale(float(np.abs(ctrl).max()), storage))
     inv = np.float32(1.0) / s
     q = (ctrl * inv).astype(np.float32)
     if storage == "f16":

@@ -5,7 +5,7 @@ the model scale (see tests/_parity.py)."""
 import numpy as np
 import pytest
 
-from _parity import assert_eval_parity, dequantize
+from _parity import assert_eval_parity, dequantize, storage_scale
 
 pytestmark = pytest.mark.gpu
 
@@ -78,7 +78,9 @@ def test_eval_parity_16bit_storage(ctx, torch_cuda, orc, storage, p):
     pts = rng.uniform(0, 1, size=(4000, 3)).astype(np.float32)
     mid = ctx.load_model(ctrl, p, storage=storage)
     info = ctx.model_info(mid)
-    assert info["scale"] == pytest.approx(float(np.abs(ctrl).max()))
+    assert info["scale"] == storage_scale(float(np.abs(ctrl).max()), storage)
+    if storage == "f16":  # a power of two putting max|P| in FP16's top binade
+        assert 2 ** 14 <= np.abs(ctrl).max() / info["scale"] < 2 ** 15
     assert info["bytes"] == ctrl.size * 32  # row layout: 16 16-bit values per lattice point
     got, sp = _run(ctx, torch_cuda, mid, pts)
     deq = dequantize(ctrl, storage)

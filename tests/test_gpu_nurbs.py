@@ -1,7 +1,7 @@
 """GPU parity for rational models (NURBS weights, Sec. 2.3) through the C ABI:
 f = A / W with A = sum w P N N N and W = sum w N N N, gradient by the
 quotient rule.  The library stores w P and w (16-bit: each with its own
-max-abs scale); the oracle evaluates the same stored lattices, i.e. weights
+own scale); the oracle evaluates the same stored lattices, i.e. weights
 W' and control points Q' / W'."""
 import numpy as np
 import pytest
