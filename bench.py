@@ -502,7 +502,10 @@ def run_noise512(args, wl):
     steps = max(3, min(args.steps, 40))
     out = {}
     for st in ("f32", "bf16"):
-        mid = ctx.load_model(wl["ctrl"], p, storage=st)
+        # FP32 with --form auto renders in the power form here too: its cells
+        # (84 GB) exceed AUTO's 4 GiB default, so the form is requested
+        form = FORMS["power"] if st == "f32" and args.form == "auto" else FORMS[args.form]
+        mid = ctx.load_model(wl["ctrl"], p, storage=st, render_form=form if st == "f32" else FORMS["auto"])
         # untimed set-up: the library's autotuner picks the launch shape
         ctx.autotune(mid, wl["camera"], prm, d_tf, wl["tf"].shape[0], d_img, d_ns, stream=stream)
         for _ in range(max(args.warmup, 3) if st == "f32" else 2):
@@ -545,7 +548,8 @@ def run_noise512(args, wl):
             "frames_per_s": world * 1000.0 / r_ms,
             "render": {"samples_per_frame": r["samples"], "ms_mean": r_ms, "ms_p50": statistics.median(r["ms"]),
                        "ms_p99": sorted(r["ms"])[min(len(r["ms"]) - 1, int(0.99 * len(r["ms"])))]},
-            "roofline": {"kernel": "render_kernel<4, float>", "bound": "alu", "achieved": tflops, "peak": peak,
+            "roofline": {"kernel": "render_kernel<4, PolyF32>" if args.form != "bspline" else "render_kernel<4, float>",
+                         "bound": "alu", "achieved": tflops, "peak": peak,
                          "unit": "TFLOP/s", "frac": tflops / peak, "traffic": None,
                          "per_unit": f"{C_FMA[p]} FMA per sample (degree {p})"},
             "mixed_precision": {"bf16": {"render_ms": b_ms, "samples_per_s": b["samples"] / (b_ms / 1000.0),
@@ -915,14 +919,17 @@ def _pct(xs, q):
     return xs[min(len(xs) - 1, int(q * len(xs)))]
 
 
-def serve_legs(ctx, torch, dev, local, mods, reqs, prm, args, err_requests=0):
+def serve_legs(ctx, torch, dev, local, mods, reqs, prm, args, err_requests=0, capacity=False):
     """One request stream through three renderers, each replayed in real time
     (every request submitted at its arrival time): the serving loop with FP16
     models, the serving loop with FP32 models, and serial plain-FP32 rendering
     (one request at a time, synchronously, in arrival order: a request waits
     for all earlier ones).  Latency = completion - arrival.  err_requests > 0:
     the FP16-served images of that many of the stream's 256^2 requests are
-    compared with the FP64 oracle of the FP32 lattice (every 2nd row)."""
+    compared with the FP64 oracle of the FP32 lattice (every 2nd row).
+    capacity: also the saturated case, every request available at once (the
+    stream submitted back to back), for the served FP16 and the serial FP32
+    renderers: the samples/s each sustains when the GPU is the bottleneck."""
     import numpy as np
 
     import oracle
@@ -940,8 +947,9 @@ def serve_legs(ctx, torch, dev, local, mods, reqs, prm, args, err_requests=0):
     resident = {}  # HBM bytes of the loaded models, per storage type
     kept = {}      # host copies of the checked requests' images
 
-    def served(storage):
+    def served(storage, paced=True):
         ids = [ctx.load_model(m["ctrl"], m["degree"], storage=storage) for m in mods]
+        arr = [r["arrival"] if paced else 0.0 for r in reqs]  # unpaced: every request there at once
         resident[storage] = sum(ctx.model_info(i)["bytes"] for i in ids)
         ctx.serve_start(frame_budget_bytes=2 << 30, max_batch=args.serve_batch, max_in_flight=args.serve_flights)
         # the clock sampler starts before the warm-up: its first nvidia-smi
@@ -967,14 +975,14 @@ def serve_legs(ctx, torch, dev, local, mods, reqs, prm, args, err_requests=0):
         submit_t, lat = {}, {}
 
         def retire(i, side, slot):
-            lat[i] = ctx.wait(submit_t[i][1]) / 1e6 + (submit_t[i][0] - reqs[i]["arrival"])
+            lat[i] = ctx.wait(submit_t[i][1]) / 1e6 + (submit_t[i][0] - arr[i])
             if storage == "f16" and i in check:
                 kept[i] = bufs[side][slot][0].cpu().numpy()
             return bufs[side][slot][1].sum(dtype=torch.int64)
 
         t0 = time.perf_counter()
         for i, r in enumerate(reqs):
-            target = t0 + r["arrival"]
+            target = t0 + arr[i]
             while True:
                 dt = target - time.perf_counter()
                 if dt <= 0:
@@ -1002,8 +1010,8 @@ def serve_legs(ctx, torch, dev, local, mods, reqs, prm, args, err_requests=0):
             ctx.unload_model(m)
         n = int(samples.item())
         lats = [lat[i] for i in range(len(reqs))]
-        makespan = max(reqs[i]["arrival"] + lats[i] for i in range(len(reqs))) - reqs[0]["arrival"]
-        client_wait = max(submit_t[i][0] - reqs[i]["arrival"] for i in range(len(reqs)))
+        makespan = max(arr[i] + lats[i] for i in range(len(reqs))) - arr[0]
+        client_wait = max(submit_t[i][0] - arr[i] for i in range(len(reqs)))
         return {"latency_ms_p50": 1000 * _pct(lats, 0.50), "latency_ms_p99": 1000 * _pct(lats, 0.99),
                 "latency_ms_max": 1000 * max(lats), "samples": n, "makespan_s": makespan,
                 "samples_per_s": n / makespan, "frames_per_s": len(reqs) / makespan,
@@ -1012,9 +1020,8 @@ def serve_legs(ctx, torch, dev, local, mods, reqs, prm, args, err_requests=0):
     srv16 = served("f16")
     srv32 = served("f32")
 
-    # serial plain FP32, replayed in real time: one request at a time,
-    # synchronously, each started at its arrival or when the previous one is
-    # done, whichever is later
+    # serial plain FP32: one request at a time, synchronously, each started
+    # at its arrival (paced) or at once, and when the previous one is done
     ids32 = [ctx.load_model(m["ctrl"], m["degree"]) for m in mods]
     stream = torch.cuda.current_stream(dev)
     for k in range(len(mods)):  # warm-up
@@ -1022,37 +1029,50 @@ def serve_legs(ctx, torch, dev, local, mods, reqs, prm, args, err_requests=0):
         ctx.render(j["model_id"], j["camera"], j["params"], j["tf_dev"], 256, j["rgba_dev"], j["nsamples_dev"],
                    stream=stream)
     torch.cuda.synchronize(dev)
-    acc = torch.zeros((), dtype=torch.int64, device=dev)
-    clocks = ClockSampler(local)
-    clocks.start()
-    slat, busy = [], 0.0
-    t0 = time.perf_counter()
-    for r in reqs:
-        while time.perf_counter() - t0 < r["arrival"]:
-            pass
-        rgba, ns = bufs[r["side"]][0]
-        j = job(r, ids32, rgba, ns)
-        ts = time.perf_counter()
-        ctx.render(j["model_id"], j["camera"], j["params"], j["tf_dev"], 256, rgba, ns, stream=stream)
-        acc += ns.sum(dtype=torch.int64)
-        stream.synchronize()
-        te = time.perf_counter()
-        busy += te - ts
-        slat.append(te - t0 - r["arrival"])
-    clk = clocks.stop()
-    serial_samples = int(acc.item())
-    serial_makespan = max(r["arrival"] + l for r, l in zip(reqs, slat)) - reqs[0]["arrival"]
+
+    def serial_run(paced=True):
+        arr = [r["arrival"] if paced else 0.0 for r in reqs]
+        acc = torch.zeros((), dtype=torch.int64, device=dev)
+        clocks = ClockSampler(local)
+        clocks.start()
+        slat, busy = [], 0.0
+        t0 = time.perf_counter()
+        for r, a in zip(reqs, arr):
+            while time.perf_counter() - t0 < a:
+                pass
+            rgba, ns = bufs[r["side"]][0]
+            j = job(r, ids32, rgba, ns)
+            ts = time.perf_counter()
+            ctx.render(j["model_id"], j["camera"], j["params"], j["tf_dev"], 256, rgba, ns, stream=stream)
+            acc += ns.sum(dtype=torch.int64)
+            stream.synchronize()
+            te = time.perf_counter()
+            busy += te - ts
+            slat.append(te - t0 - a)
+        clk = clocks.stop()
+        n = int(acc.item())
+        makespan = max(a + l for a, l in zip(arr, slat)) - arr[0]
+        return {"latency_ms_p50": 1000 * _pct(slat, 0.50), "latency_ms_p99": 1000 * _pct(slat, 0.99),
+                "latency_ms_max": 1000 * max(slat), "samples": n, "busy_s": busy, "makespan_s": makespan,
+                "samples_per_s": n / makespan, "frames_per_s": len(reqs) / makespan, "clocks": clk,
+                "replay": ("real time" if paced else "all requests at once") +
+                          ", synchronous, one request at a time"}
+
+    serial = serial_run()
+    serial_cap = serial_run(paced=False) if capacity else None
+    busy = serial["busy_s"]
     for m in ids32:
         ctx.unload_model(m)
-    serial = {"latency_ms_p50": 1000 * _pct(slat, 0.50), "latency_ms_p99": 1000 * _pct(slat, 0.99),
-              "latency_ms_max": 1000 * max(slat), "samples": serial_samples, "busy_s": busy,
-              "makespan_s": serial_makespan, "samples_per_s": serial_samples / serial_makespan,
-              "frames_per_s": len(reqs) / serial_makespan, "clocks": clk,
-              "replay": "real time, synchronous, one request at a time"}
     span = reqs[-1]["arrival"] - reqs[0]["arrival"]
     out = {"served_f16": srv16, "served_f32": srv32, "serial_f32": serial, "resident_model_bytes": resident,
            "offered_load_serial_f32": busy / span if span > 0 else None,
            "f16_vs_serial_f32_samples_per_s": srv16["samples_per_s"] / serial["samples_per_s"]}
+    if capacity:
+        cap16 = served("f16", paced=False)
+        out["saturated"] = {"served_f16": cap16, "serial_f32": serial_cap,
+                            "f16_vs_serial_f32_samples_per_s": cap16["samples_per_s"] / serial_cap["samples_per_s"],
+                            "what": "every request available at once: the samples/s each renderer sustains "
+                                    "when the GPU is the bottleneck"}
     if check:
         oracle.build()
         worst, rms = 0.0, []
@@ -1150,8 +1170,12 @@ def leg_noise512(torch, dev, local, flush, stream, frames=3):
     d_img = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
     d_ns = torch.empty((H, W), dtype=torch.int32, device=dev)
     out, imgs = {}, {}
-    for st in ("f32", "bf16"):
-        mid = ctx.load_model(wl["ctrl"], p, storage=st)
+    # FP32 in the power form, requested (its cells take 84 GB, beyond the
+    # AUTO default's 4 GiB), and in the B-spline form; BF16 (B-spline form)
+    for st, storage, form in (("f32", "f32", FORMS["power"]), ("f32_bspline", "f32", FORMS["bspline"]),
+                              ("bf16", "bf16", FORMS["auto"])):
+        mid = ctx.load_model(wl["ctrl"], p, storage=storage, render_form=form)
+        resident = ctx.model_info(mid)["bytes"]
         ms, samples, clk = _timed_frames(ctx, torch, dev, local, mid, wl, prm, d_tf, d_img, d_ns, flush, stream,
                                          frames, 2)
         imgs[st] = d_img.cpu().numpy()
@@ -1160,7 +1184,7 @@ def leg_noise512(torch, dev, local, flush, stream, frames=3):
         tflops = samples * C_FMA[p] * 2 / (r_ms / 1000.0) / 1e12
         peak = _fp32_peak(torch, dev, clk)
         out[st] = {"render_ms": r_ms, "samples_per_frame": samples, "samples_per_s": samples / (r_ms / 1000.0),
-                   "tflops": tflops, "frac": tflops / peak, "clocks": clk}
+                   "tflops": tflops, "frac": tflops / peak, "resident_model_bytes": resident, "clocks": clk}
     ctx.close()
     oracle.build()
     rows = np.arange(0, H, 540)
@@ -1169,6 +1193,7 @@ def leg_noise512(torch, dev, local, flush, stream, frames=3):
         e = np.minimum(np.abs(imgs[st] - ref["rgba"]).max(-1), np.abs(imgs[st] - ref["rgba_alt"]).max(-1))[rows]
         out[st]["pixel_err_vs_oracle"] = {"max": float(e.max()), "rms": float(np.sqrt(np.mean(e * e)))}
     out["bf16"]["vs_f32"] = out["f32"]["render_ms"] / out["bf16"]["render_ms"]
+    out["f32_bspline"]["vs_f32"] = out["f32"]["render_ms"] / out["f32_bspline"]["render_ms"]
     return {"workload": "noise512_p4: 3840x2160 perspective, 512^3 value noise, step 1/2048, TF 1024, shading",
             "frames": frames, "per_unit": f"{C_FMA[p]} FMA per sample", "error_rows": "every 540th row",
             **out}
@@ -1183,7 +1208,7 @@ def leg_serve_slice(torch, dev, local, args, models=8, requests=200):
     mods, reqs, prm = workloads.serving_workload(models=models, requests=requests)
     prm = dict(prm, step=args.serve_step)
     ctx = mfadvr.Context(local)
-    legs = serve_legs(ctx, torch, dev, local, mods, reqs, prm, args, err_requests=4)
+    legs = serve_legs(ctx, torch, dev, local, mods, reqs, prm, args, err_requests=4, capacity=True)
     ctx.close()
     return {"workload": f"serve slice: {requests} requests, Poisson 200/s, {models} resident models "
                         f"(degree 3-4, lattices {min(m['ncp'][0] for m in mods)}^3.."
@@ -1208,7 +1233,7 @@ def run_serve48(args, wl):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     ctx = mfadvr.Context(local)
-    legs = serve_legs(ctx, torch, dev, local, mods, reqs, prm, args, err_requests=8)
+    legs = serve_legs(ctx, torch, dev, local, mods, reqs, prm, args, err_requests=8, capacity=True)
     ctx.close()
     srv16 = legs["served_f16"]
     line = {"metric": METRIC, "value": srv16["samples_per_s"], "unit": UNIT, "n_gpus": world,

@@ -251,15 +251,17 @@ def test_load_model_rejects_sides_whose_product_wraps(ctx, torch_cuda):
     assert mid.value == -1
 
 
-@pytest.mark.parametrize("storage", ["f32", "bf16"])
-def test_full_size_value_noise_sampled_rows(ctx, torch_cuda, orc, storage):
+@pytest.mark.parametrize("storage,form", [("f32", 2), ("f32", 1), ("bf16", 0)])
+def test_full_size_value_noise_sampled_rows(ctx, torch_cuda, orc, storage, form):
     """Degree 4, 512^3 value-noise model, 3840x2160 perspective frame at step
-    1/2048 with a 1024-entry TF, in the launch the benchmark times; every
-    216th row against the oracle (on the lattice the model stores)."""
+    1/2048 with a 1024-entry TF, in the launch the benchmark times (FP32 in
+    the power form, requested: 84 GB of span polynomials; and in the B-spline
+    form); every 216th row against the oracle (on the lattice the model
+    stores)."""
     from paper_2204_11762_gb300 import workloads
     wl = workloads.value_noise_workload(512)
     ctrl = wl["ctrl"]
-    mid = ctx.load_model(ctrl, wl["degree"], storage=storage)
+    mid = ctx.load_model(ctrl, wl["degree"], storage=storage, render_form=form)
     img, ns = _render(ctx, torch_cuda, mid, wl["camera"], wl["params"], wl["tf"])
     ctx.unload_model(mid)
     deq = ctrl if storage == "f32" else dequantize(ctrl, storage)
@@ -275,7 +277,7 @@ def test_full_size_value_noise_sampled_rows(ctx, torch_cuda, orc, storage):
     # oracle's tie range and within the pixel tolerance.
     st = assert_ties_rare(img, ns, ref, rows, limit=1e-2)
     assert st["max_samples_off"] <= 2  # 1 measured
-    print(f"noise512 {storage} tie use: {st}")
+    print(f"noise512 {storage} form {form} tie use: {st}")
     assert np.isfinite(img).all()
 
 
