@@ -31,9 +31,9 @@ sys.path.insert(0, ROOT)
 # form) on the 128^3 workload from one ncu capture
 # (profiles/render_kernel_gauss128_p3_persp1024.md), valid only for the kernel
 # sources it was taken on.
-RENDER_TRAFFIC = {"sources_sha256_16": "157c2fc88db5fc61", "bytes": 539675136}
+RENDER_TRAFFIC = {"sources_sha256_16": "4fbf0b6c4a2b4006", "bytes": 534096128}
 RENDER_SOURCES = ("paper_2204_11762_gb300/csrc/render_kernels.cuh", "paper_2204_11762_gb300/csrc/mfa_basis.cuh",
-                  "paper_2204_11762_gb300/csrc/mfa_internal.h")
+                  "paper_2204_11762_gb300/csrc/mfa_internal.h", "paper_2204_11762_gb300/csrc/render_kernels.cu")
 
 METRIC = "MFA value+grad samples/s"
 UNIT = "samples/s"
@@ -363,7 +363,7 @@ def run_ours(args, wl):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else
             f"f32 (storage {args.storage})", "data": "synthetic", "config": _config(wl, args),
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": 4 * args.steps,  # tile costs, tile order, render, point query
             "frames_per_s": world * 1000.0 / r_mean,
             "render": {"samples_per_frame": render_samples, "ms_mean": r_mean,
                        "ms_p50": statistics.median(render_ms),
@@ -544,7 +544,7 @@ def run_noise512(args, wl):
                                    "TF 1024, opacity ref 1/16, shading)",
                        "model": "MFA degree 4, 512^3 control points (5-octave value noise), clamped uniform knots",
                        "l2": "flushed between steps; the 4 GiB FP32 row array exceeds L2"},
-            "gpu_launches": steps,
+            "gpu_launches": 3 * steps,  # tile costs, tile order, render
             "frames_per_s": world * 1000.0 / r_ms,
             "render": {"samples_per_frame": r["samples"], "ms_mean": r_ms, "ms_p50": statistics.median(r["ms"]),
                        "ms_p99": sorted(r["ms"])[min(len(r["ms"]) - 1, int(0.99 * len(r["ms"])))]},
@@ -628,7 +628,7 @@ def run_ml32(args, wl):
             "config": {"workload": "ml32_p3: 128x128 orthographic render of the 32^3 Marschner-Lobb model "
                                    "(Eq. 2, f_M 6, alpha 0.25, + N(0, 0.01)), step 1/256, TF 256, shading",
                        "l2": "flushed between steps (the model fits L2)"},
-            "gpu_launches": steps,
+            "gpu_launches": 3 * steps,  # tile costs, tile order, render
             "render": {"samples_per_frame": samples, "ms_mean": r_ms, "ms_p50": statistics.median(ms)},
             "parity": {"max_pixel_err": float(err.max()), "tolerance": 2e-3},
             "cpu_baseline": {"value": int(ref["nsamples"].sum()) / t_oracle, "unit": UNIT,
@@ -874,7 +874,7 @@ def run_variants(args):
                                             stream=stream))
             samples = int(d_ns.sum(dtype=torch.int64).item())
             q_ms = timed(lambda: ctx.query_points(mid, d_pts, npts, d_out, 3, stream=stream))
-            launches += 2 * steps
+            launches += 4 * steps  # tile costs, tile order, render; point query
             row = {"render_ms": r_ms, "samples": samples, "render_samples_per_s": samples / (r_ms / 1e3),
                    "query_both_ms": q_ms, "query_points_per_s": npts / (q_ms / 1e3)}
             if name == "f32":

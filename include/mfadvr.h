@@ -261,6 +261,14 @@ MFADVR_API mfadvr_status mfadvr_query_points_host_async(mfadvr_ctx *ctx, int32_t
  *  rgba_dev:     height x width x 4 FP32, premultiplied RGBA, row 0 at the
  *                top, 16-byte aligned; pixels whose ray misses the box are 0.
  *  nsamples_dev: height x width int32 samples composited per pixel, or NULL.
+ * Scheduling (no pixel depends on it): the persistent kernel's warps take
+ * 32-ray tiles costliest first, so that the frame ends on short tiles; two
+ * small kernels before it bin the tiles by the largest sample count of their
+ * rays (the chord through the box over the step) and sort them.  That order
+ * needs a scratch area from a ring of 8 (about 2.5 MiB each, allocated at
+ * the first render of the context); a render waits on its stream for the
+ * render that used the same area 8 calls earlier.  Images of more than 2^19
+ * tiles take their tiles in row order.
  * EINVAL: bad camera/params/buffers. */
 MFADVR_API mfadvr_status mfadvr_render(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_camera *camera,
                             const mfadvr_render_params *params, float *rgba_dev, int32_t *nsamples_dev,

@@ -104,6 +104,15 @@ struct mfadvr_ctx {
     mfadvr::RenderJob *h_jobs = nullptr, *d_jobs = nullptr;
     cudaEvent_t job_done[kJobSlots] = {};
     unsigned next_jobs = 0;
+    // Longest-first tile orders of mfadvr_render launches: a ring of scratch
+    // areas for images of up to kOrderTiles ray tiles (larger images take
+    // their tiles in row order), each reused only after the launch that last
+    // read it has finished (its event).  Allocated at the first such render.
+    static constexpr unsigned kOrderSlots = 8;
+    static constexpr int64_t kOrderTiles = int64_t(1) << 19;
+    char *order_pool = nullptr;
+    cudaEvent_t order_done[kOrderSlots] = {};
+    unsigned next_order = 0;
     std::map<TuneKey, mfadvr_tuning> tuning;
     mfadvr::api::Server *server = nullptr;
     // Host-buffer point queries: chunks are copied in, evaluated and copied

@@ -67,6 +67,13 @@ struct RenderSetup {
     int32_t *nsamples;                  // H x W or nullptr
     int tile_w_log2;                    // ray tiles of 2^k x 32/2^k pixels (k = 0..5)
     int ctas_per_sm;                    // resident CTAs per SM to launch (0: as many as fit)
+    // Longest-first tile order (mfadvr_render): scratch of one launch, or
+    // nullptr for row order.  tile_order: one tile index per tile;
+    // tile_level: one byte per tile; tile_hist: 64 ints (per-level counts,
+    // then per-level cursors), zeroed by the launcher.
+    int *tile_order = nullptr;
+    unsigned char *tile_level = nullptr;
+    int *tile_hist = nullptr;
 };
 
 // One image of a batched render: its model, settings and place in the
@@ -102,6 +109,10 @@ cudaError_t launch_eval_points(const ModelView &mv, const float *params, int64_t
 // the launcher zeroes it on `stream` first.  The value-only kernel runs when
 // rs.shading is 0 (no gradient is needed).
 cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream);
+// Fills rs.tile_order (when not null) with the ray tiles of this launch's
+// shape, costliest first, on `stream`: launched by the render launcher
+// before the render kernel.
+cudaError_t launch_tile_order(const RenderSetup &rs, int tiles_x, int tiles, cudaStream_t stream);
 // The same render recording, for each ray's first max_samples samples, the
 // FP32 position the kernel walks and the knot spans it contracts with
 // (mfadvr_render_trace).  FP32 models, shading on, plain (not rational).

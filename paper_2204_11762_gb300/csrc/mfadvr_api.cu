@@ -95,6 +95,56 @@ ModelView view_of(const Model &m)
 }
 
 
+// Bytes of one tile-order scratch area: 64 ints of level counts and cursors,
+// the order (an int per tile), the levels (a byte per tile).
+constexpr size_t kOrderSlotBytes = 64 * sizeof(int) + mfadvr_ctx::kOrderTiles * (sizeof(int) + 1);
+
+// Points rs->tile_order (and its scratch) at the next ring slot when the
+// launch's ray tiles fit one, after making `s` wait for the slot's previous
+// launch; *slot = -1 (row order) otherwise.  record_order marks the slot's
+// use once the render is queued.
+mfadvr_status take_order(mfadvr_ctx *ctx, RenderSetup *rs, cudaStream_t s, int *slot)
+{
+    *slot = -1;
+    rs->tile_order = nullptr;
+    rs->tile_level = nullptr;
+    rs->tile_hist = nullptr;
+    const int64_t tw = int64_t(1) << rs->tile_w_log2, th = 32 / tw;
+    const int64_t tiles = ((rs->width + tw - 1) / tw) * ((rs->height + th - 1) / th);
+    if (tiles > mfadvr_ctx::kOrderTiles) return MFADVR_OK;
+    if (!ctx->order_pool) {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, kOrderSlotBytes * mfadvr_ctx::kOrderSlots);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "tile-order allocation");
+        for (unsigned i = 0; i < mfadvr_ctx::kOrderSlots && e == cudaSuccess; ++i)
+            e = cudaEventCreateWithFlags(&ctx->order_done[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (unsigned i = 0; i < mfadvr_ctx::kOrderSlots; ++i)
+                if (ctx->order_done[i]) cudaEventDestroy(ctx->order_done[i]), ctx->order_done[i] = nullptr;
+            cudaFree(p);
+            return cuda_fail(ctx, e, "tile-order events");
+        }
+        ctx->order_pool = static_cast<char *>(p);
+    }
+    const unsigned k = ctx->next_order++ % mfadvr_ctx::kOrderSlots;
+    cudaError_t e = cudaStreamWaitEvent(s, ctx->order_done[k], 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tile-order slot wait");
+    char *base = ctx->order_pool + kOrderSlotBytes * k;
+    rs->tile_hist = reinterpret_cast<int *>(base);
+    rs->tile_order = reinterpret_cast<int *>(base + 64 * sizeof(int));
+    rs->tile_level = reinterpret_cast<unsigned char *>(base + 64 * sizeof(int) + mfadvr_ctx::kOrderTiles * sizeof(int));
+    *slot = static_cast<int>(k);
+    return MFADVR_OK;
+}
+
+mfadvr_status record_order(mfadvr_ctx *ctx, int slot, cudaStream_t s)
+{
+    if (slot < 0) return MFADVR_OK;
+    cudaError_t e = cudaEventRecord(ctx->order_done[slot], s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tile-order slot event");
+    return MFADVR_OK;
+}
+
 mfadvr_status next_counter(mfadvr_ctx *ctx, int **out)
 {
     if (!ctx->counters) {
@@ -754,6 +804,9 @@ mfadvr_status mfadvr_destroy(mfadvr_ctx *ctx)
             if (kv.second.d_poly) cudaFree(kv.second.d_poly);
         }
         if (ctx->counters) cudaFree(ctx->counters);
+        if (ctx->order_pool) cudaFree(ctx->order_pool);
+        for (unsigned i = 0; i < mfadvr_ctx::kOrderSlots; ++i)
+            if (ctx->order_done[i]) cudaEventDestroy(ctx->order_done[i]);
         if (ctx->d_jobs) cudaFree(ctx->d_jobs);
         if (ctx->h_jobs) cudaFreeHost(ctx->h_jobs);
         for (auto &e : ctx->job_done)
@@ -1067,9 +1120,11 @@ mfadvr_status mfadvr_render(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_came
     rs.nsamples = nsamples_dev;
     int *counter = nullptr;
     if (mfadvr_status st = next_counter(ctx, &counter)) return st;
+    int slot = -1;
+    if (mfadvr_status st = take_order(ctx, &rs, s, &slot)) return st;
     cudaError_t e = launch_render(view_of(*m), rs, counter, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "render launch");
-    return MFADVR_OK;
+    return record_order(ctx, slot, s);
 }
 
 mfadvr_status mfadvr_render_trace(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_camera *camera,
@@ -1141,7 +1196,12 @@ mfadvr_status mfadvr_render_host(mfadvr_ctx *ctx, int32_t model_id, const mfadvr
     }
     int *counter = nullptr;
     if (mfadvr_status st = next_counter(ctx, &counter)) return st;
+    int slot = -1;
+    if (mfadvr_status st = take_order(ctx, &rs, s, &slot)) return st;
     e = launch_render(view_of(*m), rs, counter, s);
+    if (e == cudaSuccess) {
+        if (mfadvr_status st = record_order(ctx, slot, s)) return st;
+    }
     if (e == cudaSuccess && !direct) e = cudaMemcpyAsync(rgba_host, rs.out, img_b, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && !direct && nsamples_host)
         e = cudaMemcpyAsync(nsamples_host, rs.nsamples, ns_b, cudaMemcpyDeviceToHost, s);
@@ -1232,8 +1292,15 @@ mfadvr_status mfadvr_autotune(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_ca
                     cudaEventDestroy(e1);
                     return st;
                 }
+                int slot = -1;
+                if (mfadvr_status st = take_order(ctx, &rs, s, &slot)) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return st;
+                }
                 e = cudaEventRecord(e0, s);
                 if (e == cudaSuccess) e = launch_render(view_of(*m), rs, counter, s);
+                if (e == cudaSuccess && slot >= 0) e = cudaEventRecord(ctx->order_done[slot], s);
                 if (e == cudaSuccess) e = cudaEventRecord(e1, s);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 float ms = 0.f;

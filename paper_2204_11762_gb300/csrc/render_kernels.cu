@@ -1,9 +1,105 @@
 // mfadvr_render's launchers: pick the per-degree instantiation (the kernels
 // are in render_kernels.cuh, one degree per render_pN.cu).
+#include <algorithm>
+
 #include "mfa_internal.h"
 #include "render_kernels.cuh"
 
 namespace mfadvr {
+
+namespace {
+
+constexpr int kTileLevels = 32;
+
+// Tile costs for the longest-first order.  A warp per tile: each lane's
+// ray's sample count (the chord through the box over the step: the samples
+// it takes unless it terminates early), the tile's cost the largest of its
+// 32, quantised to kTileLevels levels of the count along the box diagonal;
+// level 0 holds the costliest tiles.  level[tile] and per-level counts in
+// hist[0 .. kTileLevels).
+__global__ void __launch_bounds__(256) tile_level_kernel(RenderSetup rs, int tiles_x, int tiles,
+                                                         unsigned char *__restrict__ level, int *__restrict__ hist)
+{
+    __shared__ int s_hist[kTileLevels];
+    if (threadIdx.x < kTileLevels) s_hist[threadIdx.x] = 0;
+    __syncthreads();
+    float diag2 = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float e = rs.box_max[a] - rs.box_min[a];
+        diag2 = fmaf(e, e, diag2);
+    }
+    const float per_level = fmaxf(sqrtf(diag2) / rs.step + 1.0f, 1.0f) / static_cast<float>(kTileLevels);
+    const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    for (int tile = blockIdx.x * warps + (threadIdx.x >> 5); tile < tiles; tile += gridDim.x * warps) {
+        int px, py;
+        slot_pixel(tile * 32 + lane, tiles_x, rs.tile_w_log2, px, py);
+        int n = 0;
+        if (px < rs.width && py < rs.height) {
+            float o[3], dir[3], t0;
+            n = static_cast<int>(ray_chord(rs, px, py, o, dir, t0));
+        }
+        n = __reduce_max_sync(kFull, n);
+        if (lane == 0) {
+            const int q = min(static_cast<int>(static_cast<float>(n) / per_level), kTileLevels - 1);
+            level[tile] = static_cast<unsigned char>(kTileLevels - 1 - q);
+            atomicAdd(&s_hist[kTileLevels - 1 - q], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kTileLevels && s_hist[threadIdx.x]) atomicAdd(&hist[threadIdx.x], s_hist[threadIdx.x]);
+}
+
+// Counting sort of the tiles by level: order[] lists level 0's tiles first.
+// Lanes of a warp with equal levels take consecutive places through one
+// atomic on the level's cursor (hist[kTileLevels + level]); within a level
+// the order is that of the atomics.
+__global__ void __launch_bounds__(256) tile_order_kernel(int tiles, const unsigned char *__restrict__ level,
+                                                         int *__restrict__ hist, int *__restrict__ order)
+{
+    __shared__ int s_base[kTileLevels];
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < kTileLevels) {
+        const int c = hist[threadIdx.x];
+        int x = c;
+#pragma unroll
+        for (int o = 1; o < kTileLevels; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        s_base[threadIdx.x] = x - c;
+    }
+    __syncthreads();
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < tiles; base += stride) {
+        const int t = base + lane;
+        const bool ok = t < tiles;
+        const int lv = ok ? level[t] : kTileLevels;
+        const unsigned peers = __match_any_sync(kFull, lv);
+        const int leader = __ffs(peers) - 1;
+        int first = 0;
+        if (ok && lane == leader) first = atomicAdd(&hist[kTileLevels + lv], __popc(peers));
+        first = __shfl_sync(kFull, first, leader);
+        if (ok) order[s_base[lv] + first + __popc(peers & ((1u << lane) - 1u))] = t;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_tile_order(const RenderSetup &rs, int tiles_x, int tiles, cudaStream_t stream)
+{
+    if (tiles <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(rs.tile_hist, 0, 2 * kTileLevels * sizeof(int), stream);
+    if (e != cudaSuccess) return e;
+    const int cap = sm_count() * 8;
+    const int lv_blocks = std::min((tiles + 7) / 8, cap);
+    tile_level_kernel<<<lv_blocks, 256, 0, stream>>>(rs, tiles_x, tiles, rs.tile_level, rs.tile_hist);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int ord_blocks = std::min((tiles + 255) / 256, cap);
+    tile_order_kernel<<<ord_blocks, 256, 0, stream>>>(tiles, rs.tile_level, rs.tile_hist, rs.tile_order);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream)
 {

@@ -136,48 +136,59 @@ __device__ __forceinline__ void slot_pixel(int slot, int tiles_x, int tw_log2, i
     py = ((tile / tiles_x) << th_log2) + (l >> tw_log2);
 }
 
-// Ray definition and slab test for pixel (px, py).  Returns true when the
-// ray has samples; otherwise writes the empty pixel and returns false.
-__device__ __forceinline__ bool start_ray(const RenderSetup &rs, int px, int py, LaneRay &ray)
+// Ray of pixel (px, py): origin o, direction dir (unit length for a
+// perspective camera) and the distance t0 at which it enters the world box;
+// returns its sample count, floor((t1 - t0) / step) for the chord [t0, t1]
+// inside the box, or 0 when it misses the box.
+__device__ __forceinline__ float ray_chord(const RenderSetup &rs, int px, int py, float o[3], float dir[3],
+                                           float &t0)
 {
-    ray.pix = py * rs.width + px;
     const float sx = fmaf(rs.sx_scale, static_cast<float>(px) + 0.5f, rs.sx_off);
     const float sy = fmaf(rs.sy_scale, static_cast<float>(py) + 0.5f, rs.sy_off);
-    float o[3];
     if (rs.kind == 0) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             o[a] = fmaf(sy, rs.up[a], fmaf(sx, rs.right[a], rs.eye[a]));
-            ray.dir[a] = rs.fwd[a];
+            dir[a] = rs.fwd[a];
         }
     } else {
         float dd = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             o[a] = rs.eye[a];
-            ray.dir[a] = fmaf(sy, rs.up[a], fmaf(sx, rs.right[a], rs.fwd[a]));
-            dd = fmaf(ray.dir[a], ray.dir[a], dd);
+            dir[a] = fmaf(sy, rs.up[a], fmaf(sx, rs.right[a], rs.fwd[a]));
+            dd = fmaf(dir[a], dir[a], dd);
         }
         const float inv = 1.0f / sqrtf(dd);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) ray.dir[a] *= inv;
+        for (int a = 0; a < 3; ++a) dir[a] *= inv;
     }
     // slab test: [t0, t1] inside the box, t0 >= 0
-    float t0 = 0.0f, t1 = INFINITY;
+    t0 = 0.0f;
+    float t1 = INFINITY;
     bool hit = true;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (ray.dir[a] == 0.0f) {
+        if (dir[a] == 0.0f) {
             if (o[a] < rs.box_min[a] || o[a] > rs.box_max[a]) hit = false;
         } else {
-            float ta = (rs.box_min[a] - o[a]) / ray.dir[a];
-            float tb = (rs.box_max[a] - o[a]) / ray.dir[a];
+            float ta = (rs.box_min[a] - o[a]) / dir[a];
+            float tb = (rs.box_max[a] - o[a]) / dir[a];
             if (ta > tb) { const float s = ta; ta = tb; tb = s; }
             t0 = fmaxf(t0, ta);
             t1 = fminf(t1, tb);
         }
     }
-    ray.nsf = (hit && t1 > t0) ? floorf((t1 - t0) / rs.step) : 0.0f;
+    return (hit && t1 > t0) ? floorf((t1 - t0) / rs.step) : 0.0f;
+}
+
+// Ray definition and slab test for pixel (px, py).  Returns true when the
+// ray has samples; otherwise writes the empty pixel and returns false.
+__device__ __forceinline__ bool start_ray(const RenderSetup &rs, int px, int py, LaneRay &ray)
+{
+    ray.pix = py * rs.width + px;
+    float o[3], t0;
+    ray.nsf = ray_chord(rs, px, py, o, ray.dir, t0);
     if (ray.nsf < 1.0f) {
         rs.out[ray.pix] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (rs.nsamples) rs.nsamples[ray.pix] = 0;
@@ -361,10 +372,12 @@ __device__ __forceinline__ bool sample_step(const ModelView &mv, const RenderSet
                 const float mfa = static_cast<float>(mv.m[a]);
                 const float X = fminf(fmaxf(fmaf(s, ray.dX[a], ray.X0[a]), 0.0f), mfa);
                 // span floor(X) (the last one at X = m): an add rounded toward
-                // -infinity gives 2^23 + floor(X) exactly for 0 <= X < 2^23
+                // -infinity gives 2^23 + floor(X) exactly for 0 <= X < 2^23;
+                // the centre k + 1/2 = k23 - (2^23 - 1/2) is exact too (the
+                // operands are within a factor 2: Sterbenz's lemma)
                 const float k23 = fminf(__fadd_rd(X, 8388608.0f), 8388607.0f + mfa);
                 ray.kk[a] = __float_as_int(k23) - 0x4B000000;
-                ray.kf[a] = (k23 - 8388608.0f) + 0.5f;
+                ray.kf[a] = k23 - 8388607.5f;
                 x[a] = X - ray.kf[a];
             }
         } else {
@@ -585,10 +598,14 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P, T, NU, R>::value)
         // and a quarter of its iterations change none.  The first sample of
         // every ray is then contracted in one step of its own, and later
         // iterations carry no test for a missing predecessor.
+        // Tiles are taken in the order rs.tile_order lists them (costliest
+        // first, so that the last tiles of the frame are short ones), else
+        // in row order.
         int b = 0;
         if (lane == 0) b = atomicAdd(counter, 32);
         b = __shfl_sync(kFull, b, 0);
         if (b >= total) break;
+        if (rs.tile_order) b = __ldg(rs.tile_order + (b >> 5)) << 5;
         int px, py;
         slot_pixel(b + lane, tiles_x, tw_log2, px, py);
         bool active = px < rs.width && py < rs.height && start_ray(rs, px, py, ray);
@@ -695,6 +712,10 @@ cudaError_t launch_render_t(const ModelView &mv, const RenderSetup &rs, int *cou
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
     if (e != cudaSuccess) return e;
+    if (rs.tile_order) {
+        e = launch_tile_order(rs, (rs.width + tw - 1) / tw, static_cast<int>(tiles), stream);
+        if (e != cudaSuccess) return e;
+    }
     render_kernel<P, T, G, NU, R, Tr><<<static_cast<int>(blocks), kThreads, smem, stream>>>(mv, rs, counter, tr);
     return cudaGetLastError();
 }

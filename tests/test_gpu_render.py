@@ -171,6 +171,38 @@ def test_render_host_buffers_match_device(ctx, torch_cuda):
     ctx.unload_model(mid)
 
 
+@pytest.mark.parametrize("W,H,tune", [(640, 480, False), (640, 480, True), (4100, 4090, False)])
+def test_tile_order_leaves_pixels_unchanged(ctx, torch_cuda, W, H, tune):
+    """mfadvr_render takes its ray tiles costliest first (a pre-pass sorts
+    them by their rays' sample counts); the traced render takes them in row
+    order, as does mfadvr_render itself for images of more than 2^19 tiles
+    (the last case: 513 x 1023 tiles of 8 x 4).  Pixels do not depend on the
+    order: the same bits either way, in the tuned shape too."""
+    from paper_2204_11762_gb300 import workloads
+    torch = torch_cuda
+    rng = np.random.default_rng(77)
+    ctrl = workloads.gaussian_sum_lattice((40, 36, 44), 3, rng)
+    tf = workloads.transfer_function(rng, 64)
+    mid = ctx.load_model(ctrl, 3)
+    cam = workloads.sphere_camera(rng, fovy_deg=45.0)
+    prm = {"width": W, "height": H, "step": 1 / 96, "max_opacity": 0.95, "ref_step": 1 / 16, "shading": 1}
+    d_tf = torch.from_numpy(tf).cuda()
+    if tune:
+        ctx.autotune(mid, cam, prm, d_tf, tf.shape[0], torch.empty((H, W, 4), device="cuda"),
+                     torch.empty((H, W), dtype=torch.int32, device="cuda"))
+    img, ns = _render(ctx, torch, mid, cam, prm, tf)
+    t_img = torch.full((H, W, 4), float("nan"), device="cuda")
+    t_ns = torch.full((H, W), -1, dtype=torch.int32, device="cuda")
+    pos = torch.empty((H, W, 1, 3), device="cuda")
+    span = torch.empty((H, W, 1, 3), dtype=torch.int32, device="cuda")
+    ctx.render_trace(mid, cam, prm, d_tf, tf.shape[0], t_img, t_ns, 1, pos, span)
+    torch.cuda.synchronize()
+    assert (ns > 0).mean() > 0.2 and not np.isnan(img).any()
+    np.testing.assert_array_equal(img, t_img.cpu().numpy())
+    np.testing.assert_array_equal(ns, t_ns.cpu().numpy())
+    ctx.unload_model(mid)
+
+
 def test_full_size_gaussian_workload_sampled_rows(ctx, torch_cuda, orc):
     """The 128^3 Gaussian-sum model at 1024^2, step 1/1024, in the launch the
     benchmark times (the autotuner's shape); every 64th row against the
