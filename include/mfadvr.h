@@ -267,8 +267,10 @@ MFADVR_API mfadvr_status mfadvr_query_points_host_async(mfadvr_ctx *ctx, int32_t
  * rays (the chord through the box over the step) and sort them.  That order
  * needs a scratch area from a ring of 8 (about 2.5 MiB each, allocated at
  * the first render of the context); a render waits on its stream for the
- * render that used the same area 8 calls earlier.  Images of more than 2^19
- * tiles take their tiles in row order.
+ * render that used the same area 8 calls earlier.  Images of fewer than 32
+ * or more than 1024 tiles per SM (or more than 2^19 tiles) take their tiles
+ * in row order: too few tiles leave no tail to shorten, and with many the
+ * tail is small and row order keeps the tiles that run together close.
  * EINVAL: bad camera/params/buffers. */
 MFADVR_API mfadvr_status mfadvr_render(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_camera *camera,
                             const mfadvr_render_params *params, float *rgba_dev, int32_t *nsamples_dev,
