@@ -171,13 +171,14 @@ def test_render_host_buffers_match_device(ctx, torch_cuda):
     ctx.unload_model(mid)
 
 
-@pytest.mark.parametrize("W,H,tune", [(640, 480, False), (640, 480, True), (4100, 4090, False)])
+@pytest.mark.parametrize("W,H,tune", [(640, 480, False), (640, 480, True), (650, 470, True), (4100, 4090, False)])
 def test_tile_order_leaves_pixels_unchanged(ctx, torch_cuda, W, H, tune):
     """mfadvr_render takes its ray tiles costliest first (a pre-pass sorts
     them by their rays' sample counts); the traced render takes them in row
     order, as does mfadvr_render itself for images of more than 2^19 tiles
     (the last case: 513 x 1023 tiles of 8 x 4).  Pixels do not depend on the
-    order: the same bits either way, in the tuned shape too."""
+    order: the same bits either way, in the tuned shape too, and with tiles
+    that reach past a ragged image's edge (650 x 470)."""
     from paper_2204_11762_gb300 import workloads
     torch = torch_cuda
     rng = np.random.default_rng(77)
