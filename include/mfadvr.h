@@ -271,6 +271,8 @@ MFADVR_API mfadvr_status mfadvr_query_points_host_async(mfadvr_ctx *ctx, int32_t
  * or more than 1024 tiles per SM (or more than 2^19 tiles) take their tiles
  * in row order: too few tiles leave no tail to shorten, and with many the
  * tail is small and row order keeps the tiles that run together close.
+ * The call is not meant for CUDA stream capture: its first call on a context
+ * allocates, and later ones wait on an event of an earlier render.
  * EINVAL: bad camera/params/buffers. */
 MFADVR_API mfadvr_status mfadvr_render(mfadvr_ctx *ctx, int32_t model_id, const mfadvr_camera *camera,
                             const mfadvr_render_params *params, float *rgba_dev, int32_t *nsamples_dev,
