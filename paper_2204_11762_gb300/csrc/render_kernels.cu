@@ -11,12 +11,13 @@ namespace {
 
 constexpr int kTileLevels = 32;
 
-// Tile costs for the longest-first order.  A warp per tile: each lane's
-// ray's sample count (the chord through the box over the step: the samples
-// it takes unless it terminates early), the tile's cost the largest of its
-// 32, quantised to kTileLevels levels of the count along the box diagonal;
-// level 0 holds the costliest tiles.  level[tile] and per-level counts in
-// hist[0 .. kTileLevels).
+// Tile costs for the longest-first order.  Four lanes per tile, one per
+// corner pixel of the tile (clamped into the image: a tile's first pixel is
+// always inside it), each taking its ray's sample count (the chord through
+// the box over the step: the samples it takes unless it terminates early);
+// the tile's cost is the largest of the four, quantised to kTileLevels levels
+// of the count along the box diagonal; level 0 holds the costliest tiles.
+// level[tile] and per-level counts in hist[0 .. kTileLevels).
 __global__ void __launch_bounds__(256) tile_level_kernel(RenderSetup rs, int tiles_x, int tiles,
                                                          unsigned char *__restrict__ level, int *__restrict__ hist)
 {
@@ -30,17 +31,21 @@ __global__ void __launch_bounds__(256) tile_level_kernel(RenderSetup rs, int til
         diag2 = fmaf(e, e, diag2);
     }
     const float per_level = fmaxf(sqrtf(diag2) / rs.step + 1.0f, 1.0f) / static_cast<float>(kTileLevels);
-    const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
-    for (int tile = blockIdx.x * warps + (threadIdx.x >> 5); tile < tiles; tile += gridDim.x * warps) {
-        int px, py;
-        slot_pixel(tile * 32 + lane, tiles_x, rs.tile_w_log2, px, py);
+    const int lane = threadIdx.x & 31, corner = lane & 3, warps = blockDim.x >> 5;
+    const int tw = 1 << rs.tile_w_log2;
+    const int l = corner == 0 ? 0 : (corner == 1 ? tw - 1 : (corner == 2 ? 32 - tw : 31));  // lane-in-tile
+    for (int base = (blockIdx.x * warps + (threadIdx.x >> 5)) * 8; base < tiles; base += gridDim.x * warps * 8) {
+        const int tile = base + (lane >> 2);
         int n = 0;
-        if (px < rs.width && py < rs.height) {
+        if (tile < tiles) {
+            int px, py;
+            slot_pixel(tile * 32 + l, tiles_x, rs.tile_w_log2, px, py);
             float o[3], dir[3], t0;
-            n = static_cast<int>(ray_chord(rs, px, py, o, dir, t0));
+            n = static_cast<int>(ray_chord(rs, min(px, rs.width - 1), min(py, rs.height - 1), o, dir, t0));
         }
-        n = __reduce_max_sync(kFull, n);
-        if (lane == 0) {
+        n = max(n, __shfl_xor_sync(kFull, n, 1));
+        n = max(n, __shfl_xor_sync(kFull, n, 2));
+        if (corner == 0 && tile < tiles) {
             const int q = min(static_cast<int>(static_cast<float>(n) / per_level), kTileLevels - 1);
             level[tile] = static_cast<unsigned char>(kTileLevels - 1 - q);
             atomicAdd(&s_hist[kTileLevels - 1 - q], 1);
@@ -92,7 +97,7 @@ cudaError_t launch_tile_order(const RenderSetup &rs, int tiles_x, int tiles, cud
     cudaError_t e = cudaMemsetAsync(rs.tile_hist, 0, 2 * kTileLevels * sizeof(int), stream);
     if (e != cudaSuccess) return e;
     const int cap = sm_count() * 8;
-    const int lv_blocks = std::min((tiles + 7) / 8, cap);
+    const int lv_blocks = std::min((tiles + 63) / 64, cap);  // 8 warps of 8 tiles
     tile_level_kernel<<<lv_blocks, 256, 0, stream>>>(rs, tiles_x, tiles, rs.tile_level, rs.tile_hist);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
