@@ -329,7 +329,10 @@ typedef struct {
  * launch of a persistent kernel whose warps take 32-ray tiles from a single
  * queue over the concatenated tiles of the group's images (kernels are
  * compiled per degree, so a batch of several degrees launches once per
- * degree).  Each image equals what mfadvr_render gives for its job.
+ * degree).  Each image equals what mfadvr_render gives for its job.  As in
+ * mfadvr_render, a group of 32 to 1024 tiles per SM takes them costliest
+ * first (two small kernels before it, on the ring of order scratch areas);
+ * the serving loop's batches take them in job order.
  * 1 <= njobs <= MFADVR_MAX_BATCH.  Asynchronous on `stream`; the job table
  * is copied before the call returns.  The context keeps a ring of 32 job
  * tables and 1024 tile counters: more than 32 batches (or 1024 render

@@ -127,9 +127,16 @@ cudaError_t launch_render_trace(const ModelView &mv, const RenderSetup &rs, int 
 // shading on (grad = 1) or all off (grad = 0), all on general knots (nu = 1)
 // or all on uniform ones, all rational (rat = 1) or none (jobs_dev in device
 // memory, sorted by tile_begin, total_tiles tiles in all); `counter` is
-// zeroed on `stream` first.
+// zeroed on `stream` first.  `order`: the tiles in the order the warps take
+// them (launch_tile_order_batch), or nullptr for job order.
 cudaError_t launch_render_batch(int p, int dtype, int grad, int nu, int rat, const RenderJob *jobs_dev, int njobs,
-                                int total_tiles, int ctas_per_sm, int *counter, cudaStream_t stream);
+                                int total_tiles, int ctas_per_sm, int *counter, const int *order, cudaStream_t stream);
+// Fills order[0 .. tiles) with the tiles of a batched launch (jobs_dev, as
+// for launch_render_batch), costliest first; max_count is the largest sample
+// count along a job's box diagonal (the scale of the cost levels); level
+// (tiles bytes) and hist (64 ints) are scratch.
+cudaError_t launch_tile_order_batch(const RenderJob *jobs_dev, int njobs, int tiles, float max_count, int *order,
+                                    unsigned char *level, int *hist, cudaStream_t stream);
 // Bytes of one row-layout entry (4 x 2 FP32 or 4 x 4 16-bit control points).
 constexpr size_t row_entry_bytes(int) { return 32; }
 // Builds the row array of an n0 x n1 x n2 FP32 lattice (device memory),

@@ -99,22 +99,21 @@ ModelView view_of(const Model &m)
 // the order (an int per tile), the levels (a byte per tile).
 constexpr size_t kOrderSlotBytes = 64 * sizeof(int) + mfadvr_ctx::kOrderTiles * (sizeof(int) + 1);
 
-// Points rs->tile_order (and its scratch) at the next ring slot when the
-// launch has between 2 and 64 ray tiles per resident warp (16 per SM): with
-// fewer, every warp takes a tile or two and there is no tail to shorten; with
-// more, the tail is a small part of the frame and row order keeps the tiles
-// that run together close in the model (measured on a 3840x2160 frame: the
-// order gained nothing).  Then it makes `s` wait for the slot's previous launch;
-// *slot = -1 (row order) otherwise.  record_order marks the slot's use once
-// the render is queued.
-mfadvr_status take_order(mfadvr_ctx *ctx, RenderSetup *rs, cudaStream_t s, int *slot)
+// The next tile-order scratch area for a launch of `tiles` ray tiles, when
+// they are between 2 and 64 per resident warp (16 per SM): with fewer, every
+// warp takes a tile or two and there is no tail to shorten; with more, the
+// tail is a small part of the launch and row order keeps the tiles that run
+// together close in the model (measured on a 3840x2160 frame: the order
+// gained nothing).  Makes `s` wait for the area's previous launch; *slot = -1
+// (no order) otherwise.  record_order marks the area's use once the launch
+// that reads it is queued.
+mfadvr_status take_order_slot(mfadvr_ctx *ctx, int64_t tiles, cudaStream_t s, int **order, unsigned char **level,
+                              int **hist, int *slot)
 {
     *slot = -1;
-    rs->tile_order = nullptr;
-    rs->tile_level = nullptr;
-    rs->tile_hist = nullptr;
-    const int64_t tw = int64_t(1) << rs->tile_w_log2, th = 32 / tw;
-    const int64_t tiles = ((rs->width + tw - 1) / tw) * ((rs->height + th - 1) / th);
+    *order = nullptr;
+    *level = nullptr;
+    *hist = nullptr;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) sms = 0;
     if (tiles > mfadvr_ctx::kOrderTiles || tiles < int64_t(2) * 16 * sms || tiles > int64_t(64) * 16 * sms)
@@ -137,11 +136,20 @@ mfadvr_status take_order(mfadvr_ctx *ctx, RenderSetup *rs, cudaStream_t s, int *
     cudaError_t e = cudaStreamWaitEvent(s, ctx->order_done[k], 0);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tile-order slot wait");
     char *base = ctx->order_pool + kOrderSlotBytes * k;
-    rs->tile_hist = reinterpret_cast<int *>(base);
-    rs->tile_order = reinterpret_cast<int *>(base + 64 * sizeof(int));
-    rs->tile_level = reinterpret_cast<unsigned char *>(base + 64 * sizeof(int) + mfadvr_ctx::kOrderTiles * sizeof(int));
+    *hist = reinterpret_cast<int *>(base);
+    *order = reinterpret_cast<int *>(base + 64 * sizeof(int));
+    *level = reinterpret_cast<unsigned char *>(base + 64 * sizeof(int) + mfadvr_ctx::kOrderTiles * sizeof(int));
     *slot = static_cast<int>(k);
     return MFADVR_OK;
+}
+
+// Points rs->tile_order (and its scratch) at an order area for this render
+// (take_order_slot), or at nothing (row order).
+mfadvr_status take_order(mfadvr_ctx *ctx, RenderSetup *rs, cudaStream_t s, int *slot)
+{
+    const int64_t tw = int64_t(1) << rs->tile_w_log2, th = 32 / tw;
+    const int64_t tiles = ((rs->width + tw - 1) / tw) * ((rs->height + th - 1) / th);
+    return take_order_slot(ctx, tiles, s, &rs->tile_order, &rs->tile_level, &rs->tile_hist, slot);
 }
 
 mfadvr_status record_order(mfadvr_ctx *ctx, int slot, cudaStream_t s)
@@ -1249,8 +1257,30 @@ mfadvr_status mfadvr_render_batch(mfadvr_ctx *ctx, int32_t njobs, const mfadvr_r
     for (const BatchGroup &gr : groups) {
         int *counter = nullptr;
         if (mfadvr_status st = next_counter(ctx, &counter)) return st;
-        e = launch_render_batch(gr.p, gr.dtype, gr.grad, gr.nu, gr.rat, dj + gr.first, gr.count, gr.tiles, 0, counter, s);
+        // the group's tiles costliest first (as mfadvr_render), on one scale
+        // of cost levels: the largest sample count along a job's box diagonal
+        int *order = nullptr, *hist = nullptr;
+        unsigned char *level = nullptr;
+        int oslot = -1;
+        if (mfadvr_status st = take_order_slot(ctx, gr.tiles, s, &order, &level, &hist, &oslot)) return st;
+        if (oslot >= 0) {
+            float max_count = 1.0f;
+            for (int i = gr.first; i < gr.first + gr.count; ++i) {
+                const RenderSetup &r = hj[i].rs;
+                double d2 = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    const double ext = static_cast<double>(r.box_max[a]) - r.box_min[a];
+                    d2 += ext * ext;
+                }
+                max_count = std::max(max_count, static_cast<float>(std::sqrt(d2) / r.step + 1.0));
+            }
+            e = launch_tile_order_batch(dj + gr.first, gr.count, gr.tiles, max_count, order, level, hist, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "batched tile order");
+        }
+        e = launch_render_batch(gr.p, gr.dtype, gr.grad, gr.nu, gr.rat, dj + gr.first, gr.count, gr.tiles, 0, counter,
+                                order, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "batched render launch");
+        if (mfadvr_status st = record_order(ctx, oslot, s)) return st;
     }
     e = cudaEventRecord(ctx->job_done[slot], s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "job-table slot event");

@@ -55,6 +55,50 @@ __global__ void __launch_bounds__(256) tile_level_kernel(RenderSetup rs, int til
     if (threadIdx.x < kTileLevels && s_hist[threadIdx.x]) atomicAdd(&hist[threadIdx.x], s_hist[threadIdx.x]);
 }
 
+// The same for a batched launch: tile t of the concatenated sequence belongs
+// to the job whose tile_begin is the largest at or below t (jobs sorted by
+// tile_begin); its corner rays use that job's camera, box and step.  One
+// scale of levels for all jobs (per_level samples per level, the host's
+// largest diagonal count over the jobs / kTileLevels), so that tiles of
+// different jobs compare.
+__global__ void __launch_bounds__(256) tile_level_batch_kernel(const RenderJob *__restrict__ jobs, int njobs, int tiles,
+                                                               float per_level, unsigned char *__restrict__ level,
+                                                               int *__restrict__ hist)
+{
+    __shared__ int s_hist[kTileLevels];
+    if (threadIdx.x < kTileLevels) s_hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, corner = lane & 3, warps = blockDim.x >> 5;
+    for (int base = (blockIdx.x * warps + (threadIdx.x >> 5)) * 8; base < tiles; base += gridDim.x * warps * 8) {
+        const int tile = base + (lane >> 2);
+        int n = 0;
+        if (tile < tiles) {
+            int lo = 0, hi = njobs - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(&jobs[mid].tile_begin) <= tile) lo = mid;
+                else hi = mid - 1;
+            }
+            const RenderSetup &rs = jobs[lo].rs;
+            const int tw_log2 = rs.tile_w_log2, tw = 1 << tw_log2;
+            const int l = corner == 0 ? 0 : (corner == 1 ? tw - 1 : (corner == 2 ? 32 - tw : 31));
+            int px, py;
+            slot_pixel((tile - jobs[lo].tile_begin) * 32 + l, jobs[lo].tiles_x, tw_log2, px, py);
+            float o[3], dir[3], t0;
+            n = static_cast<int>(ray_chord(rs, min(px, rs.width - 1), min(py, rs.height - 1), o, dir, t0));
+        }
+        n = max(n, __shfl_xor_sync(kFull, n, 1));
+        n = max(n, __shfl_xor_sync(kFull, n, 2));
+        if (corner == 0 && tile < tiles) {
+            const int q = min(static_cast<int>(static_cast<float>(n) / per_level), kTileLevels - 1);
+            level[tile] = static_cast<unsigned char>(kTileLevels - 1 - q);
+            atomicAdd(&s_hist[kTileLevels - 1 - q], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kTileLevels && s_hist[threadIdx.x]) atomicAdd(&hist[threadIdx.x], s_hist[threadIdx.x]);
+}
+
 // Counting sort of the tiles by level: order[] lists level 0's tiles first.
 // Lanes of a warp with equal levels take consecutive places through one
 // atomic on the level's cursor (hist[kTileLevels + level]); within a level
@@ -106,6 +150,23 @@ cudaError_t launch_tile_order(const RenderSetup &rs, int tiles_x, int tiles, cud
     return cudaGetLastError();
 }
 
+cudaError_t launch_tile_order_batch(const RenderJob *jobs_dev, int njobs, int tiles, float max_count, int *order,
+                                    unsigned char *level, int *hist, cudaStream_t stream)
+{
+    if (tiles <= 0 || njobs <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(hist, 0, 2 * kTileLevels * sizeof(int), stream);
+    if (e != cudaSuccess) return e;
+    const int cap = sm_count() * 8;
+    const float per_level = fmaxf(max_count, 1.0f) / static_cast<float>(kTileLevels);
+    const int lv_blocks = std::min((tiles + 63) / 64, cap);
+    tile_level_batch_kernel<<<lv_blocks, 256, 0, stream>>>(jobs_dev, njobs, tiles, per_level, level, hist);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int ord_blocks = std::min((tiles + 255) / 256, cap);
+    tile_order_kernel<<<ord_blocks, 256, 0, stream>>>(tiles, level, hist, order);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_render(const ModelView &mv, const RenderSetup &rs, int *counter, cudaStream_t stream)
 {
     switch (mv.p) {
@@ -132,23 +193,23 @@ cudaError_t launch_render_trace(const ModelView &mv, const RenderSetup &rs, int 
 }
 
 cudaError_t launch_render_batch(int p, int dtype, int grad, int nu, int rat, const RenderJob *jobs_dev, int njobs,
-                                int total_tiles, int ctas_per_sm, int *counter, cudaStream_t stream)
+                                int total_tiles, int ctas_per_sm, int *counter, const int *order, cudaStream_t stream)
 {
     switch (p) {
     case 1:
-        return launch_render_batch_p1(dtype, grad, nu, rat, jobs_dev, njobs, total_tiles, ctas_per_sm, counter,
+        return launch_render_batch_p1(dtype, grad, nu, rat, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, order,
                                         stream);
     case 2:
-        return launch_render_batch_p2(dtype, grad, nu, rat, jobs_dev, njobs, total_tiles, ctas_per_sm, counter,
+        return launch_render_batch_p2(dtype, grad, nu, rat, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, order,
                                         stream);
     case 3:
-        return launch_render_batch_p3(dtype, grad, nu, rat, jobs_dev, njobs, total_tiles, ctas_per_sm, counter,
+        return launch_render_batch_p3(dtype, grad, nu, rat, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, order,
                                         stream);
     case 4:
-        return launch_render_batch_p4(dtype, grad, nu, rat, jobs_dev, njobs, total_tiles, ctas_per_sm, counter,
+        return launch_render_batch_p4(dtype, grad, nu, rat, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, order,
                                         stream);
     case 5:
-        return launch_render_batch_p5(dtype, grad, nu, rat, jobs_dev, njobs, total_tiles, ctas_per_sm, counter,
+        return launch_render_batch_p5(dtype, grad, nu, rat, jobs_dev, njobs, total_tiles, ctas_per_sm, counter, order,
                                         stream);
     default: return cudaErrorInvalidValue;
     }

@@ -620,7 +620,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P, T, NU, R>::value)
 // ---------------------------------------------------------------------------
 template <int P, typename T, bool G, bool NU, bool R>
 __global__ void __launch_bounds__(kThreads, MinBlocks<P, T, NU, R>::value)
-    render_batch_kernel(const RenderJob *__restrict__ jobs, int njobs, int total_tiles, int *__restrict__ counter)
+    render_batch_kernel(const RenderJob *__restrict__ jobs, int njobs, int total_tiles, int *__restrict__ counter,
+                        const int *__restrict__ order)
 {
     __shared__ RenderJob s_job[kWarps];  // the current job of each warp
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -643,8 +644,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P, T, NU, R>::value)
                 int t = 0;
                 if (lane == 0) t = atomicAdd(counter, 1);
                 t = __shfl_sync(kFull, t, 0);
+                // tiles costliest first when `order` lists them, else in job order
                 if (t >= total_tiles) exhausted = true;
-                else held = t;
+                else held = order ? __ldg(order + t) : t;
             }
             if (held >= 0 && pool_next >= pool_end) {
                 // the job owning the tile: jobs are sorted by tile_begin
@@ -727,7 +729,7 @@ cudaError_t launch_render_t(const ModelView &mv, const RenderSetup &rs, int *cou
 
 template <int P, typename T, bool G, bool NU, bool R>
 cudaError_t launch_batch_t(const RenderJob *jobs, int njobs, int total_tiles, int ctas_per_sm, int *counter,
-                           cudaStream_t stream)
+                           const int *order, cudaStream_t stream)
 {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_batch_kernel<P, T, G, NU, R>, kThreads, 0);
@@ -740,7 +742,7 @@ cudaError_t launch_batch_t(const RenderJob *jobs, int njobs, int total_tiles, in
     if (blocks < 1) return cudaSuccess;
     e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
     if (e != cudaSuccess) return e;
-    render_batch_kernel<P, T, G, NU, R><<<static_cast<int>(blocks), kThreads, 0, stream>>>(jobs, njobs, total_tiles, counter);
+    render_batch_kernel<P, T, G, NU, R><<<static_cast<int>(blocks), kThreads, 0, stream>>>(jobs, njobs, total_tiles, counter, order);
     return cudaGetLastError();
 }
 
@@ -766,9 +768,9 @@ struct RenderTrace {
 template <int P, typename T, bool G, bool NU, bool R>
 struct RenderBatch {
     static cudaError_t run(const RenderJob *jobs, int njobs, int total_tiles, int ctas_per_sm, int *counter,
-                           cudaStream_t s)
+                           const int *order, cudaStream_t s)
     {
-        return launch_batch_t<P, T, G, NU, R>(jobs, njobs, total_tiles, ctas_per_sm, counter, s);
+        return launch_batch_t<P, T, G, NU, R>(jobs, njobs, total_tiles, ctas_per_sm, counter, order, s);
     }
 };
 
@@ -838,10 +840,10 @@ cudaError_t dispatch_degree(int dtype, bool grad, bool nu, bool rat, A... args)
     }                                                                                                        \
     cudaError_t launch_render_batch_p##PP(int dtype, int grad, int nu, int rat, const RenderJob *jobs_dev,     \
                                           int njobs, int total_tiles, int ctas_per_sm, int *counter,           \
-                                          cudaStream_t stream)                                               \
+                                          const int *order, cudaStream_t stream)                             \
     {                                                                                                        \
         return dispatch_degree<PP, RenderBatch>(dtype, grad != 0, nu != 0, rat != 0, jobs_dev, njobs,         \
-                                                 total_tiles, ctas_per_sm, counter, stream);                 \
+                                                 total_tiles, ctas_per_sm, counter, order, stream);          \
     }
 
 cudaError_t launch_render_p1(const ModelView &, const RenderSetup &, int *, cudaStream_t);
@@ -854,10 +856,15 @@ cudaError_t launch_render_trace_p2(const ModelView &, const RenderSetup &, int *
 cudaError_t launch_render_trace_p3(const ModelView &, const RenderSetup &, int *, const TraceOn &, cudaStream_t);
 cudaError_t launch_render_trace_p4(const ModelView &, const RenderSetup &, int *, const TraceOn &, cudaStream_t);
 cudaError_t launch_render_trace_p5(const ModelView &, const RenderSetup &, int *, const TraceOn &, cudaStream_t);
-cudaError_t launch_render_batch_p1(int, int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);
-cudaError_t launch_render_batch_p2(int, int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);
-cudaError_t launch_render_batch_p3(int, int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);
-cudaError_t launch_render_batch_p4(int, int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);
-cudaError_t launch_render_batch_p5(int, int, int, int, const RenderJob *, int, int, int, int *, cudaStream_t);
+cudaError_t launch_render_batch_p1(int, int, int, int, const RenderJob *, int, int, int, int *, const int *,
+                                   cudaStream_t);
+cudaError_t launch_render_batch_p2(int, int, int, int, const RenderJob *, int, int, int, int *, const int *,
+                                   cudaStream_t);
+cudaError_t launch_render_batch_p3(int, int, int, int, const RenderJob *, int, int, int, int *, const int *,
+                                   cudaStream_t);
+cudaError_t launch_render_batch_p4(int, int, int, int, const RenderJob *, int, int, int, int *, const int *,
+                                   cudaStream_t);
+cudaError_t launch_render_batch_p5(int, int, int, int, const RenderJob *, int, int, int, int *, const int *,
+                                   cudaStream_t);
 
 }  // namespace mfadvr

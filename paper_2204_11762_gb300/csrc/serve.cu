@@ -116,7 +116,7 @@ struct Server {
             if (body != cudaSuccess) break;
             int *counter = counters + (next_counter++ % kCounters);
             body = launch_render_batch(g.p, g.dtype, g.grad, g.nu, g.rat, dj + g.first, g.count, g.tiles, 0, counter,
-                                       s);
+                                       nullptr, s);
         }
         e = cudaStreamEndCapture(s, &graph);
         if (body != cudaSuccess) e = body;

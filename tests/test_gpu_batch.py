@@ -206,3 +206,26 @@ def test_tile_order_leaves_every_kernel_kind_unchanged(torch_cuda, kind):
         assert (ns_b > 0).mean() > 0.2
         np.testing.assert_array_equal(img.cpu().numpy(), img_b)
         np.testing.assert_array_equal(ns.cpu().numpy(), ns_b)
+
+
+def test_ordered_batch_of_several_jobs_equals_single_renders(torch_cuda):
+    """Three degree-3 jobs of different sizes, models and cameras in one
+    launch (20800 tiles of 8 x 4: the group takes its tiles costliest first,
+    each tile's cost from its own job's camera), and a degree-2 group with
+    them: every image equals mfadvr_render's bit for bit."""
+    from paper_2204_11762_gb300 import mfadvr
+    torch = torch_cuda
+    specs = [(3, (40, 36, 44), "f32", (640, 480)), (3, (30, 33, 28), "f32", (480, 320)),
+             (3, (24, 26, 22), "f32", (512, 400)), (2, (30, 25, 33), "f32", (300, 200))]
+    with mfadvr.Context(0) as ctx:
+        jobs = _jobs(ctx, torch, specs, seed=17)
+        ctx.render_batch(jobs)
+        torch.cuda.synchronize()
+        batch = [(j["rgba_dev"].cpu().numpy(), j["nsamples_dev"].cpu().numpy()) for j in jobs]
+        for j, (img, ns) in zip(jobs, batch):
+            assert not np.isnan(img).any() and (ns >= 0).all()
+            ctx.render(j["model_id"], j["camera"], j["params"], j["tf_dev"], j["tf_size"], j["rgba_dev"],
+                       j["nsamples_dev"])
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(img, j["rgba_dev"].cpu().numpy())
+            np.testing.assert_array_equal(ns, j["nsamples_dev"].cpu().numpy())
