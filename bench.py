@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 # form) on the 128^3 workload from one ncu capture
 # (profiles/render_kernel_gauss128_p3_persp1024.md), valid only for the kernel
 # sources it was taken on.
-RENDER_TRAFFIC = {"sources_sha256_16": "3e3eb472bb0a95db", "bytes": 536469760}
+RENDER_TRAFFIC = {"sources_sha256_16": "98fa770bb15a0f88", "bytes": 537079040}
 RENDER_SOURCES = ("paper_2204_11762_gb300/csrc/render_kernels.cuh", "paper_2204_11762_gb300/csrc/mfa_basis.cuh",
                   "paper_2204_11762_gb300/csrc/mfa_internal.h")
 
