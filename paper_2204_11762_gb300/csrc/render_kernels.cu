@@ -11,6 +11,28 @@ namespace {
 
 constexpr int kTileLevels = 32;
 
+// Lane-in-tile of corner c (0..3) of a tile of tw x 32/tw pixels.
+__device__ __forceinline__ int corner_lane(int c, int tw)
+{
+    return c == 0 ? 0 : (c == 1 ? tw - 1 : (c == 2 ? 32 - tw : 31));
+}
+
+// Takes the largest of the sample counts n of the four lanes of a corner
+// group (lanes 4g .. 4g + 3, all lanes of the warp calling) and, in the
+// group's first lane, records the tile's level (kTileLevels levels of
+// per_level samples, level 0 the costliest) and counts it in s_hist.
+__device__ __forceinline__ void record_tile_level(int n, bool valid, int tile, float per_level,
+                                                  unsigned char *__restrict__ level, int *s_hist)
+{
+    n = max(n, __shfl_xor_sync(kFull, n, 1));
+    n = max(n, __shfl_xor_sync(kFull, n, 2));
+    if ((threadIdx.x & 3) == 0 && valid) {
+        const int q = min(static_cast<int>(static_cast<float>(n) / per_level), kTileLevels - 1);
+        level[tile] = static_cast<unsigned char>(kTileLevels - 1 - q);
+        atomicAdd(&s_hist[kTileLevels - 1 - q], 1);
+    }
+}
+
 // Tile costs for the longest-first order.  Four lanes per tile, one per
 // corner pixel of the tile (clamped into the image: a tile's first pixel is
 // always inside it), each taking its ray's sample count (the chord through
@@ -31,9 +53,8 @@ __global__ void __launch_bounds__(256) tile_level_kernel(RenderSetup rs, int til
         diag2 = fmaf(e, e, diag2);
     }
     const float per_level = fmaxf(sqrtf(diag2) / rs.step + 1.0f, 1.0f) / static_cast<float>(kTileLevels);
-    const int lane = threadIdx.x & 31, corner = lane & 3, warps = blockDim.x >> 5;
-    const int tw = 1 << rs.tile_w_log2;
-    const int l = corner == 0 ? 0 : (corner == 1 ? tw - 1 : (corner == 2 ? 32 - tw : 31));  // lane-in-tile
+    const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    const int l = corner_lane(lane & 3, 1 << rs.tile_w_log2);
     for (int base = (blockIdx.x * warps + (threadIdx.x >> 5)) * 8; base < tiles; base += gridDim.x * warps * 8) {
         const int tile = base + (lane >> 2);
         int n = 0;
@@ -43,13 +64,7 @@ __global__ void __launch_bounds__(256) tile_level_kernel(RenderSetup rs, int til
             float o[3], dir[3], t0;
             n = static_cast<int>(ray_chord(rs, min(px, rs.width - 1), min(py, rs.height - 1), o, dir, t0));
         }
-        n = max(n, __shfl_xor_sync(kFull, n, 1));
-        n = max(n, __shfl_xor_sync(kFull, n, 2));
-        if (corner == 0 && tile < tiles) {
-            const int q = min(static_cast<int>(static_cast<float>(n) / per_level), kTileLevels - 1);
-            level[tile] = static_cast<unsigned char>(kTileLevels - 1 - q);
-            atomicAdd(&s_hist[kTileLevels - 1 - q], 1);
-        }
+        record_tile_level(n, tile < tiles, tile, per_level, level, s_hist);
     }
     __syncthreads();
     if (threadIdx.x < kTileLevels && s_hist[threadIdx.x]) atomicAdd(&hist[threadIdx.x], s_hist[threadIdx.x]);
@@ -68,7 +83,7 @@ __global__ void __launch_bounds__(256) tile_level_batch_kernel(const RenderJob *
     __shared__ int s_hist[kTileLevels];
     if (threadIdx.x < kTileLevels) s_hist[threadIdx.x] = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31, corner = lane & 3, warps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
     for (int base = (blockIdx.x * warps + (threadIdx.x >> 5)) * 8; base < tiles; base += gridDim.x * warps * 8) {
         const int tile = base + (lane >> 2);
         int n = 0;
@@ -80,20 +95,13 @@ __global__ void __launch_bounds__(256) tile_level_batch_kernel(const RenderJob *
                 else hi = mid - 1;
             }
             const RenderSetup &rs = jobs[lo].rs;
-            const int tw_log2 = rs.tile_w_log2, tw = 1 << tw_log2;
-            const int l = corner == 0 ? 0 : (corner == 1 ? tw - 1 : (corner == 2 ? 32 - tw : 31));
             int px, py;
-            slot_pixel((tile - jobs[lo].tile_begin) * 32 + l, jobs[lo].tiles_x, tw_log2, px, py);
+            slot_pixel((tile - jobs[lo].tile_begin) * 32 + corner_lane(lane & 3, 1 << rs.tile_w_log2),
+                       jobs[lo].tiles_x, rs.tile_w_log2, px, py);
             float o[3], dir[3], t0;
             n = static_cast<int>(ray_chord(rs, min(px, rs.width - 1), min(py, rs.height - 1), o, dir, t0));
         }
-        n = max(n, __shfl_xor_sync(kFull, n, 1));
-        n = max(n, __shfl_xor_sync(kFull, n, 2));
-        if (corner == 0 && tile < tiles) {
-            const int q = min(static_cast<int>(static_cast<float>(n) / per_level), kTileLevels - 1);
-            level[tile] = static_cast<unsigned char>(kTileLevels - 1 - q);
-            atomicAdd(&s_hist[kTileLevels - 1 - q], 1);
-        }
+        record_tile_level(n, tile < tiles, tile, per_level, level, s_hist);
     }
     __syncthreads();
     if (threadIdx.x < kTileLevels && s_hist[threadIdx.x]) atomicAdd(&hist[threadIdx.x], s_hist[threadIdx.x]);
